@@ -1,0 +1,424 @@
+/*
+ * ksg_oracle.c -- CPU oracle for the KSG conditional-mutual-information path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain, obviously correct
+ * statement of what the GPU library computes.  Only the tests, the package's
+ * smoke check and the benchmark's CPU-baseline leg may load it.  It shares no
+ * code, header, table or constant generator with the CUDA library.
+ *
+ * What it follows (the paper is the IDTxl software paper, arXiv 1807.10459):
+ *   - Summary, paragraph 6: the nonlinear estimator of Kraskov, Stoegbauer and
+ *     Grassberger (2004) for (conditional) mutual information.  The paper
+ *     prints no formula; the estimator used here is KSG "algorithm 1" in its
+ *     conditional form (a reading, listed in the design notes):
+ *         I(X;Y|Z) = psi(k) + (1/N) sum_i [ psi(n_z+1) - psi(n_xz+1) - psi(n_yz+1) ]
+ *     with eps_i the k-th smallest joint max-norm distance over j != i and
+ *     n_S the number of j != i whose max-norm distance in subspace S is
+ *     strictly smaller than eps_i.  Result in nats.
+ *   - Summary, paragraph 4: surrogate null distributions gate the greedy
+ *     parent selection and stop it.  Surrogates permute the rows of X
+ *     (a reading); the gate is the maximum statistic over candidates.
+ *
+ * Arithmetic: distances are fp32 (|a-b| in round-to-nearest, then max), the
+ * digamma values and all sums are computed in long double / double.  Build
+ * without -ffast-math and with -ffp-contract=off.
+ *
+ * Parity status of each function (what pins it) is stated in its comment.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Digamma at positive integers.                                             */
+/* Definition: psi(1) = -gamma (Euler-Mascheroni), psi(n+1) = psi(n) + 1/n.  */
+/* Pinned by: scipy.special.digamma at integers; psi(1) = -gamma.            */
+/* ------------------------------------------------------------------------ */
+static const long double ORC_EULER_GAMMA = 0.577215664901532860606512090082402431L;
+
+/* out[0] is set to NaN (psi has a pole at 0); out[n] = psi(n) for 1 <= n <= n_max. */
+int orc_psi_table(int64_t n_max, double *out)
+{
+    if (n_max < 1 || out == NULL) return -1;
+    long double acc = -ORC_EULER_GAMMA;
+    out[0] = NAN;
+    for (int64_t n = 1; n <= n_max; ++n) {
+        out[n] = (double)acc;
+        acc += 1.0L / (long double)n;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Max-norm distances between samples i and j in a block of columns.       */
+/* Columns are stored one after another with leading dimension ld:          */
+/* value of dimension d at sample t is col[d*ld + t].  dim == 0 gives 0.     */
+/* ------------------------------------------------------------------------ */
+static float orc_maxnorm(const float *col, int dim, int64_t ld, int64_t i, int64_t j)
+{
+    float m = 0.0f;
+    for (int d = 0; d < dim; ++d) {
+        float a = col[(int64_t)d * ld + i];
+        float b = col[(int64_t)d * ld + j];
+        float v = fabsf(a - b);
+        if (v > m) m = v;
+    }
+    return m;
+}
+
+static float orc_max2(float a, float b) { return a > b ? a : b; }
+
+/* ------------------------------------------------------------------------ */
+/* KSG neighbour statistics of one estimate.                                 */
+/*   eps[i]  = k-th smallest of { max(dX,dY,dZ)(i,j) : j != i }              */
+/*   nxz[i]  = #{ j != i : max(dX,dZ)(i,j) < eps[i] }                        */
+/*   nyz[i]  = #{ j != i : max(dY,dZ)(i,j) < eps[i] }                        */
+/*   nz[i]   = #{ j != i : dZ(i,j)        < eps[i] }   (dz == 0: dZ = 0)     */
+/* Pinned by: the hand-worked N=6 example, an independent numpy brute force, */
+/* the X<->Y swap, sample-reordering and power-of-two scaling invariants.    */
+/* Returns 0, or -1 on bad arguments.                                        */
+/* ------------------------------------------------------------------------ */
+/* Statistics of one query i; best[] is scratch for k floats. */
+static void orc_ksg_query(const float *x, int dx, const float *y, int dy, const float *z, int dz,
+                          int64_t n, int64_t ld, int k, int64_t i, float *best, float *eps,
+                          int32_t *nxz, int32_t *nyz, int32_t *nz)
+{
+    /* pass 1: the k smallest joint distances, kept sorted ascending */
+    for (int m = 0; m < k; ++m) best[m] = INFINITY;
+    for (int64_t j = 0; j < n; ++j) {
+        if (j == i) continue;
+        float d = orc_max2(orc_maxnorm(x, dx, ld, i, j),
+                           orc_max2(orc_maxnorm(y, dy, ld, i, j), orc_maxnorm(z, dz, ld, i, j)));
+        if (d < best[k - 1]) {
+            int m = k - 1;
+            while (m > 0 && best[m - 1] > d) {
+                best[m] = best[m - 1];
+                --m;
+            }
+            best[m] = d;
+        }
+    }
+    float e = best[k - 1];
+    *eps = e;
+    /* pass 2: strict-radius counts in the three subspaces */
+    int32_t cxz = 0, cyz = 0, cz = 0;
+    for (int64_t j = 0; j < n; ++j) {
+        if (j == i) continue;
+        float ddx = orc_maxnorm(x, dx, ld, i, j);
+        float ddy = orc_maxnorm(y, dy, ld, i, j);
+        float ddz = orc_maxnorm(z, dz, ld, i, j);
+        if (orc_max2(ddx, ddz) < e) ++cxz;
+        if (orc_max2(ddy, ddz) < e) ++cyz;
+        if (ddz < e) ++cz;
+    }
+    *nxz = cxz;
+    *nyz = cyz;
+    *nz = cz;
+}
+
+static int orc_args_ok(const float *x, int dx, const float *y, int dy, const float *z, int dz,
+                       int64_t n, int64_t ld, int k)
+{
+    if (n < 2 || k < 1 || k > n - 1 || dx < 1 || dy < 1 || dz < 0 || ld < n) return 0;
+    if (!x || !y || (dz > 0 && !z)) return 0;
+    return 1;
+}
+
+int orc_ksg_counts(const float *x, int dx, const float *y, int dy, const float *z, int dz,
+                   int64_t n, int64_t ld, int k, float *eps, int32_t *nxz, int32_t *nyz,
+                   int32_t *nz)
+{
+    if (!orc_args_ok(x, dx, y, dy, z, dz, n, ld, k) || !eps || !nxz || !nyz || !nz) return -1;
+#pragma omp parallel
+    {
+        float *best = (float *)malloc(sizeof(float) * (size_t)k);
+#pragma omp for schedule(static)
+        for (int64_t i = 0; i < n; ++i)
+            orc_ksg_query(x, dx, y, dy, z, dz, n, ld, k, i, best, &eps[i], &nxz[i], &nyz[i],
+                          &nz[i]);
+        free(best);
+    }
+    return 0;
+}
+
+/* The same statistics for the m queries listed in idx (outputs indexed 0..m-1). */
+int orc_ksg_counts_at(const float *x, int dx, const float *y, int dy, const float *z, int dz,
+                      int64_t n, int64_t ld, int k, const int64_t *idx, int64_t m, float *eps,
+                      int32_t *nxz, int32_t *nyz, int32_t *nz)
+{
+    if (!orc_args_ok(x, dx, y, dy, z, dz, n, ld, k) || !idx || m < 0 || !eps || !nxz || !nyz ||
+        !nz)
+        return -1;
+    for (int64_t q = 0; q < m; ++q)
+        if (idx[q] < 0 || idx[q] >= n) return -1;
+#pragma omp parallel
+    {
+        float *best = (float *)malloc(sizeof(float) * (size_t)k);
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t q = 0; q < m; ++q)
+            orc_ksg_query(x, dx, y, dy, z, dz, n, ld, k, idx[q], best, &eps[q], &nxz[q], &nyz[q],
+                          &nz[q]);
+        free(best);
+    }
+    return 0;
+}
+
+/* The estimate from its counts: psi(k) + mean_i[psi(nz+1) - psi(nxz+1) - psi(nyz+1)].
+ * psi is the table from orc_psi_table covering index n (counts are <= n-1). */
+double orc_cmi_from_counts(const int32_t *nxz, const int32_t *nyz, const int32_t *nz, int64_t n,
+                           int k, const double *psi)
+{
+    double sum = 0.0;
+    for (int64_t i = 0; i < n; ++i)
+        sum += psi[nz[i] + 1] - psi[nxz[i] + 1] - psi[nyz[i] + 1];
+    return psi[k] + sum / (double)n;
+}
+
+/* One KSG CMI estimate I(X;Y|Z) in nats.  Optional outputs may be NULL.
+ * Returns 0 or -1. */
+int orc_cmi_ksg(const float *x, int dx, const float *y, int dy, const float *z, int dz, int64_t n,
+                int64_t ld, int k, double *cmi, float *eps_out, int32_t *counts_out)
+{
+    if (n < 2 || !cmi) return -1;
+    float *eps = eps_out ? eps_out : (float *)malloc(sizeof(float) * (size_t)n);
+    int32_t *cnt = counts_out ? counts_out : (int32_t *)malloc(sizeof(int32_t) * 3 * (size_t)n);
+    double *psi = (double *)malloc(sizeof(double) * (size_t)(n + 1));
+    int rc = orc_ksg_counts(x, dx, y, dy, z, dz, n, ld, k, eps, cnt, cnt + n, cnt + 2 * n);
+    if (rc == 0) {
+        orc_psi_table(n, psi);
+        *cmi = orc_cmi_from_counts(cnt, cnt + n, cnt + 2 * n, n, k, psi);
+    }
+    free(psi);
+    if (!eps_out) free(eps);
+    if (!counts_out) free(cnt);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Surrogate permutations (a reading: the paper only says "surrogates").     */
+/*                                                                           */
+/* SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): the state advances by      */
+/* 0x9E3779B97F4A7C15 and each output is the state passed through the mixer  */
+/*   z ^= z>>30; z *= 0xBF58476D1CE4E5B9; z ^= z>>27; z *= 0x94D049BB133111EB; */
+/*   z ^= z>>31.                                                             */
+/* Pinned by: the generator's published output sequence for seed 1234567.    */
+/*                                                                           */
+/* The permutation of [0,n) keyed by (seed, stream) is the Fisher-Yates      */
+/* (Durstenfeld) shuffle of the identity driven by SplitMix64 started from   */
+/* the state seed ^ mix(stream): for i = n-1 down to 1, draw r and swap      */
+/* a[i] with a[j], j = floor(r * (i+1) / 2^64) (the high word of the 128-bit */
+/* product).  pi = a.                                                        */
+/* Pinned by: bijection on many n, chi-square uniformity of positions.       */
+/* ------------------------------------------------------------------------ */
+static uint64_t orc_mix64(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* n outputs of SplitMix64 from the given initial state. */
+void orc_splitmix64(uint64_t state, int n, uint64_t *out)
+{
+    for (int t = 0; t < n; ++t) {
+        state += 0x9E3779B97F4A7C15ULL;
+        out[t] = orc_mix64(state);
+    }
+}
+
+/* out[i] = pi(i) for 0 <= i < n. */
+int orc_perm(uint64_t seed, uint64_t stream, int64_t n, int64_t *out)
+{
+    if (n < 1 || !out) return -1;
+    uint64_t state = seed ^ orc_mix64(stream);
+    for (int64_t i = 0; i < n; ++i) out[i] = i;
+    for (int64_t i = n - 1; i >= 1; --i) {
+        state += 0x9E3779B97F4A7C15ULL;
+        uint64_t r = orc_mix64(state);
+        int64_t j = (int64_t)(((unsigned __int128)r * (unsigned __int128)(uint64_t)(i + 1)) >> 64);
+        int64_t t = out[i];
+        out[i] = out[j];
+        out[j] = t;
+    }
+    return 0;
+}
+
+/* Surrogate columns: xs[d*ld + i] = x[d*ld + pi(i)] for every X dimension. */
+static void orc_permute_rows(const float *x, int dx, int64_t n, int64_t ld, const int64_t *pi,
+                             float *xs)
+{
+    for (int d = 0; d < dx; ++d)
+        for (int64_t i = 0; i < n; ++i) xs[(int64_t)d * ld + i] = x[(int64_t)d * ld + pi[i]];
+}
+
+/* One estimate plus n_surr surrogates: out[0] = I(X;Y|Z), out[1+s] = the
+ * estimate with X's rows permuted by the permutation keyed (seed, stream = s).
+ * Returns 0 or -1. */
+int orc_cmi_surrogates(const float *x, int dx, const float *y, int dy, const float *z, int dz,
+                       int64_t n, int64_t ld, int k, int n_surr, uint64_t seed, double *out)
+{
+    if (n_surr < 0 || !out) return -1;
+    if (orc_cmi_ksg(x, dx, y, dy, z, dz, n, ld, k, &out[0], NULL, NULL) != 0) return -1;
+    float *xs = (float *)malloc(sizeof(float) * (size_t)dx * (size_t)ld);
+    int64_t *pi = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    int rc = 0;
+    for (int s = 0; s < n_surr && rc == 0; ++s) {
+        orc_perm(seed, (uint64_t)s, n, pi);
+        orc_permute_rows(x, dx, n, ld, pi, xs);
+        rc = orc_cmi_ksg(xs, dx, y, dy, z, dz, n, ld, k, &out[1 + s], NULL, NULL);
+    }
+    free(xs);
+    free(pi);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Greedy parent selection for one target with max-statistic gating         */
+/* (Summary, paragraph 4: parents are added by maximising a CMI criterion;   */
+/* surrogate tests gate each addition and stop the loop; paragraph 3: the    */
+/* test must control errors from testing many sources).  Readings:          */
+/*   - samples t in [L, T), L = max(max_lag, n_past); N = T - L;            */
+/*   - Y[i] = series[target][L+i]; target past = lags 1..n_past of target;  */
+/*   - candidates (p, lag), p in [0,n_proc), lag in [min_lag, max_lag],      */
+/*     without the target-past variables; candidate id                       */
+/*     c = p*(max_lag-min_lag+1) + (lag-min_lag);                           */
+/*   - T_obs = max_c I(X_c;Y|Z), ties to the lowest c;                      */
+/*   - T_s = max_c I(X_c o pi_{step,c,s}; Y|Z), stream = step<<48|c<<24|s;  */
+/*   - p = #{s : T_s >= T_obs} / S; significant iff p < alpha.              */
+/* Pinned by: a strongly coupled VAR recovers its true parents; tiny cases   */
+/* checked against a brute-force gate in the tests.                          */
+/* ------------------------------------------------------------------------ */
+static void orc_gather_lag(const float *series, int64_t T, int p, int lag, int64_t L, float *col)
+{
+    int64_t n = T - L;
+    for (int64_t i = 0; i < n; ++i) col[i] = series[(int64_t)p * T + L + i - lag];
+}
+
+/* Per-step record written by orc_select_target. */
+typedef struct {
+    int32_t cand;     /* candidate id of the step's maximiser (-1: no candidate) */
+    int32_t significant;
+    double stat;      /* T_obs */
+    double pval;
+} orc_step;
+
+/* est_out (nullable): [n_cand_total][1+n_surr] estimates of the FIRST step,
+ * indexed by candidate id (rows of excluded candidates are left untouched). */
+int orc_select_target(const float *series, int n_proc, int64_t T, int target, int n_past,
+                      int min_lag, int max_lag, int k, int n_surr, double alpha, uint64_t seed,
+                      int max_parents, orc_step *steps, int *n_steps, int32_t *parents,
+                      int *n_parents, double *est_out)
+{
+    if (!series || n_proc < 1 || target < 0 || target >= n_proc || n_past < 0 || min_lag < 1 ||
+        max_lag < min_lag || k < 1 || n_surr < 1 || max_parents < 0 || !steps || !n_steps ||
+        !parents || !n_parents)
+        return -1;
+    int n_lags = max_lag - min_lag + 1;
+    int n_cand_total = n_proc * n_lags;
+    int64_t L = max_lag > n_past ? max_lag : n_past;
+    if (T - L < (int64_t)k + 1) return -1;
+    int64_t n = T - L;
+
+    int *alive = (int *)calloc((size_t)n_cand_total, sizeof(int));
+    for (int p = 0; p < n_proc; ++p)
+        for (int lag = min_lag; lag <= max_lag; ++lag)
+            alive[p * n_lags + (lag - min_lag)] = !(p == target && lag <= n_past);
+
+    int dz_max = n_past + max_parents;
+    float *y = (float *)malloc(sizeof(float) * (size_t)n);
+    float *z = (float *)malloc(sizeof(float) * (size_t)n * (size_t)(dz_max > 0 ? dz_max : 1));
+    float *xc = (float *)malloc(sizeof(float) * (size_t)n);
+    float *xs = (float *)malloc(sizeof(float) * (size_t)n);
+    int64_t *pi = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    double *est = (double *)malloc(sizeof(double) * (size_t)n_cand_total * (size_t)(1 + n_surr));
+    orc_gather_lag(series, T, target, 0, L, y);
+    int dz = 0;
+    for (int lag = 1; lag <= n_past; ++lag) orc_gather_lag(series, T, target, lag, L, z + (int64_t)dz++ * n);
+
+    int np = 0, ns = 0, rc = 0;
+    for (int step = 0; step <= max_parents && rc == 0; ++step) {
+        int any = 0;
+        for (int c = 0; c < n_cand_total; ++c) any |= alive[c];
+        if (!any || step == max_parents) break;
+        for (int c = 0; c < n_cand_total && rc == 0; ++c) {
+            if (!alive[c]) continue;
+            int p = c / n_lags, lag = min_lag + c % n_lags;
+            orc_gather_lag(series, T, p, lag, L, xc);
+            double *row = est + (int64_t)c * (1 + n_surr);
+            rc |= orc_cmi_ksg(xc, 1, y, 1, z, dz, n, n, k, &row[0], NULL, NULL);
+            for (int s = 0; s < n_surr && rc == 0; ++s) {
+                uint64_t stream = ((uint64_t)step << 48) | ((uint64_t)c << 24) | (uint64_t)s;
+                orc_perm(seed, stream, n, pi);
+                orc_permute_rows(xc, 1, n, n, pi, xs);
+                rc |= orc_cmi_ksg(xs, 1, y, 1, z, dz, n, n, k, &row[1 + s], NULL, NULL);
+            }
+        }
+        if (rc) break;
+        if (step == 0 && est_out)
+            for (int c = 0; c < n_cand_total; ++c)
+                if (alive[c])
+                    memcpy(est_out + (int64_t)c * (1 + n_surr), est + (int64_t)c * (1 + n_surr),
+                           sizeof(double) * (size_t)(1 + n_surr));
+        /* maximum statistic */
+        int best = -1;
+        double t_obs = -INFINITY;
+        for (int c = 0; c < n_cand_total; ++c)
+            if (alive[c] && est[(int64_t)c * (1 + n_surr)] > t_obs) {
+                t_obs = est[(int64_t)c * (1 + n_surr)];
+                best = c;
+            }
+        int count = 0;
+        for (int s = 0; s < n_surr; ++s) {
+            double t_s = -INFINITY;
+            for (int c = 0; c < n_cand_total; ++c)
+                if (alive[c] && est[(int64_t)c * (1 + n_surr) + 1 + s] > t_s)
+                    t_s = est[(int64_t)c * (1 + n_surr) + 1 + s];
+            if (t_s >= t_obs) ++count;
+        }
+        double pval = (double)count / (double)n_surr;
+        int sig = pval < alpha;
+        steps[ns].cand = best;
+        steps[ns].significant = sig;
+        steps[ns].stat = t_obs;
+        steps[ns].pval = pval;
+        ++ns;
+        if (!sig) break;
+        parents[np++] = best;
+        alive[best] = 0;
+        orc_gather_lag(series, T, best / n_lags, min_lag + best % n_lags, L, z + (int64_t)dz++ * n);
+    }
+    *n_steps = ns;
+    *n_parents = np;
+    free(alive);
+    free(y);
+    free(z);
+    free(xc);
+    free(xs);
+    free(pi);
+    free(est);
+    return rc;
+}
+
+/* Number of threads the OpenMP runtime will use (1 without OpenMP). */
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void orc_set_num_threads(int t)
+{
+#ifdef _OPENMP
+    if (t > 0) omp_set_num_threads(t);
+#else
+    (void)t;
+#endif
+}

@@ -1,0 +1,280 @@
+"""Pins for the CPU oracle: each test ties it to something other than itself.
+
+The IDTxl paper (arXiv 1807.10459) prints no formula or worked example, so the
+pins are a hand-worked example, closed forms (the linear-Gaussian estimator the
+paper lists beside KSG, Summary paragraph on estimators), invariants of the
+max-norm neighbour statistics, special cases that reduce to textbook formulas
+and library routines, and the published output sequence of SplitMix64.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.special
+import scipy.stats
+
+import oracle
+from paper_1807_10459_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def gaussian_closed_form(cov, dx, dy, dz):
+    """I(X;Y|Z) = 1/2 ln[det S_xz det S_yz / (det S_z det S_xyz)] for a Gaussian law."""
+    X = list(range(dx))
+    Y = list(range(dx, dx + dy))
+    Z = list(range(dx + dy, dx + dy + dz))
+
+    def ld(idx):
+        return np.linalg.slogdet(cov[np.ix_(idx, idx)])[1] if idx else 0.0
+
+    return 0.5 * (ld(X + Z) + ld(Y + Z) - ld(Z) - ld(X + Y + Z))
+
+
+def numpy_bruteforce(x, y, z, k):
+    """Independent float32 brute force with numpy broadcasting and np.partition."""
+    x = np.asarray(x, np.float32)
+    y = np.asarray(y, np.float32)
+    n = x.shape[1]
+
+    def cheb(a):
+        if a is None or a.shape[0] == 0:
+            return np.zeros((n, n), np.float32)
+        return np.max(np.abs(a[:, :, None] - a[:, None, :]), axis=0)
+
+    dX, dY, dZ = cheb(x), cheb(y), cheb(None if z is None else np.asarray(z, np.float32))
+    joint = np.maximum(np.maximum(dX, dY), dZ)
+    np.fill_diagonal(joint, np.inf)
+    eps = np.partition(joint, k - 1, axis=1)[:, k - 1]
+    off = ~np.eye(n, dtype=bool)
+    e = eps[:, None]
+    nxz = ((np.maximum(dX, dZ) < e) & off).sum(1)
+    nyz = ((np.maximum(dY, dZ) < e) & off).sum(1)
+    nz = ((dZ < e) & off).sum(1)
+    return eps.astype(np.float32), nxz, nyz, nz
+
+
+# ---------------------------------------------------------------- hand example
+def test_hand_worked_example():
+    g = json.load(open(os.path.join(GOLDEN, "hand_n6_k1.json")))
+    x = np.array([g["x"]], np.float32)
+    y = np.array([g["y"]], np.float32)
+    z = np.array([g["z"]], np.float32)
+    eps, nxz, nyz, nz = oracle.ksg_counts(x, y, z, g["k"])
+    assert eps.tolist() == [float(v) for v in g["eps"]]
+    assert nxz.tolist() == g["nxz"]
+    assert nyz.tolist() == g["nyz"]
+    assert nz.tolist() == g["nz"]
+    cmi = oracle.cmi_ksg(x, y, z, g["k"])
+    assert abs(cmi - g["cmi_numerator"] / g["cmi_denominator"]) < 1e-14
+
+
+# ---------------------------------------------------------------- digamma
+def test_psi_matches_library_digamma():
+    n_max = 100000
+    t = oracle.psi_table(n_max)
+    assert math.isnan(t[0])
+    assert abs(t[1] + np.euler_gamma) < 1e-16
+    n = np.arange(1, n_max + 1, dtype=np.float64)
+    assert np.max(np.abs(t[1:] - scipy.special.digamma(n))) < 1e-13
+
+
+def test_psi_recurrence():
+    t = oracle.psi_table(5000)
+    n = np.arange(1, 5000)
+    assert np.max(np.abs((t[2:] - t[1:-1]) - 1.0 / n)) < 1e-13
+
+
+# ---------------------------------------------------------------- brute force
+@pytest.mark.parametrize("dims,k,n", [((1, 1, 2), 4, 300), ((2, 1, 0), 3, 257), ((1, 2, 3), 1, 200),
+                                      ((2, 2, 5), 6, 180)])
+def test_matches_independent_numpy_bruteforce(dims, k, n):
+    dx, dy, dz = dims
+    g = synth.gaussian_problem(n, dx, dy, dz, seed=77 + n)
+    z = g.z if dz else None
+    eps, nxz, nyz, nz = oracle.ksg_counts(g.x, g.y, z, k)
+    e2, a2, b2, c2 = numpy_bruteforce(g.x, g.y, z, k)
+    assert np.array_equal(eps, e2)
+    assert np.array_equal(nxz, a2)
+    assert np.array_equal(nyz, b2)
+    assert np.array_equal(nz, c2)
+
+
+def test_bruteforce_with_ties_and_duplicates():
+    rng = np.random.default_rng(5)
+    # values on a coarse grid: many equal distances and duplicate samples
+    x = rng.integers(0, 4, (1, 150)).astype(np.float32)
+    y = rng.integers(0, 4, (1, 150)).astype(np.float32)
+    z = rng.integers(0, 3, (2, 150)).astype(np.float32)
+    for k in (1, 2, 4, 8):
+        got = oracle.ksg_counts(x, y, z, k)
+        ref = numpy_bruteforce(x, y, z, k)
+        for a, b in zip(got, ref):
+            assert np.array_equal(a, b)
+
+
+# ---------------------------------------------------------------- special case dz = 0
+def test_dz0_reduces_to_ksg_mutual_information():
+    g = synth.gaussian_problem(2000, 1, 1, 0, seed=11)
+    k = 4
+    eps, nx, ny, nz = oracle.ksg_counts(g.x, g.y, None, k)
+    n = g.x.shape[1]
+    assert np.all(eps > 0)
+    assert np.all(nz == n - 1)
+    mi = scipy.special.digamma(k) + scipy.special.digamma(n) - np.mean(
+        scipy.special.digamma(nx + 1.0) + scipy.special.digamma(ny + 1.0))
+    assert abs(oracle.cmi_ksg(g.x, g.y, None, k) - mi) < 1e-12
+    # bivariate Gaussian MI closed form -1/2 ln(1 - rho^2)
+    c = g.cov
+    rho = c[0, 1] / math.sqrt(c[0, 0] * c[1, 1])
+    assert abs(mi - (-0.5 * math.log(1 - rho * rho))) < 0.06
+
+
+# ---------------------------------------------------------------- closed forms
+def test_gaussian_closed_form_n1e4_mean_of_10():
+    cov = synth.gaussian_problem(1000, 1, 1, 2).cov
+    truth = gaussian_closed_form(cov, 1, 1, 2)
+    vals = [oracle.cmi_ksg(*(lambda g: (g.x, g.y, g.z))(
+        synth.gaussian_problem(10000, 1, 1, 2, seed=1000 + s, cov=cov)), 4) for s in range(10)]
+    assert abs(np.mean(vals) - truth) < 0.02
+
+
+def test_gaussian_closed_form_n1e3_single():
+    g = synth.gaussian_problem(1000, 1, 1, 2)
+    truth = gaussian_closed_form(g.cov, 1, 1, 2)
+    assert abs(oracle.cmi_ksg(g.x, g.y, g.z, 4) - truth) < 0.06
+
+
+def test_independent_shuffle_is_near_zero():
+    cov = synth.gaussian_problem(1000, 1, 1, 2).cov
+    vals = []
+    for s in range(10):
+        g = synth.gaussian_problem(10000, 1, 1, 2, seed=3000 + s, cov=cov)
+        xs = g.x[:, np.random.default_rng(s).permutation(10000)]
+        vals.append(oracle.cmi_ksg(xs, g.y, g.z, 4))
+    assert abs(np.mean(vals)) < 0.01
+
+
+# ---------------------------------------------------------------- invariants
+def test_xy_swap_is_bit_identical():
+    g = synth.gaussian_problem(700, 1, 1, 2, seed=3)
+    a = oracle.ksg_counts(g.x, g.y, g.z, 4)
+    b = oracle.ksg_counts(g.y, g.x, g.z, 4)
+    assert np.array_equal(a[0], b[0])
+    assert np.array_equal(a[1], b[2]) and np.array_equal(a[2], b[1])
+    assert np.array_equal(a[3], b[3])
+    assert oracle.cmi_ksg(g.x, g.y, g.z, 4) == oracle.cmi_ksg(g.y, g.x, g.z, 4)
+
+
+def test_sample_reordering_permutes_counts():
+    g = synth.gaussian_problem(600, 2, 1, 2, seed=4)
+    perm = np.random.default_rng(9).permutation(600)
+    a = oracle.ksg_counts(g.x, g.y, g.z, 4)
+    b = oracle.ksg_counts(g.x[:, perm], g.y[:, perm], g.z[:, perm], 4)
+    for u, v in zip(a, b):
+        assert np.array_equal(u[perm], v)
+
+
+@pytest.mark.parametrize("m", [-3, 5])
+def test_power_of_two_scaling_is_bit_identical(m):
+    g = synth.gaussian_problem(500, 1, 1, 3, seed=6)
+    s = np.float32(2.0 ** m)
+    a = oracle.ksg_counts(g.x, g.y, g.z, 4)
+    b = oracle.ksg_counts(g.x * s, g.y * s, g.z * s, 4)
+    assert np.array_equal(a[0] * s, b[0])
+    for u, v in zip(a[1:], b[1:]):
+        assert np.array_equal(u, v)
+
+
+def test_count_nesting_and_lower_bounds():
+    g = synth.gaussian_problem(800, 1, 1, 2, seed=8)
+    eps, nxz, nyz, nz = oracle.ksg_counts(g.x, g.y, g.z, 4)
+    assert np.all(nz >= nxz) and np.all(nz >= nyz)
+    # continuous data: no ties at eps, so at least k-1 neighbours lie strictly inside
+    assert np.all(nxz >= 3) and np.all(nyz >= 3)
+
+
+# ---------------------------------------------------------------- permutations
+def test_splitmix64_published_sequence():
+    g = json.load(open(os.path.join(GOLDEN, "splitmix64_1234567.json")))
+    out = oracle.splitmix64(g["state"], len(g["outputs"]))
+    assert [int(v) for v in out] == [int(s) for s in g["outputs"]]
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 16, 17, 255, 1000, 9995, 65537])
+def test_permutation_is_a_bijection(n):
+    for stream in (0, 1, 12345, (3 << 48) | (7 << 24) | 9):
+        p = oracle.perm(20181027, stream, n)
+        assert np.array_equal(np.sort(p), np.arange(n))
+
+
+def test_permutation_positions_are_uniform():
+    n, reps = 10, 20000
+    hist = np.zeros((n, n))
+    for s in range(reps):
+        p = oracle.perm(99, s, n)
+        hist[np.arange(n), p] += 1
+    expected = reps / n
+    chi2 = ((hist - expected) ** 2 / expected).sum(axis=1)
+    # each row: chi-square with n-1 = 9 dof; 0.999 quantile is 27.9
+    assert np.all(chi2 < 27.9 * 1.3)
+    assert scipy.stats.chi2.sf(chi2.sum(), n * (n - 1)) > 1e-3
+
+
+def test_permutations_differ_by_stream_and_seed():
+    a = oracle.perm(1, 0, 1000)
+    b = oracle.perm(1, 1, 1000)
+    c = oracle.perm(2, 0, 1000)
+    assert not np.array_equal(a, b) and not np.array_equal(a, c)
+
+
+# ---------------------------------------------------------------- surrogates
+def test_surrogates_permute_rows_of_x():
+    g = synth.gaussian_problem(400, 2, 1, 1, seed=12)
+    out = oracle.cmi_surrogates(g.x, g.y, g.z, 4, 5, 777)
+    assert out[0] == oracle.cmi_ksg(g.x, g.y, g.z, 4)
+    for s in range(5):
+        p = oracle.perm(777, s, 400)
+        assert out[1 + s] == oracle.cmi_ksg(g.x[:, p], g.y, g.z, 4)
+
+
+def test_surrogate_distribution_is_centred_below_signal():
+    g = synth.gaussian_problem(1000, 1, 1, 2)
+    out = oracle.cmi_surrogates(g.x, g.y, g.z, 4, 40, 5)
+    assert out[0] > np.max(out[1:])
+    assert abs(np.mean(out[1:])) < 0.03
+
+
+# ---------------------------------------------------------------- greedy selection
+def test_greedy_recovers_strong_parents():
+    net = synth.var_network(n_nodes=5, order=3, T=1500, density=0.35, weight=0.9, seed=31)
+    target = 0
+    edges = {(p, lag) for (p, q, lag) in net.edges if q == target}
+    truth = {(p, lag) for (p, lag) in edges if abs(net.coef[lag - 1, target, p]) > 0.2}
+    assert truth, "generator seed must give the target at least one strong parent"
+    res = oracle.select_target(net.series, target, n_past=1, min_lag=1, max_lag=3, k=4,
+                               n_surr=20, alpha=0.05, seed=123, max_parents=6)
+    got = {(c // 3, 1 + c % 3) for c in res["parents"]}
+    assert truth <= got
+    assert len(got - edges) <= 1
+    last = res["steps"][-1]
+    assert not last[1] or len(res["parents"]) == 6
+
+
+def test_greedy_first_step_gate_from_estimates():
+    net = synth.var_network(n_nodes=4, order=2, T=600, density=0.5, weight=0.7, seed=8)
+    S = 20
+    res = oracle.select_target(net.series, 1, n_past=1, min_lag=1, max_lag=2, k=3, n_surr=S,
+                               alpha=0.05, seed=9, max_parents=1, want_first_step=True)
+    est = res["first_step"]
+    alive = ~np.isnan(est[:, 0])
+    assert alive.sum() == 4 * 2 - 1       # the target's own lag 1 is in Z
+    c_best = int(np.flatnonzero(alive)[np.argmax(est[alive, 0])])
+    t_obs = est[c_best, 0]
+    t_s = np.max(est[alive, 1:], axis=0)
+    cand, sig, stat, pval = res["steps"][0]
+    assert cand == c_best and stat == t_obs
+    assert pval == np.count_nonzero(t_s >= t_obs) / S
+    assert sig == (pval < 0.05)
