@@ -1,0 +1,196 @@
+/*
+ * idtx.h -- C ABI of the GB300 KSG conditional-mutual-information library.
+ *
+ * The library computes the hot path of greedy multivariate transfer-entropy
+ * inference as described in the IDTxl paper (arXiv 1807.10459):
+ *   - the Kraskov-Stoegbauer-Grassberger (KSG) nonlinear estimator of
+ *     conditional mutual information (Summary, paragraph on estimators; the
+ *     paper names the estimator and its GPU implementation but prints no
+ *     formula -- the conditional form of KSG algorithm 1 is used);
+ *   - surrogate null distributions that gate parent selection and stop it
+ *     (Summary, paragraph on the greedy approach);
+ *   - the greedy parent-set loop that maximises a CMI criterion over
+ *     candidate (source, lag) variables (same paragraph).
+ *
+ * Estimator, for samples i = 0..N-1 of the joint variable (X, Y, Z):
+ *   eps_i   = k-th smallest over j != i of max(|X_i-X_j|, |Y_i-Y_j|, |Z_i-Z_j|)
+ *             (max norm over all dimensions, fp32);
+ *   n_xz,i  = #{ j != i : max-norm distance in (X,Z) < eps_i }, likewise n_yz,i
+ *             and n_z,i (dz == 0: the Z distance is 0);
+ *   I(X;Y|Z) = psi(k) + (1/N) sum_i [psi(n_z,i+1) - psi(n_xz,i+1) - psi(n_yz,i+1)]
+ *             in nats (digamma and sums in fp64).
+ * Surrogate s of an estimate replaces X by its rows permuted by pi_s, the
+ * Fisher-Yates shuffle of [0,N) driven by SplitMix64 started from the state
+ * seed ^ mix64(stream) (mix64 = SplitMix64's output mixer): X_s[i] = X[pi_s(i)].
+ *
+ * Conventions for every call:
+ *   - Return value: IDTX_OK or an error code; idtx_last_error() gives a
+ *     message for the calling thread's last failure.
+ *   - Column data: dimension d of a variable at sample t is p[d*ld + t]
+ *     (fp32, ld >= N).  Input pointers may be device pointers or host
+ *     pointers (pageable or pinned); host inputs are copied in by the
+ *     library.  Output pointers may likewise be host or device memory.
+ *     The caller owns every pointer it passes; the library never frees them.
+ *   - Inputs must be finite: NaN or Inf anywhere in the used samples gives
+ *     IDTX_EINVAL and no outputs.
+ *   - Work is enqueued on `stream` (a cudaStream_t, NULL = legacy default
+ *     stream) on the context's device; every call synchronises that stream
+ *     before it returns, so outputs are complete on return.
+ *   - A context is not re-entrant: one call at a time per context.  The
+ *     library allocates its own scratch (grown on demand) and frees it in
+ *     idtx_ctx_destroy.
+ *   - Device waits inside kernels are bounded (settings.timeout_ms); a wait
+ *     that runs out returns IDTX_ETIMEOUT and leaves the context usable.
+ */
+#ifndef IDTX_H
+#define IDTX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    IDTX_OK = 0,
+    IDTX_EINVAL = 1,    /* bad argument, unsupported shape or non-finite input */
+    IDTX_ENOMEM = 2,    /* device or host allocation failed */
+    IDTX_ECUDA = 3,     /* a CUDA runtime call failed */
+    IDTX_ETIMEOUT = 4,  /* a bounded device wait ran out */
+    IDTX_EINTERNAL = 5  /* an internal consistency check failed */
+};
+
+/* Limits of the current kernels (larger shapes return IDTX_EINVAL). */
+#define IDTX_MAX_DX 4
+#define IDTX_MAX_DY 4
+#define IDTX_MAX_DZ 16
+#define IDTX_MAX_K 15
+#define IDTX_MAX_N 2000000
+
+typedef struct idtx_ctx idtx_ctx;
+
+/* Estimation settings.  k: neighbours (1 <= k <= min(N-1, IDTX_MAX_K));
+ * n_surr: surrogates per estimate (>= 0; the greedy calls need >= 1);
+ * seed: surrogate seed; alpha: gate level of the greedy calls (0 < alpha < 1);
+ * timeout_ms: bound on any device wait (<= 0 selects 2000 ms). */
+typedef struct {
+    int32_t k;
+    int32_t n_surr;
+    uint64_t seed;
+    double alpha;
+    int32_t timeout_ms;
+    int32_t reserved;
+} idtx_settings;
+
+/* Create a context bound to CUDA device `device`.  *ctx receives the handle. */
+int idtx_ctx_create(idtx_ctx **ctx, int device);
+
+/* Free the context and all its scratch memory.  NULL is accepted. */
+int idtx_ctx_destroy(idtx_ctx *ctx);
+
+/* Message for the calling thread's last error ("" if none).  The pointer is
+ * valid until the thread's next call into the library. */
+const char *idtx_last_error(void);
+
+/* Library ABI version (major * 100 + minor). */
+int idtx_version(void);
+
+/* Counters of a context, for measurement (no counterpart in the paper: they
+ * report what the library did).  kernel_launches counts every kernel the
+ * library enqueued; the fused_* fields cover the fused estimator kernel
+ * only: its launches, its device time (CUDA events recorded on the caller's
+ * stream around each launch, only while profiling is enabled), and its
+ * algorithmic lane operations: for every (query, reference sample, group of
+ * jobs sharing Y and Z), 2(dy+dz')+1 operations in the neighbour pass and
+ * 2dz'+1 in the count pass (one subtraction and one max-abs per dimension
+ * plus the bound compare; dz' = max(dz, 1)). */
+typedef struct {
+    int64_t kernel_launches;
+    int64_t fused_launches;
+    double fused_ms;
+    double fused_lane_ops;
+} idtx_stats;
+
+/* Enable (1) or disable (0) event timing of the fused kernel. */
+int idtx_ctx_set_profiling(idtx_ctx *ctx, int enable);
+
+/* Read the counters accumulated since creation or the last reset. */
+int idtx_ctx_get_stats(idtx_ctx *ctx, idtx_stats *out);
+
+/* Zero the counters. */
+int idtx_ctx_reset_stats(idtx_ctx *ctx);
+
+/* One KSG estimate of I(X;Y|Z) plus settings->n_surr surrogates.
+ * (KSG estimator: Summary, paragraph on estimators; surrogates: paragraph on
+ * the greedy approach.)
+ *   x [dx][ld], y [dy][ld], z [dz][ld] (z may be NULL when dz == 0), fp32.
+ *   1 <= dx <= IDTX_MAX_DX, 1 <= dy <= IDTX_MAX_DY, 0 <= dz <= IDTX_MAX_DZ,
+ *   k+1 <= n <= IDTX_MAX_N, ld >= n.
+ *   cmi_out [1+n_surr] fp64: cmi_out[0] is the estimate, cmi_out[1+s] the
+ *     estimate for surrogate s (permutation stream s, seed settings->seed).
+ *   eps_out (nullable) [1+n_surr][n] fp32: eps_i of every estimate.
+ *   counts_out (nullable) [1+n_surr][3][n] int32: n_xz, n_yz, n_z of every
+ *     estimate. */
+int idtx_cmi_ksg(idtx_ctx *ctx, const float *x, int dx, const float *y, int dy, const float *z,
+                 int dz, int64_t n, int64_t ld, const idtx_settings *settings, double *cmi_out,
+                 float *eps_out, int32_t *counts_out, void *stream);
+
+/* One problem of a batch: its own columns, shape, surrogate count and seed. */
+typedef struct {
+    const float *x, *y, *z;
+    int32_t dx, dy, dz;
+    int32_t n_surr;
+    int64_t n, ld;
+    uint64_t seed;
+} idtx_problem;
+
+/* Many independent problems of uneven N and dimensions, each with its own
+ * surrogates, in one pass over the GPU (Summary, paragraph on estimators:
+ * parallel computing engines).  All problems use neighbour count k.
+ *   out: concatenated [sum_p (1 + probs[p].n_surr)] fp64, problem by problem,
+ *   each laid out as in idtx_cmi_ksg. */
+int idtx_cmi_batch(idtx_ctx *ctx, const idtx_problem *probs, int n_probs, int k, double *out,
+                   void *stream);
+
+/* Result of one greedy step. */
+typedef struct {
+    int32_t cand;        /* candidate id of the maximiser (-1 if none) */
+    int32_t significant; /* 1 if p < alpha */
+    double stat;         /* T_obs = max over candidates of I(X_c;Y|Z) */
+    double pval;         /* #{s : max_c I(X_c o pi_{c,s};Y|Z) >= T_obs} / n_surr */
+} idtx_step;
+
+/* One step of the greedy parent selection for one target (Summary, paragraph
+ * on the greedy approach).  series [n_proc][T] fp32.  Samples t in [L, T),
+ * L = max(max_lag, n_past), N = T - L.  Y_t = series[target][t]; Z = the
+ * target's own lags 1..n_past followed by the already selected candidates
+ * `selected[0..n_selected)`.  Candidates are (p, lag), p in [0, n_proc),
+ * lag in [min_lag, max_lag], with id c = p*(max_lag-min_lag+1) + lag-min_lag;
+ * the target's lags <= n_past and the selected ids are excluded.  Every
+ * candidate is estimated with settings->n_surr surrogates keyed by stream
+ * (step_index << 48) | (c << 24) | s.  T_obs is the largest estimate (ties
+ * to the lowest id), T_s the largest surrogate-s estimate over candidates;
+ * significant iff #{s : T_s >= T_obs} / n_surr < alpha.
+ *   result: the step's outcome.
+ *   est_out (nullable): [n_proc*(max_lag-min_lag+1)][1+n_surr] fp64, rows of
+ *   evaluated candidates only (others untouched). */
+int idtx_mte_step(idtx_ctx *ctx, const float *series, int n_proc, int64_t T, int target,
+                  int n_past, int min_lag, int max_lag, const int32_t *selected, int n_selected,
+                  int step_index, const idtx_settings *settings, idtx_step *result,
+                  double *est_out, void *stream);
+
+/* The whole greedy loop for one target: repeats idtx_mte_step (step_index =
+ * 0, 1, ...) adding the maximiser while the step is significant, until no
+ * candidate is left or max_parents are selected.
+ *   parents_out [max_parents] candidate ids in selection order, *n_parents;
+ *   steps_out [max_parents+1] every executed step, *n_steps. */
+int idtx_mte_select_target(idtx_ctx *ctx, const float *series, int n_proc, int64_t T, int target,
+                           int n_past, int min_lag, int max_lag, const idtx_settings *settings,
+                           int max_parents, int32_t *parents_out, int *n_parents,
+                           idtx_step *steps_out, int *n_steps, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IDTX_H */

@@ -1,0 +1,315 @@
+"""GB300-native KSG conditional mutual information and greedy mTE parent selection.
+
+Thin Python binding over the C ABI of ``libidtx.so`` (declared in
+``include/idtx.h``).  It only marshals arguments: every step of the
+estimator runs in the library's CUDA kernels.  Array arguments may be torch
+tensors (CUDA or CPU) or numpy arrays; CUDA tensors are passed as device
+pointers, everything else as host pointers that the library copies in.
+
+The library is loaded on first use; if it has not been built, or no CUDA
+device is present, the call raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+__all__ = ["IdtxError", "Settings", "Context", "load", "cmi_ksg", "cmi_batch", "mte_step",
+           "mte_select_target", "library_path"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libidtx.so")
+_lock = threading.Lock()
+_lib = None
+_default_ctx = {}
+
+IDTX_OK, IDTX_EINVAL, IDTX_ENOMEM, IDTX_ECUDA, IDTX_ETIMEOUT, IDTX_EINTERNAL = range(6)
+_ERR_NAMES = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EINTERNAL"}
+
+
+class IdtxError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"idtx error {_ERR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Settings(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("n_surr", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("alpha", ctypes.c_double), ("timeout_ms", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("z", ctypes.c_void_p),
+                ("dx", ctypes.c_int32), ("dy", ctypes.c_int32), ("dz", ctypes.c_int32),
+                ("n_surr", ctypes.c_int32), ("n", ctypes.c_int64), ("ld", ctypes.c_int64),
+                ("seed", ctypes.c_uint64)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_int64), ("fused_launches", ctypes.c_int64),
+                ("fused_ms", ctypes.c_double), ("fused_lane_ops", ctypes.c_double)]
+
+
+class Step(ctypes.Structure):
+    _fields_ = [("cand", ctypes.c_int32), ("significant", ctypes.c_int32),
+                ("stat", ctypes.c_double), ("pval", ctypes.c_double)]
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load():
+    """Load ``libidtx.so`` (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(f"{_LIB_PATH} is missing: build it first "
+                               "(python -c 'import __graft_entry__ as g; g.build()')")
+        lib = ctypes.CDLL(_LIB_PATH)
+        vp, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64
+        lib.idtx_ctx_create.argtypes = [ctypes.POINTER(vp), i32]
+        lib.idtx_ctx_destroy.argtypes = [vp]
+        lib.idtx_last_error.restype = ctypes.c_char_p
+        lib.idtx_cmi_ksg.argtypes = [vp, vp, i32, vp, i32, vp, i32, i64, i64,
+                                     ctypes.POINTER(Settings), vp, vp, vp, vp]
+        lib.idtx_cmi_batch.argtypes = [vp, ctypes.POINTER(Problem), i32, i32, vp, vp]
+        lib.idtx_mte_step.argtypes = [vp, vp, i32, i64, i32, i32, i32, i32, vp, i32, i32,
+                                      ctypes.POINTER(Settings), ctypes.POINTER(Step), vp, vp]
+        lib.idtx_mte_select_target.argtypes = [vp, vp, i32, i64, i32, i32, i32, i32,
+                                               ctypes.POINTER(Settings), i32, vp,
+                                               ctypes.POINTER(i32), ctypes.POINTER(Step),
+                                               ctypes.POINTER(i32), vp]
+        lib.idtx_ctx_set_profiling.argtypes = [vp, i32]
+        lib.idtx_ctx_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+        lib.idtx_ctx_reset_stats.argtypes = [vp]
+        for name in ("idtx_ctx_set_profiling", "idtx_ctx_get_stats", "idtx_ctx_reset_stats",
+                     "idtx_ctx_create", "idtx_ctx_destroy", "idtx_cmi_ksg", "idtx_cmi_batch",
+                     "idtx_mte_step", "idtx_mte_select_target", "idtx_version"):
+            getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _check(rc):
+    if rc != IDTX_OK:
+        msg = load().idtx_last_error()
+        raise IdtxError(rc, msg.decode() if msg else "")
+
+
+class Context:
+    """A library context bound to one CUDA device (owns the scratch memory)."""
+
+    def __init__(self, device: int = 0):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.idtx_ctx_create(ctypes.byref(h), int(device)))
+        self.handle = h
+        self.device = device
+
+    def set_profiling(self, on: bool = True):
+        """Time the fused estimator kernel with CUDA events (see stats())."""
+        _check(load().idtx_ctx_set_profiling(self.handle, 1 if on else 0))
+
+    def stats(self) -> dict:
+        st = Stats()
+        _check(load().idtx_ctx_get_stats(self.handle, ctypes.byref(st)))
+        return dict(kernel_launches=st.kernel_launches, fused_launches=st.fused_launches,
+                    fused_ms=st.fused_ms, fused_lane_ops=st.fused_lane_ops)
+
+    def reset_stats(self):
+        _check(load().idtx_ctx_reset_stats(self.handle))
+
+    def close(self):
+        if self.handle:
+            load().idtx_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def default_context(device: int = 0) -> Context:
+    with _lock:
+        ctx = _default_ctx.get(device)
+    if ctx is None:
+        ctx = Context(device)
+        with _lock:
+            _default_ctx[device] = ctx
+    return ctx
+
+
+# ------------------------------------------------------------------ marshalling
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+class _Arr:
+    """A [d][N] float32 (or other dtype) view with a raw pointer kept alive."""
+
+    def __init__(self, a, dtype=np.float32, name="array"):
+        if a is None:
+            self.obj, self.ptr, self.d, self.n = None, None, 0, 0
+            return
+        if _is_torch(a):
+            import torch
+            t = a
+            tdt = {np.float32: torch.float32, np.float64: torch.float64,
+                   np.int32: torch.int32}[dtype]
+            if t.dtype != tdt:
+                raise TypeError(f"{name} must be {tdt}")
+            if t.dim() == 1:
+                t = t.unsqueeze(0)
+            if not t.is_contiguous():
+                t = t.contiguous()
+            self.obj = t
+            self.ptr = t.data_ptr()
+            self.d, self.n = int(t.shape[0]), int(t.shape[1])
+        else:
+            arr = np.asarray(a)
+            if arr.dtype != dtype:
+                arr = arr.astype(dtype)
+            if arr.ndim == 1:
+                arr = arr[None, :]
+            arr = np.ascontiguousarray(arr)
+            self.obj = arr
+            self.ptr = arr.ctypes.data
+            self.d, self.n = int(arr.shape[0]), int(arr.shape[1])
+
+
+def _stream_for(*arrays):
+    for a in arrays:
+        if a is not None and _is_torch(a) and a.is_cuda:
+            import torch
+            return ctypes.c_void_p(torch.cuda.current_stream(a.device).cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+def _out(shape, dtype, like):
+    """Output buffer: a CUDA tensor if `like` is a CUDA tensor, else numpy."""
+    if like is not None and _is_torch(like) and like.is_cuda:
+        import torch
+        tdt = {np.float32: torch.float32, np.float64: torch.float64, np.int32: torch.int32}[dtype]
+        t = torch.empty(shape, dtype=tdt, device=like.device)
+        return t, t.data_ptr()
+    a = np.empty(shape, dtype)
+    return a, a.ctypes.data
+
+
+def _settings(k, n_surr, seed, alpha=0.05, timeout_ms=0):
+    return Settings(int(k), int(n_surr), ctypes.c_uint64(int(seed) & (2**64 - 1)).value,
+                    float(alpha), int(timeout_ms), 0)
+
+
+def cmi_ksg(x, y, z=None, k: int = 4, n_surr: int = 0, seed: int = 0, want_eps: bool = False,
+            want_counts: bool = False, timeout_ms: int = 0, ctx: Context | None = None):
+    """One KSG estimate of I(X;Y|Z) plus ``n_surr`` surrogates.
+
+    x, y, z: [d][N] float32 (1-D means d = 1; z may be None).  Returns the
+    [1+n_surr] fp64 estimates, and (if asked) eps [1+n_surr][N] and counts
+    [1+n_surr][3][N] (n_xz, n_yz, n_z), as CUDA tensors when x is one, else numpy.
+    """
+    ax, ay, az = _Arr(x, name="x"), _Arr(y, name="y"), _Arr(z, name="z")
+    n = ax.n
+    if ay.n != n or (az.d and az.n != n):
+        raise ValueError("x, y, z must have the same number of samples")
+    dev = x.device.index if (_is_torch(x) and x.is_cuda) else 0
+    ctx = ctx or default_context(dev or 0)
+    cmi, p_cmi = _out((1 + n_surr,), np.float64, x)
+    eps, p_eps = _out((1 + n_surr, n), np.float32, x) if want_eps else (None, None)
+    cnt, p_cnt = _out((1 + n_surr, 3, n), np.int32, x) if want_counts else (None, None)
+    s = _settings(k, n_surr, seed, timeout_ms=timeout_ms)
+    _check(load().idtx_cmi_ksg(ctx.handle, ax.ptr, ax.d, ay.ptr, ay.d, az.ptr, az.d, n, n,
+                               ctypes.byref(s), p_cmi, p_eps, p_cnt, _stream_for(x, y, z)))
+    if want_eps or want_counts:
+        out = [cmi]
+        if want_eps:
+            out.append(eps)
+        if want_counts:
+            out.append(cnt)
+        return tuple(out)
+    return cmi
+
+
+def cmi_batch(problems, k: int = 4, ctx: Context | None = None):
+    """Many uneven problems at once.  ``problems``: iterable of objects or dicts
+    with x, y, z ([d][N] arrays), n_surr, seed.  Returns a list of [1+n_surr]
+    fp64 arrays, one per problem."""
+    probs = list(problems)
+    keep = []
+    arr = (Problem * len(probs))()
+    like = None
+    counts = []
+    for i, p in enumerate(probs):
+        get = (lambda key: p[key]) if isinstance(p, dict) else (lambda key: getattr(p, key))
+        ax, ay, az = _Arr(get("x"), name="x"), _Arr(get("y"), name="y"), _Arr(get("z"), name="z")
+        keep += [ax, ay, az]
+        like = like if like is not None else get("x")
+        ns = int(get("n_surr"))
+        arr[i] = Problem(ax.ptr, ay.ptr, az.ptr if az.d else None, ax.d, ay.d, az.d, ns, ax.n,
+                         ax.n, ctypes.c_uint64(int(get("seed")) & (2**64 - 1)).value)
+        counts.append(1 + ns)
+    dev = like.device.index if (_is_torch(like) and like.is_cuda) else 0
+    ctx = ctx or default_context(dev or 0)
+    out, p_out = _out((sum(counts),), np.float64, like)
+    _check(load().idtx_cmi_batch(ctx.handle, arr, len(probs), int(k), p_out, _stream_for(like)))
+    res, o = [], 0
+    for c in counts:
+        res.append(out[o:o + c])
+        o += c
+    return res
+
+
+def mte_step(series, target: int, n_past: int, min_lag: int, max_lag: int, selected=(),
+             step_index: int = 0, k: int = 4, n_surr: int = 200, alpha: float = 0.05,
+             seed: int = 0, want_estimates: bool = False, timeout_ms: int = 0,
+             ctx: Context | None = None):
+    """One greedy selection step; returns (cand, significant, stat, pval) and,
+    if asked, the [n_proc*n_lags][1+n_surr] estimates (NaN rows: not evaluated)."""
+    a = _Arr(series, name="series")
+    dev = series.device.index if (_is_torch(series) and series.is_cuda) else 0
+    ctx = ctx or default_context(dev or 0)
+    sel = np.ascontiguousarray(np.asarray(list(selected), np.int32))
+    s = _settings(k, n_surr, seed, alpha, timeout_ms)
+    step = Step()
+    est, p_est = (None, None)
+    if want_estimates:
+        est = np.full((a.d * (max_lag - min_lag + 1), 1 + n_surr), np.nan, np.float64)
+        p_est = est.ctypes.data
+    _check(load().idtx_mte_step(ctx.handle, a.ptr, a.d, a.n, int(target), int(n_past),
+                                int(min_lag), int(max_lag),
+                                sel.ctypes.data if sel.size else None, int(sel.size),
+                                int(step_index), ctypes.byref(s), ctypes.byref(step), p_est,
+                                _stream_for(series)))
+    res = (int(step.cand), bool(step.significant), float(step.stat), float(step.pval))
+    return (res, est) if want_estimates else res
+
+
+def mte_select_target(series, target: int, n_past: int, min_lag: int, max_lag: int, k: int = 4,
+                      n_surr: int = 200, alpha: float = 0.05, seed: int = 0,
+                      max_parents: int = 10, timeout_ms: int = 0, ctx: Context | None = None):
+    """The greedy loop for one target: dict(parents=[ids], steps=[(cand, sig, stat, p)])."""
+    a = _Arr(series, name="series")
+    dev = series.device.index if (_is_torch(series) and series.is_cuda) else 0
+    ctx = ctx or default_context(dev or 0)
+    s = _settings(k, n_surr, seed, alpha, timeout_ms)
+    parents = np.zeros(max(1, max_parents), np.int32)
+    steps = (Step * (max_parents + 1))()
+    n_par, n_steps = ctypes.c_int(), ctypes.c_int()
+    _check(load().idtx_mte_select_target(ctx.handle, a.ptr, a.d, a.n, int(target), int(n_past),
+                                         int(min_lag), int(max_lag), ctypes.byref(s),
+                                         int(max_parents), parents.ctypes.data,
+                                         ctypes.byref(n_par), steps, ctypes.byref(n_steps),
+                                         _stream_for(series)))
+    return dict(parents=[int(p) for p in parents[:n_par.value]],
+                steps=[(int(steps[i].cand), bool(steps[i].significant), float(steps[i].stat),
+                        float(steps[i].pval)) for i in range(n_steps.value)])

@@ -1,0 +1,989 @@
+// runtime.cu -- host runtime of the KSG library: contexts, scratch memory,
+// argument checks, the small kernels around the fused estimator, and the C ABI
+// declared in include/idtx.h.
+//
+// Per call, one "group" is a set of estimates ("jobs") that share Y and Z:
+// the original estimate and its surrogates (idtx_cmi_ksg), one batch problem
+// (idtx_cmi_batch), or every candidate of a greedy step with its surrogates
+// (idtx_mte_step).  A group runs as
+//   pack_shared  : Y/Z columns -> sh [n_pad][dsp] (row per sample, +inf pads)
+//   iota + fisher_yates : surrogate permutations, one thread per permutation
+//   gather_x     : X values of every job, permuted, -> xi [groups][n_pad][GB*DX]
+//   ksg_fused    : kNN + counts + digamma partial sums (ksg_kernel.cuh)
+//   finalize     : psi(k) + sum / N per job, fixed order
+// and the greedy step adds the max-statistic gate kernel.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "idtx.h"
+#include "ksg_common.cuh"
+
+namespace idtx {
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string t_err;
+
+static int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    t_err = buf;
+    return code;
+}
+
+#define IDTX_CUDA(call)                                                                   \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(e_ == cudaErrorMemoryAllocation ? IDTX_ENOMEM : IDTX_ECUDA,        \
+                        "%s failed: %s", #call, cudaGetErrorString(e_));                  \
+    } while (0)
+
+#define IDTX_TRY(expr)            \
+    do {                          \
+        int rc_ = (expr);         \
+        if (rc_ != IDTX_OK) return rc_; \
+    } while (0)
+
+// ------------------------------------------------------------------ device helpers
+struct Col {  // value of a column at sample i: base[off + i]
+    const float *base;
+    int64_t off;
+};
+
+struct Job {  // one estimate: X source and permutation slot (-1: identity)
+    int32_t src;
+    int32_t slot;
+};
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z)
+{
+    // SplitMix64 output function (Steele, Lea & Flood 2014).
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// psi(n) for n in [0, n_max]: psi(0) is NaN; n < 16 by the finite harmonic sum
+// psi(n) = -gamma + sum_{m<n} 1/m; n >= 16 by the asymptotic expansion
+// ln n - 1/(2n) - sum_j B_2j / (2j n^2j) (Abramowitz & Stegun 6.3.18) through
+// j = 5, whose first omitted term is below 1e-16 there.
+__global__ void k_psi_table(double *psi, int64_t n_max)
+{
+    const double kEulerGamma = 0.57721566490153286060651209008240243;
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n <= n_max;
+         n += (int64_t)gridDim.x * blockDim.x) {
+        double v;
+        if (n == 0) {
+            v = nan("");
+        } else if (n < 16) {
+            v = -kEulerGamma;
+            for (int64_t m = 1; m < n; ++m) v += 1.0 / (double)m;
+        } else {
+            const double x = (double)n, r = 1.0 / x, r2 = r * r;
+            v = log(x) - 0.5 * r -
+                r2 * (1.0 / 12.0 -
+                      r2 * (1.0 / 120.0 - r2 * (1.0 / 252.0 - r2 * (1.0 / 240.0 - r2 / 132.0))));
+        }
+        psi[n] = v;
+    }
+}
+
+// sh[j][d]: d < dzb -> z (0 beyond dz), then dyb y columns (0 beyond dy),
+// then 0 up to dsp.  Rows j >= n are +inf in the dzb + dyb used columns.
+__global__ void k_pack_shared(const Col *zc, int dz, int dzb, const Col *yc, int dy, int dyb,
+                              int dsp, int64_t n, int64_t n_pad, float *sh, int *err)
+{
+    const int64_t total = n_pad * dsp;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = idx / dsp;
+        const int d = (int)(idx - j * dsp);
+        float v = 0.0f;
+        if (j >= n) {
+            v = d < dzb + dyb ? INFINITY : 0.0f;
+        } else if (d < dzb) {
+            if (d < dz) v = zc[d].base[zc[d].off + j];
+        } else if (d < dzb + dyb) {
+            const int e = d - dzb;
+            if (e < dy) v = yc[e].base[yc[e].off + j];
+        }
+        if (j < n && !isfinite(v)) atomicOr(err, kErrNonFinite);
+        sh[idx] = v;
+    }
+}
+
+__global__ void k_iota(int32_t *perm, int n_slots, int64_t n)
+{
+    const int64_t total = (int64_t)n_slots * n;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x)
+        perm[idx] = (int32_t)(idx % n);
+}
+
+// Fisher-Yates (Durstenfeld) shuffle of slot's row, driven by SplitMix64 from
+// the state seed ^ mix64(stream): for i = n-1 .. 1 swap a[i], a[hi64(r*(i+1))].
+__global__ void k_fisher_yates(int32_t *perm, const uint64_t *streams, const uint64_t *seeds,
+                               int n_slots, int64_t n)
+{
+    const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot >= n_slots) return;
+    int32_t *a = perm + (int64_t)slot * n;
+    uint64_t state = seeds[slot] ^ mix64(streams[slot]);
+    for (int64_t i = n - 1; i >= 1; --i) {
+        state += 0x9E3779B97F4A7C15ull;
+        const uint64_t r = mix64(state);
+        const int64_t j = (int64_t)__umul64hi(r, (uint64_t)(i + 1));
+        const int32_t t = a[i];
+        a[i] = a[j];
+        a[j] = t;
+    }
+}
+
+// xi[grp][j][g*dxb + d] = X_job[d][pi_job(j)] (job = grp*gb + g; jobs past the
+// end repeat job 0), 0 for d >= dx, +inf for j >= n.
+__global__ void k_gather_x(const Col *xc, int dx, int dxb, const Job *jobs, int n_jobs,
+                           const int32_t *perm, int64_t n, int64_t n_pad, int gb, int n_groups,
+                           float *xi, int *err)
+{
+    const int xw = gb * dxb;
+    const int64_t per_grp = n_pad * xw;
+    const int64_t total = per_grp * n_groups;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t grp = idx / per_grp;
+        const int64_t rem = idx - grp * per_grp;
+        const int64_t j = rem / xw;
+        const int w = (int)(rem - j * xw);
+        const int g = w / dxb, d = w - g * dxb;
+        int job = (int)grp * gb + g;
+        if (job >= n_jobs) job = 0;
+        float v;
+        if (j >= n) {
+            v = INFINITY;
+        } else if (d >= dx) {
+            v = 0.0f;
+        } else {
+            const Job jb = jobs[job];
+            const int64_t t = jb.slot < 0 ? j : (int64_t)perm[(int64_t)jb.slot * n + j];
+            const Col c = xc[(int64_t)jb.src * dx + d];
+            v = c.base[c.off + t];
+            if (!isfinite(v)) atomicOr(err, kErrNonFinite);
+        }
+        xi[idx] = v;
+    }
+}
+
+// cmi[job] = psi(k) + (sum over query tiles, in order) / n.
+__global__ void k_finalize(const double *partial, int n_jobs, int n_qt, const double *psi, int k,
+                           int64_t n, double *cmi)
+{
+    const int job = blockIdx.x * blockDim.x + threadIdx.x;
+    if (job >= n_jobs) return;
+    double s = 0.0;
+    for (int t = 0; t < n_qt; ++t) s += partial[(int64_t)job * n_qt + t];
+    cmi[job] = psi[k] + s / (double)n;
+}
+
+// Max-statistic gate over est[c][1+S] (candidates in ascending id order).
+__global__ void k_gate(const double *est, const int32_t *ids, int n_cand, int n_surr,
+                       double alpha, idtx_step *out)
+{
+    __shared__ double s_tobs;
+    __shared__ int s_best;
+    __shared__ int s_cnt[32];
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        double t = -INFINITY;
+        int b = -1;
+        for (int c = 0; c < n_cand; ++c) {
+            const double v = est[(int64_t)c * (1 + n_surr)];
+            if (v > t) {
+                t = v;
+                b = c;
+            }
+        }
+        s_tobs = t;
+        s_best = b;
+    }
+    __syncthreads();
+    int cnt = 0;
+    for (int s = tid; s < n_surr; s += blockDim.x) {
+        double ts = -INFINITY;
+        for (int c = 0; c < n_cand; ++c) ts = fmax(ts, est[(int64_t)c * (1 + n_surr) + 1 + s]);
+        cnt += ts >= s_tobs ? 1 : 0;
+    }
+    for (int off = 16; off >= 1; off >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
+    if ((tid & 31) == 0) s_cnt[tid >> 5] = cnt;
+    __syncthreads();
+    if (tid == 0) {
+        int total = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) total += s_cnt[w];
+        const double p = (double)total / (double)n_surr;
+        out->cand = s_best >= 0 ? ids[s_best] : -1;
+        out->significant = (s_best >= 0 && p < alpha) ? 1 : 0;
+        out->stat = s_tobs;
+        out->pval = p;
+    }
+}
+
+static int grid_for(int64_t total, int block)
+{
+    int64_t g = (total + block - 1) / block;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 32));
+}
+
+}  // namespace idtx
+
+using namespace idtx;
+
+// ------------------------------------------------------------------ context
+enum {
+    B_IN = 0,   // copied host inputs
+    B_DESC,     // per-call descriptor arena (columns, jobs, streams, seeds)
+    B_SH,
+    B_XI,
+    B_PERM,
+    B_PARTIAL,
+    B_CMI,
+    B_EPS,
+    B_CNT,
+    B_STEP,
+    kNumBufs
+};
+
+struct idtx_ctx {
+    int device = 0;
+    void *buf[kNumBufs] = {};
+    size_t cap[kNumBufs] = {};
+    double *psi = nullptr;
+    int64_t psi_n = 0;
+    int *d_err = nullptr;
+    int *h_err = nullptr;  // pinned
+    std::vector<KsgVariant> variants;
+    // measurement counters
+    bool profiling = false;
+    idtx_stats stats = {};
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;  // fused launches of this call
+    std::vector<cudaEvent_t> event_pool;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+int ensure(idtx_ctx *c, int slot, size_t bytes)
+{
+    if (bytes == 0) bytes = 256;
+    if (c->cap[slot] >= bytes) return IDTX_OK;
+    if (c->buf[slot]) {
+        cudaFree(c->buf[slot]);
+        c->buf[slot] = nullptr;
+        c->cap[slot] = 0;
+    }
+    size_t want = std::max(bytes, c->cap[slot] + c->cap[slot] / 2);
+    want = (want + (1u << 21) - 1) & ~((size_t)(1u << 21) - 1);
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(IDTX_ENOMEM, "cudaMalloc of %zu bytes failed: %s", want, cudaGetErrorString(e));
+    }
+    c->buf[slot] = p;
+    c->cap[slot] = want;
+    return IDTX_OK;
+}
+
+int ensure_psi(idtx_ctx *c, int64_t n_max, cudaStream_t st)
+{
+    if (c->psi_n >= n_max) return IDTX_OK;
+    int64_t want = std::max<int64_t>(n_max, 1 << 16);
+    if (c->psi) cudaFree(c->psi);
+    c->psi = nullptr;
+    c->psi_n = 0;
+    IDTX_CUDA(cudaMalloc(&c->psi, sizeof(double) * (size_t)(want + 1)));
+    k_psi_table<<<grid_for(want + 1, 256), 256, 0, st>>>(c->psi, want);
+    IDTX_CUDA(cudaGetLastError());
+    c->stats.kernel_launches += 1;
+    c->psi_n = want;
+    return IDTX_OK;
+}
+
+bool device_accessible(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+const int kZBuckets[] = {1, 2, 3, 4, 5, 6, 8, 10, 12, 16};
+
+const KsgVariant *pick_variant(const idtx_ctx *c, int dx, int dy, int dz, int k)
+{
+    const int dze = std::max(dz, 1);
+    if (k == 4 && dx <= 2 && dy <= 2) {
+        int zb = 0;
+        for (int b : kZBuckets)
+            if (b >= dze) {
+                zb = b;
+                break;
+            }
+        for (const KsgVariant &v : c->variants)
+            if (v.exact && v.k1 == 5 && v.dx == dx && v.dy == dy && v.dz == zb) return &v;
+    }
+    for (const KsgVariant &v : c->variants)
+        if (!v.exact && v.dx >= dx && v.dy >= dy && v.dz >= dze && v.k1 > k) return &v;
+    return nullptr;
+}
+
+// Host-side description of one group of jobs sharing Y and Z.
+struct Group {
+    int64_t n = 0;
+    int dx = 0, dy = 0, dz = 0, k = 0;
+    std::vector<Col> xcols;  // [n_src][dx]
+    std::vector<Col> ycols, zcols;
+    std::vector<Job> jobs;
+    std::vector<uint64_t> slot_stream, slot_seed;
+    // filled by plan()
+    const KsgVariant *v = nullptr;
+    int64_t n_pad = 0;
+    int n_qt = 0, n_groups = 0;
+    size_t off_x = 0, off_y = 0, off_z = 0, off_jobs = 0, off_streams = 0, off_seeds = 0;
+    size_t off_cmi = 0;  // index of the group's first job in the call's cmi buffer
+};
+
+int plan(idtx_ctx *c, Group &g)
+{
+    g.v = pick_variant(c, g.dx, g.dy, g.dz, g.k);
+    if (!g.v)
+        return fail(IDTX_EINVAL, "no kernel for dx=%d dy=%d dz=%d k=%d", g.dx, g.dy, g.dz, g.k);
+    g.n_pad = (g.n + kTQ - 1) / kTQ * kTQ;
+    g.n_qt = (int)(g.n_pad / kTQ);
+    g.n_groups = (int)((g.jobs.size() + g.v->gb - 1) / g.v->gb);
+    if (g.n_groups > 65535) return fail(IDTX_EINVAL, "too many estimates in one group");
+    return IDTX_OK;
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Lay out the descriptor arrays of all groups in one host arena.
+void pack_desc(std::vector<Group> &gs, std::vector<unsigned char> &arena)
+{
+    size_t off = 0;
+    auto put = [&](const void *src, size_t bytes) {
+        off = align_up(off, 16);
+        size_t at = off;
+        arena.resize(off + bytes);
+        if (bytes) memcpy(arena.data() + at, src, bytes);
+        off += bytes;
+        return at;
+    };
+    for (Group &g : gs) {
+        g.off_x = put(g.xcols.data(), g.xcols.size() * sizeof(Col));
+        g.off_y = put(g.ycols.data(), g.ycols.size() * sizeof(Col));
+        g.off_z = put(g.zcols.data(), g.zcols.size() * sizeof(Col));
+        g.off_jobs = put(g.jobs.data(), g.jobs.size() * sizeof(Job));
+        g.off_streams = put(g.slot_stream.data(), g.slot_stream.size() * sizeof(uint64_t));
+        g.off_seeds = put(g.slot_seed.data(), g.slot_seed.size() * sizeof(uint64_t));
+    }
+    if (arena.empty()) arena.resize(16);
+}
+
+struct CallBuffers {
+    size_t sh = 0, xi = 0, perm = 0, partial = 0;
+};
+
+void sizes_of(const Group &g, CallBuffers &b)
+{
+    b.sh = std::max(b.sh, (size_t)g.n_pad * g.v->dsp * sizeof(float));
+    b.xi = std::max(b.xi, (size_t)g.n_groups * g.n_pad * g.v->gb * g.v->dx * sizeof(float));
+    b.perm = std::max(b.perm, g.slot_stream.size() * (size_t)g.n * sizeof(int32_t));
+    b.partial = std::max(b.partial, g.jobs.size() * (size_t)g.n_qt * sizeof(double));
+}
+
+int take_event(idtx_ctx *c, cudaEvent_t *ev)
+{
+    if (!c->event_pool.empty()) {
+        *ev = c->event_pool.back();
+        c->event_pool.pop_back();
+        return IDTX_OK;
+    }
+    IDTX_CUDA(cudaEventCreate(ev));
+    return IDTX_OK;
+}
+
+// Enqueue one planned group.  cmi: device [n_jobs] (the group's slice).
+int enqueue_group(idtx_ctx *c, const Group &g, cudaStream_t st, double *cmi, float *eps_out,
+                  int32_t *cnt_out, long long timeout_ns)
+{
+    const unsigned char *desc = (const unsigned char *)c->buf[B_DESC];
+    const Col *xc = (const Col *)(desc + g.off_x);
+    const Col *yc = (const Col *)(desc + g.off_y);
+    const Col *zc = (const Col *)(desc + g.off_z);
+    const Job *jobs = (const Job *)(desc + g.off_jobs);
+    const uint64_t *streams = (const uint64_t *)(desc + g.off_streams);
+    const uint64_t *seeds = (const uint64_t *)(desc + g.off_seeds);
+    float *sh = (float *)c->buf[B_SH];
+    float *xi = (float *)c->buf[B_XI];
+    int32_t *perm = (int32_t *)c->buf[B_PERM];
+    double *partial = (double *)c->buf[B_PARTIAL];
+    const KsgVariant &v = *g.v;
+    const int n_jobs = (int)g.jobs.size();
+    const int n_slots = (int)g.slot_stream.size();
+
+    const int dzb = v.dz, dyb = v.dy;
+    k_pack_shared<<<grid_for(g.n_pad * v.dsp, 256), 256, 0, st>>>(
+        zc, g.dz, dzb, yc, g.dy, dyb, v.dsp, g.n, g.n_pad, sh, c->d_err);
+    IDTX_CUDA(cudaGetLastError());
+    if (n_slots > 0) {
+        k_iota<<<grid_for((int64_t)n_slots * g.n, 256), 256, 0, st>>>(perm, n_slots, g.n);
+        IDTX_CUDA(cudaGetLastError());
+        k_fisher_yates<<<(n_slots + 31) / 32, 32, 0, st>>>(perm, streams, seeds, n_slots, g.n);
+        IDTX_CUDA(cudaGetLastError());
+    }
+    k_gather_x<<<grid_for((int64_t)g.n_groups * g.n_pad * v.gb * v.dx, 256), 256, 0, st>>>(
+        xc, g.dx, v.dx, jobs, n_jobs, perm, g.n, g.n_pad, v.gb, g.n_groups, xi, c->d_err);
+    IDTX_CUDA(cudaGetLastError());
+
+    KsgLaunch a;
+    a.sh = sh;
+    a.xi = xi;
+    a.psi = c->psi;
+    a.partial = partial;
+    a.eps_out = eps_out;
+    a.cnt_out = cnt_out;
+    a.err = c->d_err;
+    a.n = g.n;
+    a.n_pad = g.n_pad;
+    a.n_jobs = n_jobs;
+    a.n_qt = g.n_qt;
+    a.k = g.k;
+    a.timeout_ns = timeout_ns;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (c->profiling) {
+        IDTX_TRY(take_event(c, &ev0));
+        IDTX_TRY(take_event(c, &ev1));
+        IDTX_CUDA(cudaEventRecord(ev0, st));
+    }
+    IDTX_CUDA(v.fn(a, g.n_groups, st));
+    if (c->profiling) {
+        IDTX_CUDA(cudaEventRecord(ev1, st));
+        c->pending.emplace_back(ev0, ev1);
+    }
+    {
+        const double pairs = (double)g.n * (double)g.n * (double)g.n_groups;
+        const int dze = std::max(g.dz, 1);
+        c->stats.fused_launches += 1;
+        c->stats.fused_lane_ops += pairs * (double)(2 * (g.dy + dze) + 1 + 2 * dze + 1);
+        c->stats.kernel_launches += (n_slots > 0 ? 6 : 4);
+    }
+    k_finalize<<<(n_jobs + 127) / 128, 128, 0, st>>>(partial, n_jobs, g.n_qt, c->psi, g.k, g.n,
+                                                      cmi);
+    IDTX_CUDA(cudaGetLastError());
+    return IDTX_OK;
+}
+
+// Copy the caller's columns (host memory) into device scratch; returns the
+// device base and sets the leading dimension to n.
+struct HostCopy {
+    const float *src;
+    int dims;
+    int64_t ld;
+    size_t off;  // float offset in B_IN
+};
+
+int finish_call(idtx_ctx *c, cudaStream_t st)
+{
+    IDTX_CUDA(cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    IDTX_CUDA(cudaStreamSynchronize(st));
+    for (auto &pe : c->pending) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, pe.first, pe.second) == cudaSuccess) c->stats.fused_ms += ms;
+        c->event_pool.push_back(pe.first);
+        c->event_pool.push_back(pe.second);
+    }
+    c->pending.clear();
+    const int e = *c->h_err;
+    if (e & kErrNonFinite) return fail(IDTX_EINVAL, "input contains NaN or Inf");
+    if (e & kErrTimeout) return fail(IDTX_ETIMEOUT, "a bounded device wait ran out");
+    if (e) return fail(IDTX_EINTERNAL, "device error word 0x%x", e);
+    return IDTX_OK;
+}
+
+long long timeout_of(const idtx_settings *s)
+{
+    const long long ms = (s && s->timeout_ms > 0) ? s->timeout_ms : 2000;
+    return ms * 1000000ll;
+}
+
+int check_cols(const float *p, int dims, const char *name)
+{
+    if (dims > 0 && !p) return fail(IDTX_EINVAL, "%s is NULL", name);
+    return IDTX_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+int idtx_version(void) { return 100; }
+
+const char *idtx_last_error(void) { return t_err.c_str(); }
+
+int idtx_ctx_create(idtx_ctx **out, int device)
+{
+    if (!out) return fail(IDTX_EINVAL, "ctx is NULL");
+    *out = nullptr;
+    int n_dev = 0;
+    IDTX_CUDA(cudaGetDeviceCount(&n_dev));
+    if (device < 0 || device >= n_dev) return fail(IDTX_EINVAL, "device %d out of range", device);
+    DeviceGuard guard(device);
+    idtx_ctx *c = new idtx_ctx();
+    c->device = device;
+    KsgVariant tmp[64];
+    int n = 0;
+    n += ksg_variants_d11(tmp + n);
+    n += ksg_variants_d12(tmp + n);
+    n += ksg_variants_d21(tmp + n);
+    n += ksg_variants_d22(tmp + n);
+    n += ksg_variants_generic(tmp + n);
+    c->variants.assign(tmp, tmp + n);
+    cudaError_t e = cudaMalloc(&c->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost(&c->h_err, sizeof(int));
+    if (e != cudaSuccess) {
+        idtx_ctx_destroy(c);
+        return fail(IDTX_ENOMEM, "context allocation failed: %s", cudaGetErrorString(e));
+    }
+    *out = c;
+    return IDTX_OK;
+}
+
+int idtx_ctx_set_profiling(idtx_ctx *c, int enable)
+{
+    if (!c) return fail(IDTX_EINVAL, "ctx is NULL");
+    c->profiling = enable != 0;
+    return IDTX_OK;
+}
+
+int idtx_ctx_get_stats(idtx_ctx *c, idtx_stats *out)
+{
+    if (!c || !out) return fail(IDTX_EINVAL, "NULL argument");
+    *out = c->stats;
+    return IDTX_OK;
+}
+
+int idtx_ctx_reset_stats(idtx_ctx *c)
+{
+    if (!c) return fail(IDTX_EINVAL, "ctx is NULL");
+    c->stats = idtx_stats{};
+    return IDTX_OK;
+}
+
+int idtx_ctx_destroy(idtx_ctx *c)
+{
+    if (!c) return IDTX_OK;
+    DeviceGuard guard(c->device);
+    cudaDeviceSynchronize();
+    for (auto &pe : c->pending) c->event_pool.push_back(pe.first), c->event_pool.push_back(pe.second);
+    for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
+    for (int i = 0; i < kNumBufs; ++i)
+        if (c->buf[i]) cudaFree(c->buf[i]);
+    if (c->psi) cudaFree(c->psi);
+    if (c->d_err) cudaFree(c->d_err);
+    if (c->h_err) cudaFreeHost(c->h_err);
+    delete c;
+    return IDTX_OK;
+}
+
+int idtx_cmi_ksg(idtx_ctx *c, const float *x, int dx, const float *y, int dy, const float *z,
+                 int dz, int64_t n, int64_t ld, const idtx_settings *s, double *cmi_out,
+                 float *eps_out, int32_t *counts_out, void *stream)
+{
+    if (!c) return fail(IDTX_EINVAL, "ctx is NULL");
+    if (!s) return fail(IDTX_EINVAL, "settings is NULL");
+    if (!cmi_out) return fail(IDTX_EINVAL, "cmi_out is NULL");
+    if (dx < 1 || dx > IDTX_MAX_DX || dy < 1 || dy > IDTX_MAX_DY || dz < 0 || dz > IDTX_MAX_DZ)
+        return fail(IDTX_EINVAL, "dims out of range (dx=%d dy=%d dz=%d)", dx, dy, dz);
+    if (n < 2 || n > IDTX_MAX_N || ld < n)
+        return fail(IDTX_EINVAL, "bad n=%lld / ld=%lld", (long long)n, (long long)ld);
+    if (s->k < 1 || s->k > IDTX_MAX_K || s->k > n - 1)
+        return fail(IDTX_EINVAL, "k=%d out of range for n=%lld", s->k, (long long)n);
+    if (s->n_surr < 0) return fail(IDTX_EINVAL, "n_surr < 0");
+    IDTX_TRY(check_cols(x, dx, "x"));
+    IDTX_TRY(check_cols(y, dy, "y"));
+    IDTX_TRY(check_cols(z, dz, "z"));
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n_jobs = 1 + s->n_surr;
+
+    // Inputs: device pointers are used in place, host pointers are copied.
+    const float *src[3] = {x, y, z};
+    const int dims[3] = {dx, dy, dz};
+    const float *dev[3] = {x, y, z};
+    int64_t lds[3] = {ld, ld, ld};
+    size_t in_floats = 0;
+    bool host[3] = {false, false, false};
+    for (int t = 0; t < 3; ++t)
+        if (dims[t] > 0 && !device_accessible(src[t])) {
+            host[t] = true;
+            in_floats += (size_t)dims[t] * (size_t)n;
+        }
+    IDTX_TRY(ensure(c, B_IN, in_floats * sizeof(float)));
+    IDTX_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
+    {
+        size_t off = 0;
+        for (int t = 0; t < 3; ++t)
+            if (host[t]) {
+                float *d = (float *)c->buf[B_IN] + off;
+                IDTX_CUDA(cudaMemcpy2DAsync(d, (size_t)n * sizeof(float), src[t],
+                                            (size_t)ld * sizeof(float), (size_t)n * sizeof(float),
+                                            (size_t)dims[t], cudaMemcpyHostToDevice, st));
+                dev[t] = d;
+                lds[t] = n;
+                off += (size_t)dims[t] * (size_t)n;
+            }
+    }
+
+    std::vector<Group> gs(1);
+    Group &g = gs[0];
+    g.n = n;
+    g.dx = dx;
+    g.dy = dy;
+    g.dz = dz;
+    g.k = s->k;
+    for (int d = 0; d < dx; ++d) g.xcols.push_back(Col{dev[0] + d * lds[0], 0});
+    for (int d = 0; d < dy; ++d) g.ycols.push_back(Col{dev[1] + d * lds[1], 0});
+    for (int d = 0; d < dz; ++d) g.zcols.push_back(Col{dev[2] + d * lds[2], 0});
+    g.jobs.push_back(Job{0, -1});
+    for (int sidx = 0; sidx < s->n_surr; ++sidx) {
+        g.jobs.push_back(Job{0, sidx});
+        g.slot_stream.push_back((uint64_t)sidx);
+        g.slot_seed.push_back(s->seed);
+    }
+    IDTX_TRY(plan(c, g));
+    std::vector<unsigned char> arena;
+    pack_desc(gs, arena);
+    CallBuffers b;
+    sizes_of(g, b);
+    const bool eps_dev = eps_out && device_accessible(eps_out);
+    const bool cnt_dev = counts_out && device_accessible(counts_out);
+    const bool cmi_dev = device_accessible(cmi_out);
+    IDTX_TRY(ensure(c, B_DESC, arena.size()));
+    IDTX_TRY(ensure(c, B_SH, b.sh));
+    IDTX_TRY(ensure(c, B_XI, b.xi));
+    IDTX_TRY(ensure(c, B_PERM, b.perm));
+    IDTX_TRY(ensure(c, B_PARTIAL, b.partial));
+    IDTX_TRY(ensure(c, B_CMI, (size_t)n_jobs * sizeof(double)));
+    if (eps_out && !eps_dev) IDTX_TRY(ensure(c, B_EPS, (size_t)n_jobs * n * sizeof(float)));
+    if (counts_out && !cnt_dev)
+        IDTX_TRY(ensure(c, B_CNT, (size_t)n_jobs * 3 * n * sizeof(int32_t)));
+    IDTX_TRY(ensure_psi(c, std::max<int64_t>(n, s->k) + 1, st));
+    IDTX_CUDA(cudaMemcpyAsync(c->buf[B_DESC], arena.data(), arena.size(), cudaMemcpyHostToDevice,
+                              st));
+    float *eps_d = eps_out ? (eps_dev ? eps_out : (float *)c->buf[B_EPS]) : nullptr;
+    int32_t *cnt_d = counts_out ? (cnt_dev ? counts_out : (int32_t *)c->buf[B_CNT]) : nullptr;
+    double *cmi_d = (double *)c->buf[B_CMI];
+    IDTX_TRY(enqueue_group(c, g, st, cmi_d, eps_d, cnt_d, timeout_of(s)));
+    IDTX_CUDA(cudaMemcpyAsync(cmi_out, cmi_d, (size_t)n_jobs * sizeof(double),
+                              cmi_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    if (eps_out && !eps_dev)
+        IDTX_CUDA(cudaMemcpyAsync(eps_out, eps_d, (size_t)n_jobs * n * sizeof(float),
+                                  cudaMemcpyDeviceToHost, st));
+    if (counts_out && !cnt_dev)
+        IDTX_CUDA(cudaMemcpyAsync(counts_out, cnt_d, (size_t)n_jobs * 3 * n * sizeof(int32_t),
+                                  cudaMemcpyDeviceToHost, st));
+    return finish_call(c, st);
+}
+
+int idtx_cmi_batch(idtx_ctx *c, const idtx_problem *probs, int n_probs, int k, double *out,
+                   void *stream)
+{
+    if (!c) return fail(IDTX_EINVAL, "ctx is NULL");
+    if (!probs || n_probs < 1 || !out) return fail(IDTX_EINVAL, "bad problem list or output");
+    if (k < 1 || k > IDTX_MAX_K) return fail(IDTX_EINVAL, "k=%d out of range", k);
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+
+    size_t in_floats = 0;
+    int64_t n_max = 0;
+    size_t total_jobs = 0;
+    std::vector<std::array<bool, 3>> host(n_probs);
+    for (int p = 0; p < n_probs; ++p) {
+        const idtx_problem &q = probs[p];
+        if (q.dx < 1 || q.dx > IDTX_MAX_DX || q.dy < 1 || q.dy > IDTX_MAX_DY || q.dz < 0 ||
+            q.dz > IDTX_MAX_DZ)
+            return fail(IDTX_EINVAL, "problem %d: dims out of range", p);
+        if (q.n < 2 || q.n > IDTX_MAX_N || q.ld < q.n || k > q.n - 1 || q.n_surr < 0)
+            return fail(IDTX_EINVAL, "problem %d: bad n/ld/k/n_surr", p);
+        IDTX_TRY(check_cols(q.x, q.dx, "x"));
+        IDTX_TRY(check_cols(q.y, q.dy, "y"));
+        IDTX_TRY(check_cols(q.z, q.dz, "z"));
+        const float *src[3] = {q.x, q.y, q.z};
+        const int dims[3] = {q.dx, q.dy, q.dz};
+        for (int t = 0; t < 3; ++t) {
+            host[p][t] = dims[t] > 0 && !device_accessible(src[t]);
+            if (host[p][t]) in_floats += (size_t)dims[t] * (size_t)q.n;
+        }
+        n_max = std::max(n_max, q.n);
+        total_jobs += 1 + (size_t)q.n_surr;
+    }
+    IDTX_TRY(ensure(c, B_IN, in_floats * sizeof(float)));
+    IDTX_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
+    std::vector<Group> gs(n_probs);
+    size_t in_off = 0, job_off = 0;
+    for (int p = 0; p < n_probs; ++p) {
+        const idtx_problem &q = probs[p];
+        const float *src[3] = {q.x, q.y, q.z};
+        const int dims[3] = {q.dx, q.dy, q.dz};
+        const float *dev[3] = {q.x, q.y, q.z};
+        int64_t lds[3] = {q.ld, q.ld, q.ld};
+        for (int t = 0; t < 3; ++t)
+            if (host[p][t]) {
+                float *d = (float *)c->buf[B_IN] + in_off;
+                IDTX_CUDA(cudaMemcpy2DAsync(d, (size_t)q.n * sizeof(float), src[t],
+                                            (size_t)q.ld * sizeof(float),
+                                            (size_t)q.n * sizeof(float), (size_t)dims[t],
+                                            cudaMemcpyHostToDevice, st));
+                dev[t] = d;
+                lds[t] = q.n;
+                in_off += (size_t)dims[t] * (size_t)q.n;
+            }
+        Group &g = gs[p];
+        g.n = q.n;
+        g.dx = q.dx;
+        g.dy = q.dy;
+        g.dz = q.dz;
+        g.k = k;
+        for (int d = 0; d < q.dx; ++d) g.xcols.push_back(Col{dev[0] + d * lds[0], 0});
+        for (int d = 0; d < q.dy; ++d) g.ycols.push_back(Col{dev[1] + d * lds[1], 0});
+        for (int d = 0; d < q.dz; ++d) g.zcols.push_back(Col{dev[2] + d * lds[2], 0});
+        g.jobs.push_back(Job{0, -1});
+        for (int sidx = 0; sidx < q.n_surr; ++sidx) {
+            g.jobs.push_back(Job{0, sidx});
+            g.slot_stream.push_back((uint64_t)sidx);
+            g.slot_seed.push_back(q.seed);
+        }
+        IDTX_TRY(plan(c, g));
+        g.off_cmi = job_off;
+        job_off += g.jobs.size();
+    }
+    std::vector<unsigned char> arena;
+    pack_desc(gs, arena);
+    CallBuffers b;
+    for (const Group &g : gs) sizes_of(g, b);
+    IDTX_TRY(ensure(c, B_DESC, arena.size()));
+    IDTX_TRY(ensure(c, B_SH, b.sh));
+    IDTX_TRY(ensure(c, B_XI, b.xi));
+    IDTX_TRY(ensure(c, B_PERM, b.perm));
+    IDTX_TRY(ensure(c, B_PARTIAL, b.partial));
+    IDTX_TRY(ensure(c, B_CMI, total_jobs * sizeof(double)));
+    IDTX_TRY(ensure_psi(c, std::max<int64_t>(n_max, k) + 1, st));
+    IDTX_CUDA(cudaMemcpyAsync(c->buf[B_DESC], arena.data(), arena.size(), cudaMemcpyHostToDevice,
+                              st));
+    double *cmi_d = (double *)c->buf[B_CMI];
+    const long long tmo = timeout_of(nullptr);
+    for (const Group &g : gs)
+        IDTX_TRY(enqueue_group(c, g, st, cmi_d + g.off_cmi, nullptr, nullptr, tmo));
+    IDTX_CUDA(cudaMemcpyAsync(out, cmi_d, total_jobs * sizeof(double),
+                              device_accessible(out) ? cudaMemcpyDeviceToDevice
+                                                     : cudaMemcpyDeviceToHost,
+                              st));
+    return finish_call(c, st);
+}
+
+int idtx_mte_step(idtx_ctx *c, const float *series, int n_proc, int64_t T, int target, int n_past,
+                  int min_lag, int max_lag, const int32_t *selected, int n_selected,
+                  int step_index, const idtx_settings *s, idtx_step *result, double *est_out,
+                  void *stream)
+{
+    if (!c) return fail(IDTX_EINVAL, "ctx is NULL");
+    if (!s || !result || !series) return fail(IDTX_EINVAL, "NULL settings/result/series");
+    if (n_proc < 1 || target < 0 || target >= n_proc || n_past < 0 || min_lag < 1 ||
+        max_lag < min_lag || n_selected < 0 || (n_selected > 0 && !selected) || step_index < 0 ||
+        step_index >= (1 << 16))
+        return fail(IDTX_EINVAL, "bad greedy-step arguments");
+    const int n_lags = max_lag - min_lag + 1;
+    const int n_cand_total = n_proc * n_lags;
+    if (n_cand_total >= (1 << 24)) return fail(IDTX_EINVAL, "too many candidates");
+    const int64_t L = std::max(max_lag, n_past);
+    if (T <= L || T - L > IDTX_MAX_N) return fail(IDTX_EINVAL, "bad T for the lags");
+    const int64_t n = T - L;
+    if (s->k < 1 || s->k > IDTX_MAX_K || s->k > n - 1) return fail(IDTX_EINVAL, "bad k");
+    if (s->n_surr < 1 || s->n_surr >= (1 << 24)) return fail(IDTX_EINVAL, "n_surr out of range");
+    if (!(s->alpha > 0.0 && s->alpha < 1.0)) return fail(IDTX_EINVAL, "alpha out of (0,1)");
+    const int dz = n_past + n_selected;
+    if (dz > IDTX_MAX_DZ) return fail(IDTX_EINVAL, "dz=%d exceeds %d", dz, IDTX_MAX_DZ);
+    std::vector<char> alive(n_cand_total, 1);
+    for (int lag = min_lag; lag <= std::min(max_lag, n_past); ++lag)
+        alive[target * n_lags + (lag - min_lag)] = 0;
+    for (int t = 0; t < n_selected; ++t) {
+        if (selected[t] < 0 || selected[t] >= n_cand_total)
+            return fail(IDTX_EINVAL, "selected id %d out of range", selected[t]);
+        alive[selected[t]] = 0;
+    }
+    std::vector<int32_t> ids;
+    for (int cid = 0; cid < n_cand_total; ++cid)
+        if (alive[cid]) ids.push_back(cid);
+    if (ids.empty()) return fail(IDTX_EINVAL, "no candidate left");
+    const int n_alive = (int)ids.size();
+    const int n_jobs = n_alive * (1 + s->n_surr);
+
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const float *ser = series;
+    const bool host_series = !device_accessible(series);
+    IDTX_TRY(ensure(c, B_IN, host_series ? (size_t)n_proc * T * sizeof(float) : 0));
+    IDTX_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
+    if (host_series) {
+        IDTX_CUDA(cudaMemcpyAsync(c->buf[B_IN], series, (size_t)n_proc * T * sizeof(float),
+                                  cudaMemcpyHostToDevice, st));
+        ser = (const float *)c->buf[B_IN];
+    }
+
+    std::vector<Group> gs(1);
+    Group &g = gs[0];
+    g.n = n;
+    g.dx = 1;
+    g.dy = 1;
+    g.dz = dz;
+    g.k = s->k;
+    // Sample i is time L + i; the variable (p, lag) at sample i is series[p][L + i - lag].
+    auto col = [&](int p, int lag) { return Col{ser + (int64_t)p * T, L - lag}; };
+    g.ycols.push_back(col(target, 0));
+    for (int lag = 1; lag <= n_past; ++lag) g.zcols.push_back(col(target, lag));
+    for (int t = 0; t < n_selected; ++t)
+        g.zcols.push_back(col(selected[t] / n_lags, min_lag + selected[t] % n_lags));
+    for (int a = 0; a < n_alive; ++a) {
+        const int cid = ids[a];
+        g.xcols.push_back(col(cid / n_lags, min_lag + cid % n_lags));
+        g.jobs.push_back(Job{a, -1});
+        for (int sidx = 0; sidx < s->n_surr; ++sidx) {
+            g.jobs.push_back(Job{a, (int32_t)g.slot_stream.size()});
+            g.slot_stream.push_back(((uint64_t)step_index << 48) | ((uint64_t)cid << 24) |
+                                    (uint64_t)sidx);
+            g.slot_seed.push_back(s->seed);
+        }
+    }
+    IDTX_TRY(plan(c, g));
+    std::vector<unsigned char> arena;
+    pack_desc(gs, arena);
+    // ids after the descriptors
+    size_t ids_off = align_up(arena.size(), 16);
+    arena.resize(ids_off + ids.size() * sizeof(int32_t));
+    memcpy(arena.data() + ids_off, ids.data(), ids.size() * sizeof(int32_t));
+    CallBuffers b;
+    sizes_of(g, b);
+    IDTX_TRY(ensure(c, B_DESC, arena.size()));
+    IDTX_TRY(ensure(c, B_SH, b.sh));
+    IDTX_TRY(ensure(c, B_XI, b.xi));
+    IDTX_TRY(ensure(c, B_PERM, b.perm));
+    IDTX_TRY(ensure(c, B_PARTIAL, b.partial));
+    IDTX_TRY(ensure(c, B_CMI, (size_t)n_jobs * sizeof(double)));
+    IDTX_TRY(ensure(c, B_STEP, sizeof(idtx_step)));
+    IDTX_TRY(ensure_psi(c, std::max<int64_t>(n, s->k) + 1, st));
+    IDTX_CUDA(cudaMemcpyAsync(c->buf[B_DESC], arena.data(), arena.size(), cudaMemcpyHostToDevice,
+                              st));
+    double *cmi_d = (double *)c->buf[B_CMI];
+    IDTX_TRY(enqueue_group(c, g, st, cmi_d, nullptr, nullptr, timeout_of(s)));
+    const int32_t *ids_d = (const int32_t *)((const unsigned char *)c->buf[B_DESC] + ids_off);
+    idtx_step *step_d = (idtx_step *)c->buf[B_STEP];
+    k_gate<<<1, 256, 0, st>>>(cmi_d, ids_d, n_alive, s->n_surr, s->alpha, step_d);
+    IDTX_CUDA(cudaGetLastError());
+    c->stats.kernel_launches += 1;
+    IDTX_CUDA(cudaMemcpyAsync(result, step_d, sizeof(idtx_step),
+                              device_accessible(result) ? cudaMemcpyDeviceToDevice
+                                                        : cudaMemcpyDeviceToHost,
+                              st));
+    if (est_out) {
+        const bool dev = device_accessible(est_out);
+        const size_t row = (size_t)(1 + s->n_surr) * sizeof(double);
+        // Candidate rows are contiguous in cmi_d; scatter them to their ids.
+        for (int a = 0; a < n_alive; ++a)
+            IDTX_CUDA(cudaMemcpyAsync((unsigned char *)est_out + (size_t)ids[a] * row,
+                                      (const unsigned char *)cmi_d + (size_t)a * row, row,
+                                      dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                      st));
+    }
+    return finish_call(c, st);
+}
+
+int idtx_mte_select_target(idtx_ctx *c, const float *series, int n_proc, int64_t T, int target,
+                           int n_past, int min_lag, int max_lag, const idtx_settings *s,
+                           int max_parents, int32_t *parents_out, int *n_parents,
+                           idtx_step *steps_out, int *n_steps, void *stream)
+{
+    if (!c) return fail(IDTX_EINVAL, "ctx is NULL");
+    if (max_parents < 0 || !n_parents || !n_steps || !steps_out ||
+        (max_parents > 0 && !parents_out))
+        return fail(IDTX_EINVAL, "bad outputs");
+    if (!series) return fail(IDTX_EINVAL, "series is NULL");
+    *n_parents = 0;
+    *n_steps = 0;
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    // Keep a device copy of host series for all steps.
+    const float *ser = series;
+    std::vector<float> none;
+    void *dev_series = nullptr;
+    if (!device_accessible(series)) {
+        IDTX_CUDA(cudaMalloc(&dev_series, (size_t)n_proc * T * sizeof(float)));
+        cudaError_t e = cudaMemcpyAsync(dev_series, series, (size_t)n_proc * T * sizeof(float),
+                                        cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) {
+            cudaFree(dev_series);
+            return fail(IDTX_ECUDA, "series copy failed: %s", cudaGetErrorString(e));
+        }
+        ser = (const float *)dev_series;
+    }
+    const int n_lags = max_lag - min_lag + 1;
+    const int n_cand_total = n_proc * n_lags;
+    int n_left = n_cand_total - std::max(0, std::min(max_lag, n_past) - min_lag + 1);
+    std::vector<int32_t> sel;
+    int rc = IDTX_OK;
+    for (int step = 0; step <= max_parents; ++step) {
+        if (n_left <= 0 || step == max_parents) break;
+        idtx_step r;
+        rc = idtx_mte_step(c, ser, n_proc, T, target, n_past, min_lag, max_lag, sel.data(),
+                           (int)sel.size(), step, s, &r, nullptr, stream);
+        if (rc != IDTX_OK) break;
+        steps_out[(*n_steps)++] = r;
+        if (!r.significant) break;
+        sel.push_back(r.cand);
+        parents_out[(*n_parents)++] = r.cand;
+        --n_left;
+    }
+    if (dev_series) {
+        cudaStreamSynchronize(st);
+        cudaFree(dev_series);
+    }
+    return rc;
+}
+
+}  // extern "C"

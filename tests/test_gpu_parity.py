@@ -1,0 +1,205 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Bar (the estimator's definition fixes it): eps_i bit-exact, every neighbour
+count exact, every estimate within 1e-10 nats (different fp64 summation order),
+greedy decisions identical.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1807_10459_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def idtx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1807_10459_gb300 as m
+    from paper_1807_10459_gb300 import build
+    build.build()
+    return m
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _oracle_all(x, y, z, k, S, seed):
+    """eps/counts/cmi of the original and every surrogate, by the oracle."""
+    n = x.shape[1]
+    eps, cnt, cmi = [], [], []
+    for s in range(S + 1):
+        xs = x if s == 0 else x[:, oracle.perm(seed, s - 1, n)]
+        e, a, b, c = oracle.ksg_counts(xs, y, z, k)
+        eps.append(e)
+        cnt.append(np.stack([a, b, c]))
+        cmi.append(oracle.cmi_ksg(xs, y, z, k))
+    return np.array(eps), np.array(cnt), np.array(cmi)
+
+
+def _check_problem(idtx, x, y, z, k, S, seed, on_device=True):
+    args = (_dev(x), _dev(y), None if z is None else _dev(z)) if on_device else (x, y, z)
+    cmi, eps, cnt = idtx.cmi_ksg(*args, k=k, n_surr=S, seed=seed, want_eps=True,
+                                 want_counts=True)
+    if on_device:
+        torch.cuda.synchronize()
+        cmi, eps, cnt = cmi.cpu().numpy(), eps.cpu().numpy(), cnt.cpu().numpy()
+    e_ref, c_ref, m_ref = _oracle_all(x, y, z, k, S, seed)
+    assert np.array_equal(eps, e_ref), "eps differs"
+    assert np.array_equal(cnt, c_ref), "counts differ"
+    assert np.max(np.abs(cmi - m_ref)) < TOL
+    return cmi
+
+
+def test_config1_full(idtx):
+    """Single problem N=1000, dims 1/1/2, k=4, 100 surrogates: every estimate."""
+    g = synth.gaussian_problem(1000, 1, 1, 2)
+    _check_problem(idtx, g.x, g.y, g.z, 4, 100, 20181028)
+
+
+@pytest.mark.parametrize("n", [2, 5, 127, 128, 129, 300, 515])
+def test_ragged_sizes(idtx, n):
+    g = synth.gaussian_problem(n, 1, 1, 2, seed=n)
+    _check_problem(idtx, g.x, g.y, g.z, min(4, n - 1), 3, 7)
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 0), (2, 1, 1), (1, 2, 3), (2, 2, 5), (1, 1, 7),
+                                  (1, 1, 10), (2, 2, 16), (3, 1, 2), (1, 4, 4), (4, 4, 16)])
+def test_dimension_buckets(idtx, dims):
+    dx, dy, dz = dims
+    g = synth.gaussian_problem(400, dx, dy, dz, seed=sum(dims))
+    _check_problem(idtx, g.x, g.y, g.z if dz else None, 4, 17, 3)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 5, 8, 15])
+def test_other_k(idtx, k):
+    g = synth.gaussian_problem(333, 1, 1, 2, seed=k)
+    _check_problem(idtx, g.x, g.y, g.z, k, 4, 11)
+
+
+def test_ties_and_duplicates(idtx):
+    rng = np.random.default_rng(5)
+    x = rng.integers(0, 4, (1, 260)).astype(np.float32)
+    y = rng.integers(0, 4, (1, 260)).astype(np.float32)
+    z = rng.integers(0, 3, (2, 260)).astype(np.float32)
+    for k in (1, 4, 8):
+        _check_problem(idtx, x, y, z, k, 3, 1)
+
+
+def test_host_pointers_match_device(idtx):
+    g = synth.gaussian_problem(700, 1, 1, 2, seed=3)
+    a = _check_problem(idtx, g.x, g.y, g.z, 4, 6, 5, on_device=False)
+    b = idtx.cmi_ksg(_dev(g.x), _dev(g.y), _dev(g.z), k=4, n_surr=6, seed=5).cpu().numpy()
+    assert np.array_equal(a, b)
+
+
+def test_deterministic(idtx):
+    g = synth.gaussian_problem(2000, 1, 1, 3, seed=9)
+    a = idtx.cmi_ksg(_dev(g.x), _dev(g.y), _dev(g.z), k=4, n_surr=40, seed=1).cpu().numpy()
+    b = idtx.cmi_ksg(_dev(g.x), _dev(g.y), _dev(g.z), k=4, n_surr=40, seed=1).cpu().numpy()
+    assert np.array_equal(a, b)
+
+
+def test_nonfinite_input_is_rejected_and_context_survives(idtx):
+    g = synth.gaussian_problem(200, 1, 1, 2, seed=4)
+    bad = g.z.copy()
+    bad[1, 17] = np.nan
+    with pytest.raises(idtx.IdtxError) as ei:
+        idtx.cmi_ksg(_dev(g.x), _dev(g.y), _dev(bad), k=4, n_surr=2, seed=1)
+    assert ei.value.code == idtx.IDTX_EINVAL
+    with pytest.raises(idtx.IdtxError):
+        idtx.cmi_ksg(_dev(g.x), _dev(g.y), _dev(g.z), k=200, n_surr=2, seed=1)
+    _check_problem(idtx, g.x, g.y, g.z, 4, 2, 1)
+
+
+def test_batch_uneven(idtx):
+    probs = synth.batch_problems(n_probs=6, n_min=150, n_max=900, n_surr=5, dz_max=8, seed=77)
+    out = idtx.cmi_batch([dict(x=_dev(p.x), y=_dev(p.y), z=_dev(p.z), n_surr=p.n_surr,
+                               seed=p.seed) for p in probs], k=4)
+    for p, o in zip(probs, out):
+        ref = oracle.cmi_surrogates(p.x, p.y, p.z, 4, p.n_surr, p.seed)
+        assert np.max(np.abs(o.cpu().numpy() - ref)) < TOL
+
+
+def test_greedy_step_matches_oracle(idtx):
+    net = synth.var_network(n_nodes=5, order=3, T=700, density=0.4, weight=0.6, seed=21)
+    S = 20
+    ref = oracle.select_target(net.series, 0, n_past=2, min_lag=1, max_lag=3, k=4, n_surr=S,
+                               alpha=0.05, seed=17, max_parents=1, want_first_step=True)
+    (cand, sig, stat, pval), est = idtx.mte_step(_dev(net.series), 0, 2, 1, 3, (), 0, k=4,
+                                                 n_surr=S, alpha=0.05, seed=17,
+                                                 want_estimates=True)
+    alive = ~np.isnan(ref["first_step"][:, 0])
+    assert np.array_equal(alive, ~np.isnan(est[:, 0]))
+    assert np.max(np.abs(est[alive] - ref["first_step"][alive])) < TOL
+    rc, rsig, rstat, rp = ref["steps"][0]
+    assert (cand, sig, pval) == (rc, rsig, rp)
+    assert abs(stat - rstat) < TOL
+
+
+def test_greedy_selection_matches_oracle(idtx):
+    net = synth.var_network(n_nodes=4, order=2, T=600, density=0.5, weight=0.8, seed=8)
+    for target in range(2):
+        ref = oracle.select_target(net.series, target, n_past=1, min_lag=1, max_lag=2, k=4,
+                                   n_surr=20, alpha=0.05, seed=5, max_parents=4)
+        got = idtx.mte_select_target(net.series, target, 1, 1, 2, k=4, n_surr=20, alpha=0.05,
+                                     seed=5, max_parents=4)
+        assert got["parents"] == ref["parents"]
+        assert [s[:2] for s in got["steps"]] == [s[:2] for s in ref["steps"]]
+        assert [s[3] for s in got["steps"]] == [s[3] for s in ref["steps"]]
+        for a, b in zip(got["steps"], ref["steps"]):
+            assert abs(a[2] - b[2]) < TOL
+
+
+@pytest.mark.slow
+def test_config2_full_size_sampled(idtx):
+    """The benchmarked greedy step at full size (10-node VAR(5), T=10000, lags 1..5,
+    target history 3, k=4, 200 surrogates): gate and sampled estimates vs the oracle."""
+    net = synth.var_network()
+    S = 200
+    (cand, sig, stat, pval), est = idtx.mte_step(_dev(net.series), 0, 3, 1, 5, (), 0, k=4,
+                                                 n_surr=S, alpha=0.05, seed=20181029,
+                                                 want_estimates=True)
+    alive = np.flatnonzero(~np.isnan(est[:, 0]))
+    assert len(alive) == 47
+    L, T = 5, net.series.shape[1]
+    y = net.series[0, L:]
+    z = np.stack([net.series[0, L - lag:T - lag] for lag in (1, 2, 3)])
+    rng = np.random.default_rng(0)
+    for c in rng.choice(alive, 3, replace=False):
+        p, lag = divmod(int(c), 5)
+        lag += 1
+        xc = net.series[p, L - lag:T - lag][None, :]
+        for s in [0, int(rng.integers(1, S + 1))]:
+            xs = xc if s == 0 else xc[:, oracle.perm(20181029, (int(c) << 24) | (s - 1), T - L)]
+            assert abs(est[c, s] - oracle.cmi_ksg(xs, y, z, 4)) < TOL
+    # the gate from the returned estimates (same decision rule)
+    t_obs = est[alive, 0].max()
+    assert cand == alive[np.argmax(est[alive, 0])] and stat == t_obs
+    assert pval == np.count_nonzero(est[alive, 1:].max(axis=0) >= t_obs) / S
+
+
+@pytest.mark.slow
+def test_large_n_sampled_queries(idtx):
+    """N = 100000 logistic-map problem, joint dim 12: sampled queries of the
+    original and one surrogate, eps and counts exact."""
+    x, y, z = synth.logistic_problem(1, 1, 10)
+    n = x.shape[1]
+    S, seed = 2, 4
+    cmi, eps, cnt = idtx.cmi_ksg(_dev(x), _dev(y), _dev(z), k=4, n_surr=S, seed=seed,
+                                 want_eps=True, want_counts=True)
+    eps, cnt = eps.cpu().numpy(), cnt.cpu().numpy()
+    idx = np.random.default_rng(1).choice(n, 64, replace=False)
+    for s in (0, 2):
+        xs = x if s == 0 else x[:, oracle.perm(seed, s - 1, n)]
+        e, a, b, c = oracle.ksg_counts_at(xs, y, z, 4, idx)
+        assert np.array_equal(eps[s, idx], e)
+        assert np.array_equal(cnt[s, 0, idx], a)
+        assert np.array_equal(cnt[s, 1, idx], b)
+        assert np.array_equal(cnt[s, 2, idx], c)
