@@ -189,6 +189,32 @@ int idtx_mte_select_target(idtx_ctx *ctx, const float *series, int n_proc, int64
                            int max_parents, int32_t *parents_out, int *n_parents,
                            idtx_step *steps_out, int *n_steps, void *stream);
 
+/* Allocation-free estimate (no counterpart in the paper; it exists for
+ * callers that cannot allocate device memory -- code whose memory pool owns
+ * the device, paths where a cudaMalloc would synchronise the device, or
+ * services that must not grow their footprint after start-up).
+ *
+ * Same estimate and surrogates as idtx_cmi_ksg (same kernels, same results),
+ * without a context: it runs on the current CUDA device and takes all its
+ * scratch from one fixed array of IDTX_NOALLOC_SCRATCH_BYTES bytes in device
+ * memory that the library declares at file scope.  Every GPU that loads the
+ * library holds that array until the process exits.
+ *   - x, y, z and cmi_out must be device memory; cmi_out [1+n_surr] fp64.
+ *   - 0 <= settings->n_surr <= IDTX_NOALLOC_MAX_SURR; a problem whose scratch
+ *     does not fit in the array returns IDTX_EINVAL with the bytes it needs.
+ *   - It calls no cudaMalloc, cudaFree or other allocating routine.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - All calls share the one array, which keeps the previous call's
+ *     contents: calls that overlap on the GPU (other threads, other streams)
+ *     race with each other and must be serialised by the caller.
+ *   - Synchronises `stream` before returning. */
+#define IDTX_NOALLOC_SCRATCH_BYTES (16u << 20)
+#define IDTX_NOALLOC_MAX_SURR 1000
+int idtx_cmi_ksg_noalloc(const float *x, int dx, const float *y, int dy, const float *z, int dz,
+                         int64_t n, int64_t ld, const idtx_settings *settings, double *cmi_out,
+                         void *stream);
+
 #ifdef __cplusplus
 }
 #endif

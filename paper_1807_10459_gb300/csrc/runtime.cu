@@ -18,6 +18,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -987,3 +988,222 @@ int idtx_mte_select_target(idtx_ctx *c, const float *series, int n_proc, int64_t
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ allocation-free variant
+//
+// For callers that cannot allocate device memory: code running where the
+// caller's memory pool owns the device and forbids other allocations, code
+// on a path where a cudaMalloc would synchronise the device (and so stall
+// other work), or long-running services that must not grow their footprint
+// after start-up.  It runs the same kernels as idtx_cmi_ksg, with every
+// scratch buffer carved out of one file-scope device array instead.
+namespace {
+
+constexpr size_t kNoAllocBytes = IDTX_NOALLOC_SCRATCH_BYTES;
+constexpr size_t kNoAllocDescBytes = 64 * 1024;  // descriptor block at the start
+
+// The shared scratch: present on every device that loads this library, until
+// the process exits.  Host code must not use the name as an address.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+void *g_noalloc_ptr[kMaxDevices] = {};  // device address of the array, per device
+std::mutex g_noalloc_mu;
+
+// Once per device, with that device current: resolve the array's address.
+int noalloc_scratch(int device, unsigned char **out)
+{
+    if (device < 0 || device >= kMaxDevices) return fail(IDTX_EINVAL, "device %d", device);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(IDTX_ECUDA, "cudaGetSymbolAddress of the scratch array failed: %s",
+                        cudaGetErrorString(e));
+        g_noalloc_ptr[device] = p;
+    }
+    *out = (unsigned char *)g_noalloc_ptr[device];
+    return IDTX_OK;
+}
+
+const KsgVariant *noalloc_variant(int dx, int dy, int dz, int k)
+{
+    static KsgVariant table[64];
+    static int n_table = 0;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        int n = 0;
+        n += ksg_variants_d11(table + n);
+        n += ksg_variants_d12(table + n);
+        n += ksg_variants_d21(table + n);
+        n += ksg_variants_d22(table + n);
+        n += ksg_variants_generic(table + n);
+        n_table = n;
+    });
+    const int dze = std::max(dz, 1);
+    if (k == 4 && dx <= 2 && dy <= 2) {
+        int zb = 0;
+        for (int b : kZBuckets)
+            if (b >= dze) {
+                zb = b;
+                break;
+            }
+        for (int i = 0; i < n_table; ++i) {
+            const KsgVariant &v = table[i];
+            if (v.exact && v.k1 == 5 && v.dx == dx && v.dy == dy && v.dz == zb) return &v;
+        }
+    }
+    for (int i = 0; i < n_table; ++i) {
+        const KsgVariant &v = table[i];
+        if (!v.exact && v.dx >= dx && v.dy >= dy && v.dz >= dze && v.k1 > k) return &v;
+    }
+    return nullptr;
+}
+
+}  // namespace
+
+extern "C" int idtx_cmi_ksg_noalloc(const float *x, int dx, const float *y, int dy,
+                                    const float *z, int dz, int64_t n, int64_t ld,
+                                    const idtx_settings *s, double *cmi_out, void *stream)
+{
+    if (!s || !cmi_out) return fail(IDTX_EINVAL, "settings or cmi_out is NULL");
+    if (dx < 1 || dx > IDTX_MAX_DX || dy < 1 || dy > IDTX_MAX_DY || dz < 0 || dz > IDTX_MAX_DZ)
+        return fail(IDTX_EINVAL, "dims out of range (dx=%d dy=%d dz=%d)", dx, dy, dz);
+    if (n < 2 || n > IDTX_MAX_N || ld < n)
+        return fail(IDTX_EINVAL, "bad n=%lld / ld=%lld", (long long)n, (long long)ld);
+    if (s->k < 1 || s->k > IDTX_MAX_K || s->k > n - 1)
+        return fail(IDTX_EINVAL, "k=%d out of range for n=%lld", s->k, (long long)n);
+    if (s->n_surr < 0 || s->n_surr > IDTX_NOALLOC_MAX_SURR)
+        return fail(IDTX_EINVAL, "n_surr=%d outside [0, %d]", s->n_surr, IDTX_NOALLOC_MAX_SURR);
+    if (!x || !y || (dz > 0 && !z)) return fail(IDTX_EINVAL, "NULL input column");
+    if (!device_accessible(x) || !device_accessible(y) || (dz > 0 && !device_accessible(z)) ||
+        !device_accessible(cmi_out))
+        return fail(IDTX_EINVAL, "inputs and cmi_out must be device memory");
+    const KsgVariant *v = noalloc_variant(dx, dy, dz, s->k);
+    if (!v) return fail(IDTX_EINVAL, "no kernel for dx=%d dy=%d dz=%d k=%d", dx, dy, dz, s->k);
+
+    // Carve the scratch: [descriptors | err | psi | sh | xi | perm | partial].
+    const int n_jobs = 1 + s->n_surr;
+    const int n_slots = s->n_surr;
+    const int64_t n_pad = (n + kTQ - 1) / kTQ * kTQ;
+    const int n_qt = (int)(n_pad / kTQ);
+    const int n_groups = (n_jobs + v->gb - 1) / v->gb;
+    size_t off = kNoAllocDescBytes;
+    auto take = [&](size_t bytes) {
+        size_t at = off;
+        off = align_up(off + bytes, 256);
+        return at;
+    };
+    const size_t at_err = take(sizeof(int));
+    const size_t at_psi = take((size_t)(std::max<int64_t>(n, s->k) + 2) * sizeof(double));
+    const size_t at_sh = take((size_t)n_pad * v->dsp * sizeof(float));
+    const size_t at_xi = take((size_t)n_groups * n_pad * v->gb * v->dx * sizeof(float));
+    const size_t at_perm = take((size_t)n_slots * n * sizeof(int32_t));
+    const size_t at_partial = take((size_t)n_jobs * n_qt * sizeof(double));
+    if (off > kNoAllocBytes)
+        return fail(IDTX_EINVAL,
+                    "problem needs %zu bytes of scratch; the allocation-free entry point has "
+                    "%zu (use idtx_cmi_ksg)",
+                    off, kNoAllocBytes);
+
+    int device = 0;
+    IDTX_CUDA(cudaGetDevice(&device));
+    unsigned char *base = nullptr;
+    IDTX_TRY(noalloc_scratch(device, &base));
+    cudaStream_t st = (cudaStream_t)stream;
+
+    // Descriptors, built in a fixed host block (no allocation) and copied in.
+    unsigned char host_desc[kNoAllocDescBytes];
+    size_t doff = 0;
+    auto put = [&](const void *src, size_t bytes) {
+        doff = align_up(doff, 16);
+        const size_t at = doff;
+        memcpy(host_desc + at, src, bytes);
+        doff += bytes;
+        return at;
+    };
+    Col xc[IDTX_MAX_DX], yc[IDTX_MAX_DY], zc[IDTX_MAX_DZ > 0 ? IDTX_MAX_DZ : 1];
+    for (int d = 0; d < dx; ++d) xc[d] = Col{x + d * ld, 0};
+    for (int d = 0; d < dy; ++d) yc[d] = Col{y + d * ld, 0};
+    for (int d = 0; d < dz; ++d) zc[d] = Col{z + d * ld, 0};
+    const size_t o_x = put(xc, sizeof(Col) * dx);
+    const size_t o_y = put(yc, sizeof(Col) * dy);
+    const size_t o_z = put(zc, sizeof(Col) * std::max(dz, 1));
+    doff = align_up(doff, 16);
+    const size_t o_jobs = doff;
+    for (int j = 0; j < n_jobs; ++j) {
+        const Job jb{0, j - 1};
+        memcpy(host_desc + doff, &jb, sizeof(Job));
+        doff += sizeof(Job);
+    }
+    doff = align_up(doff, 16);
+    const size_t o_streams = doff;
+    for (int sl = 0; sl < n_slots; ++sl) {
+        const uint64_t v64 = (uint64_t)sl;
+        memcpy(host_desc + doff, &v64, sizeof(uint64_t));
+        doff += sizeof(uint64_t);
+    }
+    const size_t o_seeds = doff;
+    for (int sl = 0; sl < n_slots; ++sl) {
+        memcpy(host_desc + doff, &s->seed, sizeof(uint64_t));
+        doff += sizeof(uint64_t);
+    }
+    if (doff > kNoAllocDescBytes) return fail(IDTX_EINTERNAL, "descriptor block overflow");
+    IDTX_CUDA(cudaMemcpyAsync(base, host_desc, doff, cudaMemcpyHostToDevice, st));
+
+    int *err = (int *)(base + at_err);
+    double *psi = (double *)(base + at_psi);
+    float *sh = (float *)(base + at_sh);
+    float *xi = (float *)(base + at_xi);
+    int32_t *perm = (int32_t *)(base + at_perm);
+    double *partial = (double *)(base + at_partial);
+    const int64_t psi_n = std::max<int64_t>(n, s->k) + 1;
+
+    // The error word must start at zero; every other region is fully written
+    // before it is read, so the previous call's contents do not matter.
+    IDTX_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+    k_psi_table<<<grid_for(psi_n + 1, 256), 256, 0, st>>>(psi, psi_n);
+    IDTX_CUDA(cudaGetLastError());
+    k_pack_shared<<<grid_for(n_pad * v->dsp, 256), 256, 0, st>>>(
+        (const Col *)(base + o_z), dz, v->dz, (const Col *)(base + o_y), dy, v->dy, v->dsp, n,
+        n_pad, sh, err);
+    IDTX_CUDA(cudaGetLastError());
+    if (n_slots > 0) {
+        k_iota<<<grid_for((int64_t)n_slots * n, 256), 256, 0, st>>>(perm, n_slots, n);
+        IDTX_CUDA(cudaGetLastError());
+        k_fisher_yates<<<(n_slots + 31) / 32, 32, 0, st>>>(
+            perm, (const uint64_t *)(base + o_streams), (const uint64_t *)(base + o_seeds),
+            n_slots, n);
+        IDTX_CUDA(cudaGetLastError());
+    }
+    k_gather_x<<<grid_for((int64_t)n_groups * n_pad * v->gb * v->dx, 256), 256, 0, st>>>(
+        (const Col *)(base + o_x), dx, v->dx, (const Job *)(base + o_jobs), n_jobs, perm, n,
+        n_pad, v->gb, n_groups, xi, err);
+    IDTX_CUDA(cudaGetLastError());
+    KsgLaunch a;
+    a.sh = sh;
+    a.xi = xi;
+    a.psi = psi;
+    a.partial = partial;
+    a.eps_out = nullptr;
+    a.cnt_out = nullptr;
+    a.err = err;
+    a.n = n;
+    a.n_pad = n_pad;
+    a.n_jobs = n_jobs;
+    a.n_qt = n_qt;
+    a.k = s->k;
+    a.timeout_ns = timeout_of(s);
+    IDTX_CUDA(v->fn(a, n_groups, st));
+    k_finalize<<<(n_jobs + 127) / 128, 128, 0, st>>>(partial, n_jobs, n_qt, psi, s->k, n,
+                                                      cmi_out);
+    IDTX_CUDA(cudaGetLastError());
+    int h_err = 0;
+    IDTX_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    IDTX_CUDA(cudaStreamSynchronize(st));
+    if (h_err & kErrNonFinite) return fail(IDTX_EINVAL, "input contains NaN or Inf");
+    if (h_err & kErrTimeout) return fail(IDTX_ETIMEOUT, "a bounded device wait ran out");
+    if (h_err) return fail(IDTX_EINTERNAL, "device error word 0x%x", h_err);
+    return IDTX_OK;
+}
