@@ -134,6 +134,82 @@ __device__ __forceinline__ float select_kth(const float (&h)[K1], int k)
     return v;
 }
 
+// Reference row jj of a staged sh tile (DSP floats, float4 aligned).
+template <int DSP>
+__device__ __forceinline__ void load_row(const float *rs, int jj, float (&r)[DSP])
+{
+#pragma unroll
+    for (int m = 0; m < DSP / 4; ++m) {
+        const float4 v = reinterpret_cast<const float4 *>(rs + jj * DSP)[m];
+        r[4 * m + 0] = v.x;
+        r[4 * m + 1] = v.y;
+        r[4 * m + 2] = v.z;
+        r[4 * m + 3] = v.w;
+    }
+}
+
+// X values of the GB jobs at reference jj of a staged xi tile.
+template <int XW>
+__device__ __forceinline__ void load_xrow(const float *rx, int jj, float (&xv)[XW])
+{
+#pragma unroll
+    for (int m = 0; m < XW / 4; ++m) {
+        const float4 v = reinterpret_cast<const float4 *>(rx + jj * XW)[m];
+        xv[4 * m + 0] = v.x;
+        xv[4 * m + 1] = v.y;
+        xv[4 * m + 2] = v.z;
+        xv[4 * m + 3] = v.w;
+    }
+}
+
+// 0xffffffff if a < b else 0 (IEEE compare; false for NaN).
+__device__ __forceinline__ uint32_t lt_mask(float a, float b)
+{
+    uint32_t r;
+    asm("set.lt.u32.f32 %0, %1, %2;" : "=r"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+// Bit jj of (lo | hi << 64) is set iff the max-norm distance over the first
+// ND coordinates between the query and reference jj of the tile is < bound.
+template <int ND, int DSP>
+__device__ __forceinline__ void tile_mask(const float *rs, const float *q, float bound,
+                                          uint64_t &lo, uint64_t &hi)
+{
+    uint32_t w[kTJ / 32];
+#pragma unroll
+    for (int word = 0; word < kTJ / 32; ++word) {
+        uint32_t m = 0;
+#pragma unroll 8
+        for (int b = 31; b >= 0; --b) {
+            float r[DSP];
+            load_row<DSP>(rs, word * 32 + b, r);
+            float d = fabsf(q[0] - r[0]);
+#pragma unroll
+            for (int t = 1; t < ND; ++t) d = fmaxf(d, fabsf(q[t] - r[t]));
+            m = m + m - lt_mask(d, bound);  // shift in one bit: 2m + (d < bound)
+        }
+        w[word] = m;
+    }
+    static_assert(kTJ == 128, "two 64-bit masks per tile");
+    lo = (uint64_t)w[0] | ((uint64_t)w[1] << 32);
+    hi = (uint64_t)w[2] | ((uint64_t)w[3] << 32);
+}
+
+// Pop the lowest set reference index of (lo, hi).
+__device__ __forceinline__ int next_ref(uint64_t &lo, uint64_t &hi)
+{
+    const bool use_lo = lo != 0;
+    const uint64_t m = use_lo ? lo : hi;
+    const int jj = (__ffsll((long long)m) - 1) + (use_lo ? 0 : 64);
+    const uint64_t rest = m & (m - 1);
+    if (use_lo)
+        lo = rest;
+    else
+        hi = rest;
+    return jj;
+}
+
 template <int DX, int DY, int DZ, int K1, bool EXACT, int GB>
 struct KsgShape {
     static constexpr int DS = DZ + DY;
@@ -242,49 +318,37 @@ __global__ void __launch_bounds__(kTQ) ksg_fused_kernel(const KsgLaunch a)
             wait_tile(it);
             const float *rs = s_sh + (it & 1) * kTJ * DSP;
             const float *rx = s_x + (it & 1) * kTJ * XW;
-#pragma unroll 1
-            for (int jj = 0; jj < kTJ; ++jj) {
+            // Phase 1: which references of the tile pass the shared bound.
+            uint64_t lo, hi;
+            tile_mask<DS, DSP>(rs, q, bound, lo, hi);
+            // Phase 2: this thread's passing references only (warps iterate
+            // max-over-lanes times instead of union-over-lanes).
+            while (lo | hi) {
+                const int jj = next_ref(lo, hi);
                 float r[DSP];
-#pragma unroll
-                for (int m = 0; m < DSP / 4; ++m) {
-                    const float4 v = reinterpret_cast<const float4 *>(rs + jj * DSP)[m];
-                    r[4 * m + 0] = v.x;
-                    r[4 * m + 1] = v.y;
-                    r[4 * m + 2] = v.z;
-                    r[4 * m + 3] = v.w;
-                }
+                load_row<DSP>(rs, jj, r);
                 float dyz = fabsf(q[0] - r[0]);
 #pragma unroll
                 for (int d = 1; d < DS; ++d) dyz = fmaxf(dyz, fabsf(q[d] - r[d]));
-                if (dyz < bound) {
-                    float xv[XW];
+                float xv[XW];
+                load_xrow<XW>(rx, jj, xv);
 #pragma unroll
-                    for (int m = 0; m < XW / 4; ++m) {
-                        const float4 v = reinterpret_cast<const float4 *>(rx + jj * XW)[m];
-                        xv[4 * m + 0] = v.x;
-                        xv[4 * m + 1] = v.y;
-                        xv[4 * m + 2] = v.z;
-                        xv[4 * m + 3] = v.w;
-                    }
+                for (int g = 0; g < GB; ++g) {
+                    float dxg = fabsf(xq[g][0] - xv[g * DX]);
 #pragma unroll
-                    for (int g = 0; g < GB; ++g) {
-                        float dxg = fabsf(xq[g][0] - xv[g * DX]);
-#pragma unroll
-                        for (int d = 1; d < DX; ++d)
-                            dxg = fmaxf(dxg, fabsf(xq[g][d] - xv[g * DX + d]));
-                        const float dd = fmaxf(dxg, dyz);
-                        const float th = EXACT ? h[g][K1 - 1] : kth[g];
-                        if (dd < th) {
-                            sorted_insert<K1>(h[g], dd);
-                            if (!EXACT) kth[g] = select_kth<K1>(h[g], a.k);
-                        }
+                    for (int d = 1; d < DX; ++d) dxg = fmaxf(dxg, fabsf(xq[g][d] - xv[g * DX + d]));
+                    const float dd = fmaxf(dxg, dyz);
+                    const float th = EXACT ? h[g][K1 - 1] : kth[g];
+                    if (dd < th) {
+                        sorted_insert<K1>(h[g], dd);
+                        if (!EXACT) kth[g] = select_kth<K1>(h[g], a.k);
                     }
                 }
             }
-            float b = EXACT ? h[0][K1 - 1] : kth[0];
+            float bb = EXACT ? h[0][K1 - 1] : kth[0];
 #pragma unroll
-            for (int g = 1; g < GB; ++g) b = fmaxf(b, EXACT ? h[g][K1 - 1] : kth[g]);
-            bound = b;
+            for (int g = 1; g < GB; ++g) bb = fmaxf(bb, EXACT ? h[g][K1 - 1] : kth[g]);
+            bound = bb;
             __syncthreads();
             if (s_abort) break;
             release_tile(it);
@@ -308,43 +372,28 @@ __global__ void __launch_bounds__(kTQ) ksg_fused_kernel(const KsgLaunch a)
             wait_tile(it);
             const float *rs = s_sh + (it & 1) * kTJ * DSP;
             const float *rx = s_x + (it & 1) * kTJ * XW;
-#pragma unroll 1
-            for (int jj = 0; jj < kTJ; ++jj) {
+            uint64_t lo, hi;
+            tile_mask<DZ, DSP>(rs, q, bound, lo, hi);  // Z distance < max eps
+            while (lo | hi) {
+                const int jj = next_ref(lo, hi);
                 float r[DSP];
-#pragma unroll
-                for (int m = 0; m < DSP / 4; ++m) {
-                    const float4 v = reinterpret_cast<const float4 *>(rs + jj * DSP)[m];
-                    r[4 * m + 0] = v.x;
-                    r[4 * m + 1] = v.y;
-                    r[4 * m + 2] = v.z;
-                    r[4 * m + 3] = v.w;
-                }
+                load_row<DSP>(rs, jj, r);
                 float dz = fabsf(q[0] - r[0]);
 #pragma unroll
                 for (int d = 1; d < DZ; ++d) dz = fmaxf(dz, fabsf(q[d] - r[d]));
-                if (dz < bound) {
-                    float dyz = dz;
+                float dyz = dz;
 #pragma unroll
-                    for (int d = DZ; d < DS; ++d) dyz = fmaxf(dyz, fabsf(q[d] - r[d]));
-                    float xv[XW];
+                for (int d = DZ; d < DS; ++d) dyz = fmaxf(dyz, fabsf(q[d] - r[d]));
+                float xv[XW];
+                load_xrow<XW>(rx, jj, xv);
 #pragma unroll
-                    for (int m = 0; m < XW / 4; ++m) {
-                        const float4 v = reinterpret_cast<const float4 *>(rx + jj * XW)[m];
-                        xv[4 * m + 0] = v.x;
-                        xv[4 * m + 1] = v.y;
-                        xv[4 * m + 2] = v.z;
-                        xv[4 * m + 3] = v.w;
-                    }
+                for (int g = 0; g < GB; ++g) {
+                    float dxg = fabsf(xq[g][0] - xv[g * DX]);
 #pragma unroll
-                    for (int g = 0; g < GB; ++g) {
-                        float dxg = fabsf(xq[g][0] - xv[g * DX]);
-#pragma unroll
-                        for (int d = 1; d < DX; ++d)
-                            dxg = fmaxf(dxg, fabsf(xq[g][d] - xv[g * DX + d]));
-                        cz[g] += dz < e[g] ? 1 : 0;
-                        cyz[g] += dyz < e[g] ? 1 : 0;
-                        cxz[g] += fmaxf(dxg, dz) < e[g] ? 1 : 0;
-                    }
+                    for (int d = 1; d < DX; ++d) dxg = fmaxf(dxg, fabsf(xq[g][d] - xv[g * DX + d]));
+                    cz[g] += dz < e[g] ? 1 : 0;
+                    cyz[g] += dyz < e[g] ? 1 : 0;
+                    cxz[g] += fmaxf(dxg, dz) < e[g] ? 1 : 0;
                 }
             }
             __syncthreads();
