@@ -255,7 +255,15 @@ def run_ours(args):
                 "kernel": "ksg_fused_kernel<1,1,4,5,true,16>",
                 "peak_basis": f"{N_SMS} SMs x {LANES_PER_SM} lanes x median SM clock "
                               f"{sm_mhz:.0f} MHz under load (issue-slot peak)",
-                "fused_share_of_step": st["fused_ms"] / ms if ms else None}
+                "fused_share_of_step": st["fused_ms"] / ms if ms else None,
+                "scanned_fraction_of_exhaustive":
+                    ((st["scanned_a"] + st["scanned_b"]) / st["exhaustive_pairs"])
+                    if st["exhaustive_pairs"] else None,
+                "work_per_step": {k: st[k] / args.steps for k in
+                                  ("scanned_a", "passed_a", "scanned_b", "passed_b")},
+                "ops_basis": "lane-ops the kernel's algorithm needs for the tiles it scans: "
+                             "shared scan per (query, reference, job group) plus per-job work "
+                             "for pairs passing the shared bound (counted in-kernel)"}
     cpu = cpu_oracle_sample(net.series, target, budget_s=12.0) if world == 1 else None
     line = {"metric": METRIC, "value": value, "unit": "estimates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,

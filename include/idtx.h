@@ -101,14 +101,23 @@ int idtx_version(void);
  * only: its launches, its device time (CUDA events recorded on the caller's
  * stream around each launch, only while profiling is enabled), and its
  * algorithmic lane operations: for every (query, reference sample, group of
- * jobs sharing Y and Z), 2(dy+dz')+1 operations in the neighbour pass and
- * 2dz'+1 in the count pass (one subtraction and one max-abs per dimension
- * plus the bound compare; dz' = max(dz, 1)). */
+ * jobs sharing Y and Z) that the kernel scans, 2(dy+dz')+1 operations in the
+ * neighbour pass and 2dz'+1 in the count pass (one subtraction and one
+ * max-abs per dimension plus the bound compare; dz' = max(dz, 1)); for
+ * every scanned pair that passes the pass's shared bound, 2dx+1 per job in
+ * the neighbour pass and 2dy + (2dx+7) per job in the count pass.
+ * scanned_a / scanned_b count the (query, reference, group) triples scanned
+ * by the neighbour / count pass, passed_a / passed_b those that passed the
+ * pass's shared bound; exhaustive_pairs what scanning every reference tile in
+ * both passes would have been (tiles whose bounding box is provably out of
+ * reach are skipped; results are identical either way). */
 typedef struct {
     int64_t kernel_launches;
     int64_t fused_launches;
     double fused_ms;
     double fused_lane_ops;
+    double scanned_a, passed_a, scanned_b, passed_b;
+    double exhaustive_pairs;
 } idtx_stats;
 
 /* Enable (1) or disable (0) event timing of the fused kernel. */

@@ -51,7 +51,10 @@ class Problem(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_int64), ("fused_launches", ctypes.c_int64),
-                ("fused_ms", ctypes.c_double), ("fused_lane_ops", ctypes.c_double)]
+                ("fused_ms", ctypes.c_double), ("fused_lane_ops", ctypes.c_double),
+                ("scanned_a", ctypes.c_double), ("passed_a", ctypes.c_double),
+                ("scanned_b", ctypes.c_double), ("passed_b", ctypes.c_double),
+                ("exhaustive_pairs", ctypes.c_double)]
 
 
 class Step(ctypes.Structure):
@@ -121,7 +124,9 @@ class Context:
         st = Stats()
         _check(load().idtx_ctx_get_stats(self.handle, ctypes.byref(st)))
         return dict(kernel_launches=st.kernel_launches, fused_launches=st.fused_launches,
-                    fused_ms=st.fused_ms, fused_lane_ops=st.fused_lane_ops)
+                    fused_ms=st.fused_ms, fused_lane_ops=st.fused_lane_ops,
+                    scanned_a=st.scanned_a, passed_a=st.passed_a, scanned_b=st.scanned_b,
+                    passed_b=st.passed_b, exhaustive_pairs=st.exhaustive_pairs)
 
     def reset_stats(self):
         _check(load().idtx_ctx_reset_stats(self.handle))

@@ -26,6 +26,11 @@ NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2"
                      "-I" + INCLUDE, "-I" + CSRC]
 
 
+def _extra_flags() -> list:
+    """Extra nvcc flags from IDTX_NVCC_FLAGS (launch-shape tuning knobs)."""
+    return os.environ.get("IDTX_NVCC_FLAGS", "").split()
+
+
 def nvcc() -> str:
     path = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
     if not os.path.exists(path):
@@ -43,7 +48,7 @@ def _inputs() -> list:
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or _extra_flags():
         return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(p) <= t for p in _inputs())
@@ -59,7 +64,7 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [cc] + NVCC_FLAGS + ["-c", src, "-o", obj]
+        cmd = [cc] + NVCC_FLAGS + _extra_flags() + ["-c", src, "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)

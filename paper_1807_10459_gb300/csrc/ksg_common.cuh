@@ -1,11 +1,16 @@
 // ksg_common.cuh -- internal declarations shared by the library's translation units.
 //
 // Layouts in device memory (all fp32 unless stated):
-//   sh   [n_pad][dsp]        "shared" coordinates of every sample, the same for all
-//                            jobs of a group: DZ z-dimensions, then DY y-dimensions,
-//                            then unused padding up to dsp (a multiple of 4).
-//                            Missing z/y dimensions of a bucket are 0; rows
-//                            j >= n (padding samples) are +inf in every column.
+//   sh   [n_tiles][kTJ+2][dsp]  "shared" coordinates of every sample, the same for
+//                            all jobs of a group, in tiles of kTJ samples: rows
+//                            0..kTJ-1 hold DZ z-dimensions, then DY y-dimensions,
+//                            then unused padding up to dsp (a multiple of 4);
+//                            row kTJ holds the tile's per-dimension minimum and
+//                            row kTJ+1 its maximum over its real samples.
+//                            Missing z/y dimensions of a bucket are 0; samples
+//                            j >= n (padding) are +inf in every column.
+//   Samples are stored in the order `order` (sorted position m holds original
+//   sample order[m]); without a sort order is the identity.
 //   xi   [n_groups][n_pad][GB*DX]
 //                            per-job X values, GB jobs interleaved per sample:
 //                            element (j, g, d) = X_job[d][pi_job(j)], +inf for j >= n.
@@ -20,7 +25,7 @@
 
 namespace idtx {
 
-constexpr int kTQ = 128;  // queries per CTA (one per thread)
+constexpr int kTQ = 128;  // sample padding granularity (= kTJ)
 constexpr int kTJ = 128;  // reference samples per staged tile
 
 // Device error word bits.
@@ -30,13 +35,23 @@ enum : int {
     kErrInternal = 4,   // an internal check failed
 };
 
+constexpr int kTileRows = kTJ + 2;  // samples + bounding box rows
+
+// Work counters written by the fused kernel (per launch, summed over CTAs):
+//   [0] (query, reference) pairs scanned by the neighbour pass,
+//   [1] pairs that passed its shared bound (per-job work done),
+//   [2] pairs scanned by the count pass, [3] pairs that passed its bound.
+constexpr int kNumWork = 4;
+
 struct KsgLaunch {
     const float *sh;
     const float *xi;
     const double *psi;
     double *partial;
-    float *eps_out;      // nullable, [n_jobs][n]
-    int32_t *cnt_out;    // nullable, [n_jobs][3][n]: n_xz, n_yz, n_z
+    float *eps_out;      // nullable, [n_jobs][n] in original sample order
+    int32_t *cnt_out;    // nullable, [n_jobs][3][n]: n_xz, n_yz, n_z, original order
+    const int32_t *order;  // nullable: original index of sorted position m
+    unsigned long long *work;  // nullable, [kNumWork]
     int *err;
     int64_t n, n_pad;
     int n_jobs, n_qt, k;
@@ -50,10 +65,17 @@ struct KsgVariant {
     int dx, dy, dz;   // bucket dimensions (inputs are zero-padded up to them)
     int k1;           // heap length (k+1 when exact, else an upper bound)
     int exact;        // 1: only k == k1-1
-    int gb;           // jobs per CTA
+    int gb;           // jobs per CTA (one per lane)
     int dsp;          // floats per row of sh
+    int qc;           // queries per CTA
     KsgLaunchFn fn;
 };
+
+// Radix sort of (key, index) pairs on the low end_bit key bits (sort.cu).
+// With tmp == nullptr only sets tmp_bytes.
+cudaError_t sort_pairs_u32(void *tmp, size_t &tmp_bytes, const uint32_t *keys_in,
+                           uint32_t *keys_out, const int32_t *vals_in, int32_t *vals_out, int n,
+                           int end_bit, cudaStream_t stream);
 
 // Registries filled by the instantiation units.
 int ksg_variants_d11(KsgVariant *out);

@@ -101,10 +101,13 @@ __global__ void k_psi_table(double *psi, int64_t n_max)
     }
 }
 
-// sh[j][d]: d < dzb -> z (0 beyond dz), then dyb y columns (0 beyond dy),
-// then 0 up to dsp.  Rows j >= n are +inf in the dzb + dyb used columns.
+// Sample rows of sh (tiled layout, see ksg_common.cuh): sorted position j
+// holds original sample order[j]; d < dzb -> z (0 beyond dz), then dyb y
+// columns (0 beyond dy), then 0 up to dsp.  Positions j >= n are +inf in
+// the dzb + dyb used columns.
 __global__ void k_pack_shared(const Col *zc, int dz, int dzb, const Col *yc, int dy, int dyb,
-                              int dsp, int64_t n, int64_t n_pad, float *sh, int *err)
+                              int dsp, int64_t n, int64_t n_pad, const int32_t *order, float *sh,
+                              int *err)
 {
     const int64_t total = n_pad * dsp;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
@@ -114,14 +117,108 @@ __global__ void k_pack_shared(const Col *zc, int dz, int dzb, const Col *yc, int
         float v = 0.0f;
         if (j >= n) {
             v = d < dzb + dyb ? INFINITY : 0.0f;
-        } else if (d < dzb) {
-            if (d < dz) v = zc[d].base[zc[d].off + j];
-        } else if (d < dzb + dyb) {
-            const int e = d - dzb;
-            if (e < dy) v = yc[e].base[yc[e].off + j];
+        } else {
+            const int64_t t = order ? (int64_t)order[j] : j;
+            if (d < dzb) {
+                if (d < dz) v = zc[d].base[zc[d].off + t];
+            } else if (d < dzb + dyb) {
+                const int e = d - dzb;
+                if (e < dy) v = yc[e].base[yc[e].off + t];
+            }
+            if (!isfinite(v)) atomicOr(err, kErrNonFinite);
         }
-        if (j < n && !isfinite(v)) atomicOr(err, kErrNonFinite);
-        sh[idx] = v;
+        const int64_t tile = j / kTJ, row = j - tile * kTJ;
+        sh[(tile * kTileRows + row) * dsp + d] = v;
+    }
+}
+
+// Rows kTJ and kTJ+1 of every sh tile: per-dimension minimum and maximum over
+// the tile's real samples (one block of kTJ threads per tile).
+__global__ void __launch_bounds__(kTJ) k_tile_boxes(float *sh, int dsp, int64_t n)
+{
+    __shared__ float s_mn[kTJ / 32], s_mx[kTJ / 32];
+    const int64_t tile = blockIdx.x;
+    const int r = threadIdx.x;
+    const bool real = tile * kTJ + r < n;
+    float *base = sh + tile * kTileRows * dsp;
+    for (int d = 0; d < dsp; ++d) {
+        const float v = base[r * dsp + d];
+        float mn = real ? v : INFINITY, mx = real ? v : -INFINITY;
+        for (int off = 16; off >= 1; off >>= 1) {
+            mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, off));
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        }
+        if ((r & 31) == 0) {
+            s_mn[r >> 5] = mn;
+            s_mx[r >> 5] = mx;
+        }
+        __syncthreads();
+        if (r == 0) {
+            for (int w = 1; w < kTJ / 32; ++w) {
+                mn = fminf(mn, s_mn[w]);
+                mx = fmaxf(mx, s_mx[w]);
+            }
+            base[kTJ * dsp + d] = mn;
+            base[(kTJ + 1) * dsp + d] = mx;
+        }
+        __syncthreads();
+    }
+}
+
+// Per shared column (z columns, then y columns): minimum and maximum over n
+// samples; one block per column.
+__global__ void k_minmax_cols(const Col *zc, int dz, const Col *yc, int dy, int64_t n, float *mm)
+{
+    __shared__ float s_mn[32], s_mx[32];
+    const int c = blockIdx.x;
+    const Col col = c < dz ? zc[c] : yc[c - dz];
+    float mn = INFINITY, mx = -INFINITY;
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+        const float v = col.base[col.off + j];
+        mn = fminf(mn, v);
+        mx = fmaxf(mx, v);
+    }
+    for (int off = 16; off >= 1; off >>= 1) {
+        mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, off));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        s_mn[threadIdx.x >> 5] = mn;
+        s_mx[threadIdx.x >> 5] = mx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            mn = fminf(mn, s_mn[w]);
+            mx = fmaxf(mx, s_mx[w]);
+        }
+        mm[2 * c] = mn;
+        mm[2 * c + 1] = mx;
+    }
+}
+
+// Morton (Z-order) key of every sample over its first nk shared coordinates,
+// each quantised to `bits` bits between the column's minimum and maximum;
+// idx[j] = j.  Only the order of the samples depends on it, never a result.
+__global__ void k_morton_keys(const Col *zc, int dz, const Col *yc, int nk, int bits, int64_t n,
+                              const float *mm, uint32_t *keys, int32_t *idx)
+{
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t qv[32];
+        const float scale = (float)(1u << bits);
+        for (int c = 0; c < nk; ++c) {
+            const Col col = c < dz ? zc[c] : yc[c - dz];
+            const float lo = mm[2 * c], hi = mm[2 * c + 1];
+            const float t = hi > lo ? (col.base[col.off + j] - lo) / (hi - lo) : 0.0f;
+            const float f = fminf(fmaxf(t * scale, 0.0f), scale - 1.0f);
+            qv[c] = (uint32_t)f;
+        }
+        uint32_t key = 0;
+        for (int b = bits - 1; b >= 0; --b)
+            for (int c = 0; c < nk; ++c) key = (key << 1) | ((qv[c] >> b) & 1u);
+        keys[j] = key;
+        idx[j] = (int32_t)j;
     }
 }
 
@@ -152,11 +249,11 @@ __global__ void k_fisher_yates(int32_t *perm, const uint64_t *streams, const uin
     }
 }
 
-// xi[grp][j][g*dxb + d] = X_job[d][pi_job(j)] (job = grp*gb + g; jobs past the
-// end repeat job 0), 0 for d >= dx, +inf for j >= n.
+// xi[grp][j][g*dxb + d] = X_job[d][pi_job(order[j])] (job = grp*gb + g; jobs
+// past the end repeat job 0), 0 for d >= dx, +inf for j >= n.
 __global__ void k_gather_x(const Col *xc, int dx, int dxb, const Job *jobs, int n_jobs,
                            const int32_t *perm, int64_t n, int64_t n_pad, int gb, int n_groups,
-                           float *xi, int *err)
+                           const int32_t *order, float *xi, int *err)
 {
     const int xw = gb * dxb;
     const int64_t per_grp = n_pad * xw;
@@ -177,7 +274,8 @@ __global__ void k_gather_x(const Col *xc, int dx, int dxb, const Job *jobs, int 
             v = 0.0f;
         } else {
             const Job jb = jobs[job];
-            const int64_t t = jb.slot < 0 ? j : (int64_t)perm[(int64_t)jb.slot * n + j];
+            const int64_t t0 = order ? (int64_t)order[j] : j;
+            const int64_t t = jb.slot < 0 ? t0 : (int64_t)perm[(int64_t)jb.slot * n + t0];
             const Col c = xc[(int64_t)jb.src * dx + d];
             v = c.base[c.off + t];
             if (!isfinite(v)) atomicOr(err, kErrNonFinite);
@@ -261,7 +359,17 @@ enum {
     B_EPS,
     B_CNT,
     B_STEP,
+    B_ORDER,    // sample order along the Morton curve, sort keys, column ranges
+    B_SORT,     // radix-sort temporary storage
+    B_WORK,     // fused-kernel work counters, kNumWork per group
     kNumBufs
+};
+
+// Shape of one fused launch, to turn its work counters into operations.
+struct WorkShape {
+    int dx, dy, dz_eff, gb;
+    double job_frac;  // real jobs / (groups * gb)
+    double exhaustive_pairs;
 };
 
 struct idtx_ctx {
@@ -278,6 +386,9 @@ struct idtx_ctx {
     idtx_stats stats = {};
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;  // fused launches of this call
     std::vector<cudaEvent_t> event_pool;
+    std::vector<WorkShape> call_shapes;  // launches of the current call, by work slot
+    unsigned long long *h_work = nullptr;  // pinned copy of the counters
+    size_t h_work_cap = 0;
 };
 
 namespace {
@@ -377,6 +488,8 @@ struct Group {
     int n_qt = 0, n_groups = 0;
     size_t off_x = 0, off_y = 0, off_z = 0, off_jobs = 0, off_streams = 0, off_seeds = 0;
     size_t off_cmi = 0;  // index of the group's first job in the call's cmi buffer
+    bool sort = false;   // order the samples along a Morton curve first
+    int work_slot = 0;   // index of the group's work counters in the call
 };
 
 int plan(idtx_ctx *c, Group &g)
@@ -384,11 +497,19 @@ int plan(idtx_ctx *c, Group &g)
     g.v = pick_variant(c, g.dx, g.dy, g.dz, g.k);
     if (!g.v)
         return fail(IDTX_EINVAL, "no kernel for dx=%d dy=%d dz=%d k=%d", g.dx, g.dy, g.dz, g.k);
-    g.n_pad = (g.n + kTQ - 1) / kTQ * kTQ;
-    g.n_qt = (int)(g.n_pad / kTQ);
+    g.n_pad = (g.n + kTJ - 1) / kTJ * kTJ;
+    g.n_qt = (int)(g.n_pad / g.v->qc);
     g.n_groups = (int)((g.jobs.size() + g.v->gb - 1) / g.v->gb);
     if (g.n_groups > 65535) return fail(IDTX_EINVAL, "too many estimates in one group");
+    g.sort = g.n > 2 * kTJ;
     return IDTX_OK;
+}
+
+// Bits per coordinate and number of coordinates of the Morton key.
+void morton_shape(int n_shared, int &nk, int &bits)
+{
+    nk = std::min(n_shared, 32);
+    bits = std::max(1, std::min(10, 32 / std::max(nk, 1)));
 }
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -417,12 +538,21 @@ void pack_desc(std::vector<Group> &gs, std::vector<unsigned char> &arena)
 }
 
 struct CallBuffers {
-    size_t sh = 0, xi = 0, perm = 0, partial = 0;
+    size_t sh = 0, xi = 0, perm = 0, partial = 0, order = 0, sort_tmp = 0;
 };
+
+// B_ORDER layout for n samples: order | idx | keys_in | keys_out | column ranges.
+size_t order_bytes(int64_t n) { return 4 * align_up((size_t)n * 4, 256) + 256; }
 
 void sizes_of(const Group &g, CallBuffers &b)
 {
-    b.sh = std::max(b.sh, (size_t)g.n_pad * g.v->dsp * sizeof(float));
+    b.sh = std::max(b.sh, (size_t)(g.n_pad / kTJ) * kTileRows * g.v->dsp * sizeof(float));
+    if (g.sort) {
+        b.order = std::max(b.order, order_bytes(g.n));
+        size_t tmp = 0;
+        sort_pairs_u32(nullptr, tmp, nullptr, nullptr, nullptr, nullptr, (int)g.n, 32, nullptr);
+        b.sort_tmp = std::max(b.sort_tmp, tmp);
+    }
     b.xi = std::max(b.xi, (size_t)g.n_groups * g.n_pad * g.v->gb * g.v->dx * sizeof(float));
     b.perm = std::max(b.perm, g.slot_stream.size() * (size_t)g.n * sizeof(int32_t));
     b.partial = std::max(b.partial, g.jobs.size() * (size_t)g.n_qt * sizeof(double));
@@ -459,18 +589,47 @@ int enqueue_group(idtx_ctx *c, const Group &g, cudaStream_t st, double *cmi, flo
     const int n_slots = (int)g.slot_stream.size();
 
     const int dzb = v.dz, dyb = v.dy;
+    const int32_t *order = nullptr;
+    int launches = 0;
+    if (g.sort) {
+        // Order the samples along a Morton curve of the shared coordinates, so
+        // that a warp's queries and a tile's references are spatial neighbours.
+        unsigned char *ob = (unsigned char *)c->buf[B_ORDER];
+        const size_t col = align_up((size_t)g.n * 4, 256);
+        int32_t *ord = (int32_t *)ob;
+        int32_t *idx = (int32_t *)(ob + col);
+        uint32_t *kin = (uint32_t *)(ob + 2 * col);
+        uint32_t *kout = (uint32_t *)(ob + 3 * col);
+        float *mm = (float *)(ob + 4 * col);
+        int nk, bits;
+        morton_shape(g.dz + g.dy, nk, bits);
+        k_minmax_cols<<<nk, 256, 0, st>>>(zc, g.dz, yc, g.dy, g.n, mm);
+        IDTX_CUDA(cudaGetLastError());
+        k_morton_keys<<<grid_for(g.n, 256), 256, 0, st>>>(zc, g.dz, yc, nk, bits, g.n, mm, kin,
+                                                          idx);
+        IDTX_CUDA(cudaGetLastError());
+        size_t tmp_bytes = c->cap[B_SORT];
+        IDTX_CUDA(sort_pairs_u32(c->buf[B_SORT], tmp_bytes, kin, kout, idx, ord, (int)g.n,
+                                 nk * bits, st));
+        order = ord;
+        launches += 3;
+    }
     k_pack_shared<<<grid_for(g.n_pad * v.dsp, 256), 256, 0, st>>>(
-        zc, g.dz, dzb, yc, g.dy, dyb, v.dsp, g.n, g.n_pad, sh, c->d_err);
+        zc, g.dz, dzb, yc, g.dy, dyb, v.dsp, g.n, g.n_pad, order, sh, c->d_err);
+    IDTX_CUDA(cudaGetLastError());
+    k_tile_boxes<<<(unsigned)(g.n_pad / kTJ), kTJ, 0, st>>>(sh, v.dsp, g.n);
     IDTX_CUDA(cudaGetLastError());
     if (n_slots > 0) {
         k_iota<<<grid_for((int64_t)n_slots * g.n, 256), 256, 0, st>>>(perm, n_slots, g.n);
         IDTX_CUDA(cudaGetLastError());
         k_fisher_yates<<<(n_slots + 31) / 32, 32, 0, st>>>(perm, streams, seeds, n_slots, g.n);
         IDTX_CUDA(cudaGetLastError());
+        launches += 2;
     }
     k_gather_x<<<grid_for((int64_t)g.n_groups * g.n_pad * v.gb * v.dx, 256), 256, 0, st>>>(
-        xc, g.dx, v.dx, jobs, n_jobs, perm, g.n, g.n_pad, v.gb, g.n_groups, xi, c->d_err);
+        xc, g.dx, v.dx, jobs, n_jobs, perm, g.n, g.n_pad, v.gb, g.n_groups, order, xi, c->d_err);
     IDTX_CUDA(cudaGetLastError());
+    launches += 5;  // pack, boxes, gather, fused, finalize
 
     KsgLaunch a;
     a.sh = sh;
@@ -479,6 +638,8 @@ int enqueue_group(idtx_ctx *c, const Group &g, cudaStream_t st, double *cmi, flo
     a.partial = partial;
     a.eps_out = eps_out;
     a.cnt_out = cnt_out;
+    a.order = order;
+    a.work = (unsigned long long *)c->buf[B_WORK] + (size_t)g.work_slot * kNumWork;
     a.err = c->d_err;
     a.n = g.n;
     a.n_pad = g.n_pad;
@@ -498,11 +659,17 @@ int enqueue_group(idtx_ctx *c, const Group &g, cudaStream_t st, double *cmi, flo
         c->pending.emplace_back(ev0, ev1);
     }
     {
-        const double pairs = (double)g.n * (double)g.n * (double)g.n_groups;
-        const int dze = std::max(g.dz, 1);
+        WorkShape ws;
+        ws.dx = g.dx;
+        ws.dy = g.dy;
+        ws.dz_eff = std::max(g.dz, 1);
+        ws.gb = v.gb;
+        ws.job_frac = (double)n_jobs / ((double)g.n_groups * v.gb);
+        ws.exhaustive_pairs = 2.0 * (double)g.n * (double)g.n * (double)g.n_groups;
+        if ((int)c->call_shapes.size() <= g.work_slot) c->call_shapes.resize(g.work_slot + 1);
+        c->call_shapes[g.work_slot] = ws;
         c->stats.fused_launches += 1;
-        c->stats.fused_lane_ops += pairs * (double)(2 * (g.dy + dze) + 1 + 2 * dze + 1);
-        c->stats.kernel_launches += (n_slots > 0 ? 6 : 4);
+        c->stats.kernel_launches += launches;
     }
     k_finalize<<<(n_jobs + 127) / 128, 128, 0, st>>>(partial, n_jobs, g.n_qt, c->psi, g.k, g.n,
                                                       cmi);
@@ -519,10 +686,53 @@ struct HostCopy {
     size_t off;  // float offset in B_IN
 };
 
+// Reset the per-call work counters for n_slots fused launches.
+int begin_call(idtx_ctx *c, int n_slots, cudaStream_t st)
+{
+    c->call_shapes.clear();
+    const size_t bytes = (size_t)std::max(n_slots, 1) * kNumWork * sizeof(unsigned long long);
+    IDTX_TRY(ensure(c, B_WORK, bytes));
+    if (c->h_work_cap < bytes) {
+        if (c->h_work) cudaFreeHost(c->h_work);
+        c->h_work = nullptr;
+        c->h_work_cap = 0;
+        IDTX_CUDA(cudaMallocHost(&c->h_work, bytes));
+        c->h_work_cap = bytes;
+    }
+    IDTX_CUDA(cudaMemsetAsync(c->buf[B_WORK], 0, bytes, st));
+    IDTX_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
+    return IDTX_OK;
+}
+
 int finish_call(idtx_ctx *c, cudaStream_t st)
 {
     IDTX_CUDA(cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    const size_t n_shapes = c->call_shapes.size();
+    if (n_shapes)
+        IDTX_CUDA(cudaMemcpyAsync(c->h_work, c->buf[B_WORK],
+                                  n_shapes * kNumWork * sizeof(unsigned long long),
+                                  cudaMemcpyDeviceToHost, st));
     IDTX_CUDA(cudaStreamSynchronize(st));
+    for (size_t w = 0; w < n_shapes; ++w) {
+        // Algorithmic lane operations of the work the fused kernel did:
+        //  neighbour pass: per scanned pair 2(dy+dz')+1 (|d| and max per shared
+        //    dimension, bound compare); per passing pair and job 2dx+1;
+        //  count pass: per scanned pair 2dz'+1; per passing pair 2dy (Y
+        //    distance) and per job 2dx+7 (X distance, three compares, three adds).
+        const WorkShape &ws = c->call_shapes[w];
+        const unsigned long long *k = c->h_work + w * kNumWork;
+        const double jobs = ws.gb * ws.job_frac;
+        c->stats.fused_lane_ops += (double)k[0] * (2.0 * (ws.dy + ws.dz_eff) + 1.0) +
+                                   (double)k[1] * jobs * (2.0 * ws.dx + 1.0) +
+                                   (double)k[2] * (2.0 * ws.dz_eff + 1.0) +
+                                   (double)k[3] * (2.0 * ws.dy + jobs * (2.0 * ws.dx + 7.0));
+        c->stats.scanned_a += (double)k[0];
+        c->stats.passed_a += (double)k[1];
+        c->stats.scanned_b += (double)k[2];
+        c->stats.passed_b += (double)k[3];
+        c->stats.exhaustive_pairs += ws.exhaustive_pairs;
+    }
+    c->call_shapes.clear();
     for (auto &pe : c->pending) {
         float ms = 0.0f;
         if (cudaEventElapsedTime(&ms, pe.first, pe.second) == cudaSuccess) c->stats.fused_ms += ms;
@@ -619,6 +829,7 @@ int idtx_ctx_destroy(idtx_ctx *c)
     if (c->psi) cudaFree(c->psi);
     if (c->d_err) cudaFree(c->d_err);
     if (c->h_err) cudaFreeHost(c->h_err);
+    if (c->h_work) cudaFreeHost(c->h_work);
     delete c;
     return IDTX_OK;
 }
@@ -657,7 +868,7 @@ int idtx_cmi_ksg(idtx_ctx *c, const float *x, int dx, const float *y, int dy, co
             in_floats += (size_t)dims[t] * (size_t)n;
         }
     IDTX_TRY(ensure(c, B_IN, in_floats * sizeof(float)));
-    IDTX_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
+    IDTX_TRY(begin_call(c, 1, st));
     {
         size_t off = 0;
         for (int t = 0; t < 3; ++t)
@@ -701,6 +912,8 @@ int idtx_cmi_ksg(idtx_ctx *c, const float *x, int dx, const float *y, int dy, co
     IDTX_TRY(ensure(c, B_XI, b.xi));
     IDTX_TRY(ensure(c, B_PERM, b.perm));
     IDTX_TRY(ensure(c, B_PARTIAL, b.partial));
+    IDTX_TRY(ensure(c, B_ORDER, b.order));
+    IDTX_TRY(ensure(c, B_SORT, b.sort_tmp));
     IDTX_TRY(ensure(c, B_CMI, (size_t)n_jobs * sizeof(double)));
     if (eps_out && !eps_dev) IDTX_TRY(ensure(c, B_EPS, (size_t)n_jobs * n * sizeof(float)));
     if (counts_out && !cnt_dev)
@@ -756,7 +969,7 @@ int idtx_cmi_batch(idtx_ctx *c, const idtx_problem *probs, int n_probs, int k, d
         total_jobs += 1 + (size_t)q.n_surr;
     }
     IDTX_TRY(ensure(c, B_IN, in_floats * sizeof(float)));
-    IDTX_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
+    IDTX_TRY(begin_call(c, n_probs, st));
     std::vector<Group> gs(n_probs);
     size_t in_off = 0, job_off = 0;
     for (int p = 0; p < n_probs; ++p) {
@@ -792,6 +1005,7 @@ int idtx_cmi_batch(idtx_ctx *c, const idtx_problem *probs, int n_probs, int k, d
             g.slot_seed.push_back(q.seed);
         }
         IDTX_TRY(plan(c, g));
+        g.work_slot = p;
         g.off_cmi = job_off;
         job_off += g.jobs.size();
     }
@@ -804,6 +1018,8 @@ int idtx_cmi_batch(idtx_ctx *c, const idtx_problem *probs, int n_probs, int k, d
     IDTX_TRY(ensure(c, B_XI, b.xi));
     IDTX_TRY(ensure(c, B_PERM, b.perm));
     IDTX_TRY(ensure(c, B_PARTIAL, b.partial));
+    IDTX_TRY(ensure(c, B_ORDER, b.order));
+    IDTX_TRY(ensure(c, B_SORT, b.sort_tmp));
     IDTX_TRY(ensure(c, B_CMI, total_jobs * sizeof(double)));
     IDTX_TRY(ensure_psi(c, std::max<int64_t>(n_max, k) + 1, st));
     IDTX_CUDA(cudaMemcpyAsync(c->buf[B_DESC], arena.data(), arena.size(), cudaMemcpyHostToDevice,
@@ -861,7 +1077,7 @@ int idtx_mte_step(idtx_ctx *c, const float *series, int n_proc, int64_t T, int t
     const float *ser = series;
     const bool host_series = !device_accessible(series);
     IDTX_TRY(ensure(c, B_IN, host_series ? (size_t)n_proc * T * sizeof(float) : 0));
-    IDTX_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
+    IDTX_TRY(begin_call(c, 1, st));
     if (host_series) {
         IDTX_CUDA(cudaMemcpyAsync(c->buf[B_IN], series, (size_t)n_proc * T * sizeof(float),
                                   cudaMemcpyHostToDevice, st));
@@ -906,6 +1122,8 @@ int idtx_mte_step(idtx_ctx *c, const float *series, int n_proc, int64_t T, int t
     IDTX_TRY(ensure(c, B_XI, b.xi));
     IDTX_TRY(ensure(c, B_PERM, b.perm));
     IDTX_TRY(ensure(c, B_PARTIAL, b.partial));
+    IDTX_TRY(ensure(c, B_ORDER, b.order));
+    IDTX_TRY(ensure(c, B_SORT, b.sort_tmp));
     IDTX_TRY(ensure(c, B_CMI, (size_t)n_jobs * sizeof(double)));
     IDTX_TRY(ensure(c, B_STEP, sizeof(idtx_step)));
     IDTX_TRY(ensure_psi(c, std::max<int64_t>(n, s->k) + 1, st));
@@ -1086,8 +1304,8 @@ extern "C" int idtx_cmi_ksg_noalloc(const float *x, int dx, const float *y, int 
     // Carve the scratch: [descriptors | err | psi | sh | xi | perm | partial].
     const int n_jobs = 1 + s->n_surr;
     const int n_slots = s->n_surr;
-    const int64_t n_pad = (n + kTQ - 1) / kTQ * kTQ;
-    const int n_qt = (int)(n_pad / kTQ);
+    const int64_t n_pad = (n + kTJ - 1) / kTJ * kTJ;
+    const int n_qt = (int)(n_pad / v->qc);
     const int n_groups = (n_jobs + v->gb - 1) / v->gb;
     size_t off = kNoAllocDescBytes;
     auto take = [&](size_t bytes) {
@@ -1097,7 +1315,7 @@ extern "C" int idtx_cmi_ksg_noalloc(const float *x, int dx, const float *y, int 
     };
     const size_t at_err = take(sizeof(int));
     const size_t at_psi = take((size_t)(std::max<int64_t>(n, s->k) + 2) * sizeof(double));
-    const size_t at_sh = take((size_t)n_pad * v->dsp * sizeof(float));
+    const size_t at_sh = take((size_t)(n_pad / kTJ) * kTileRows * v->dsp * sizeof(float));
     const size_t at_xi = take((size_t)n_groups * n_pad * v->gb * v->dx * sizeof(float));
     const size_t at_perm = take((size_t)n_slots * n * sizeof(int32_t));
     const size_t at_partial = take((size_t)n_jobs * n_qt * sizeof(double));
@@ -1167,7 +1385,9 @@ extern "C" int idtx_cmi_ksg_noalloc(const float *x, int dx, const float *y, int 
     IDTX_CUDA(cudaGetLastError());
     k_pack_shared<<<grid_for(n_pad * v->dsp, 256), 256, 0, st>>>(
         (const Col *)(base + o_z), dz, v->dz, (const Col *)(base + o_y), dy, v->dy, v->dsp, n,
-        n_pad, sh, err);
+        n_pad, nullptr, sh, err);
+    IDTX_CUDA(cudaGetLastError());
+    k_tile_boxes<<<(unsigned)(n_pad / kTJ), kTJ, 0, st>>>(sh, v->dsp, n);
     IDTX_CUDA(cudaGetLastError());
     if (n_slots > 0) {
         k_iota<<<grid_for((int64_t)n_slots * n, 256), 256, 0, st>>>(perm, n_slots, n);
@@ -1179,7 +1399,7 @@ extern "C" int idtx_cmi_ksg_noalloc(const float *x, int dx, const float *y, int 
     }
     k_gather_x<<<grid_for((int64_t)n_groups * n_pad * v->gb * v->dx, 256), 256, 0, st>>>(
         (const Col *)(base + o_x), dx, v->dx, (const Job *)(base + o_jobs), n_jobs, perm, n,
-        n_pad, v->gb, n_groups, xi, err);
+        n_pad, v->gb, n_groups, nullptr, xi, err);
     IDTX_CUDA(cudaGetLastError());
     KsgLaunch a;
     a.sh = sh;
@@ -1188,6 +1408,8 @@ extern "C" int idtx_cmi_ksg_noalloc(const float *x, int dx, const float *y, int 
     a.partial = partial;
     a.eps_out = nullptr;
     a.cnt_out = nullptr;
+    a.order = nullptr;
+    a.work = nullptr;
     a.err = err;
     a.n = n;
     a.n_pad = n_pad;
