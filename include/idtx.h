@@ -110,7 +110,9 @@ int idtx_version(void);
  * by the neighbour / count pass, passed_a / passed_b those that passed the
  * pass's shared bound; exhaustive_pairs what scanning every reference tile in
  * both passes would have been (tiles whose bounding box is provably out of
- * reach are skipped; results are identical either way). */
+ * reach are skipped; results are identical either way).  wait_cycles /
+ * warp_cycles: SM clock cycles the kernel's warps spent waiting for staged
+ * reference tiles, and in total (summed over warps). */
 typedef struct {
     int64_t kernel_launches;
     int64_t fused_launches;
@@ -118,6 +120,7 @@ typedef struct {
     double fused_lane_ops;
     double scanned_a, passed_a, scanned_b, passed_b;
     double exhaustive_pairs;
+    double wait_cycles, warp_cycles;
 } idtx_stats;
 
 /* Enable (1) or disable (0) event timing of the fused kernel. */

@@ -54,7 +54,8 @@ class Stats(ctypes.Structure):
                 ("fused_ms", ctypes.c_double), ("fused_lane_ops", ctypes.c_double),
                 ("scanned_a", ctypes.c_double), ("passed_a", ctypes.c_double),
                 ("scanned_b", ctypes.c_double), ("passed_b", ctypes.c_double),
-                ("exhaustive_pairs", ctypes.c_double)]
+                ("exhaustive_pairs", ctypes.c_double), ("wait_cycles", ctypes.c_double),
+                ("warp_cycles", ctypes.c_double)]
 
 
 class Step(ctypes.Structure):
@@ -126,7 +127,8 @@ class Context:
         return dict(kernel_launches=st.kernel_launches, fused_launches=st.fused_launches,
                     fused_ms=st.fused_ms, fused_lane_ops=st.fused_lane_ops,
                     scanned_a=st.scanned_a, passed_a=st.passed_a, scanned_b=st.scanned_b,
-                    passed_b=st.passed_b, exhaustive_pairs=st.exhaustive_pairs)
+                    passed_b=st.passed_b, exhaustive_pairs=st.exhaustive_pairs,
+                    wait_cycles=st.wait_cycles, warp_cycles=st.warp_cycles)
 
     def reset_stats(self):
         _check(load().idtx_ctx_reset_stats(self.handle))

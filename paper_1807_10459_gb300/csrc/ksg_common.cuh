@@ -40,8 +40,10 @@ constexpr int kTileRows = kTJ + 2;  // samples + bounding box rows
 // Work counters written by the fused kernel (per launch, summed over CTAs):
 //   [0] (query, reference) pairs scanned by the neighbour pass,
 //   [1] pairs that passed its shared bound (per-job work done),
-//   [2] pairs scanned by the count pass, [3] pairs that passed its bound.
-constexpr int kNumWork = 4;
+//   [2] pairs scanned by the count pass, [3] pairs that passed its bound,
+//   [4] SM clock cycles warps spent waiting for staged tiles, [5] cycles warps
+//   spent in the kernel (both summed over warps).
+constexpr int kNumWork = 6;
 
 struct KsgLaunch {
     const float *sh;

@@ -336,9 +336,14 @@ __global__ void __launch_bounds__(KsgShape<DX, DY, DZ, K1, EXACT, QW, NWARPS>::T
 
     // Each warp walks the items on its own; the last warp to finish an item
     // refills its stage with item u + ST.  No CTA-wide barrier per tile.
+    long long wait_cycles = 0;
+    const long long t_begin = clock64();
     auto acquire = [&](int u) {
-        if (!mbar_wait_bounded(&s_bar[u % ST], static_cast<uint32_t>((u / ST) & 1),
-                               a.timeout_ns)) {
+        const long long t0 = clock64();
+        const bool got = mbar_wait_bounded(&s_bar[u % ST], static_cast<uint32_t>((u / ST) & 1),
+                                           a.timeout_ns);
+        wait_cycles += clock64() - t0;
+        if (!got) {
             *abort_flag = 1;
             atomicOr(a.err, kErrTimeout);
         }
@@ -603,6 +608,8 @@ __global__ void __launch_bounds__(KsgShape<DX, DY, DZ, K1, EXACT, QW, NWARPS>::T
         atomicAdd(&a.work[1], events_a);
         atomicAdd(&a.work[2], scanned_b);
         atomicAdd(&a.work[3], events_b);
+        atomicAdd(&a.work[4], static_cast<unsigned long long>(wait_cycles));
+        atomicAdd(&a.work[5], static_cast<unsigned long long>(clock64() - t_begin));
     }
     __syncthreads();
     if (tid < GB && job_ok) {

@@ -730,6 +730,8 @@ int finish_call(idtx_ctx *c, cudaStream_t st)
         c->stats.passed_a += (double)k[1];
         c->stats.scanned_b += (double)k[2];
         c->stats.passed_b += (double)k[3];
+        c->stats.wait_cycles += (double)k[4];
+        c->stats.warp_cycles += (double)k[5];
         c->stats.exhaustive_pairs += ws.exhaustive_pairs;
     }
     c->call_shapes.clear();
