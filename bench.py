@@ -224,6 +224,24 @@ def run_ours(args):
         t_max = float(t.item())
     value = est_per_step * args.steps * world / (t_max / 1e3)
 
+    # plain schedule (one launch per estimate, no sharing) on a subset of the
+    # step: the same 47 candidates with 4 surrogates each (its cost per estimate
+    # does not depend on the number of surrogates)
+    plain = None
+    if rank == 0:
+        def plain_step():
+            return idtx.mte_step(series_d, target, w["n_past"], w["min_lag"], w["max_lag"], (),
+                                 0, k=w["k"], n_surr=4, alpha=w["alpha"], seed=w["seed"],
+                                 mode=idtx.MODE_PLAIN, ctx=ctx)
+        plain_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plain_step()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        plain = {"value": 47 * 5 / dt, "unit": "estimates/s",
+                 "sample": "the step's 47 candidates with 4 surrogates each, one launch each"}
+
     # end to end through the public API with host (pinned) inputs and outputs
     series_h = torch.from_numpy(net.series).pin_memory()
     step(series_h)
@@ -271,7 +289,10 @@ def run_ours(args):
             "data": "synthetic", "config": _config(), "mode": "batched (one fused launch "
             "per step over all candidates and surrogates)",
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": int(st["kernel_launches"]), "clocks": clocks}
+            "gpu_launches": int(st["kernel_launches"]), "clocks": clocks,
+            "modes": {"batched": value, "plain": plain["value"] if plain else None,
+                      "batched_over_plain": value / plain["value"] if plain else None,
+                      "plain_sample": plain["sample"] if plain else None}}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -69,17 +69,27 @@ enum {
 
 typedef struct idtx_ctx idtx_ctx;
 
+/* Execution modes (same results; only the schedule differs).
+ * IDTX_MODE_BATCHED: all estimates of a call that share Y and Z (the original
+ *   and its surrogates, or every candidate of a greedy step) run in one fused
+ *   launch that computes their shared distances once.
+ * IDTX_MODE_PLAIN: one launch per estimate, thread-per-query brute force with
+ *   no sharing between estimates (the reference point for batching). */
+#define IDTX_MODE_BATCHED 0
+#define IDTX_MODE_PLAIN 1
+
 /* Estimation settings.  k: neighbours (1 <= k <= min(N-1, IDTX_MAX_K));
  * n_surr: surrogates per estimate (>= 0; the greedy calls need >= 1);
  * seed: surrogate seed; alpha: gate level of the greedy calls (0 < alpha < 1);
- * timeout_ms: bound on any device wait (<= 0 selects 2000 ms). */
+ * timeout_ms: bound on any device wait (<= 0 selects 2000 ms);
+ * mode: IDTX_MODE_BATCHED (default, 0) or IDTX_MODE_PLAIN. */
 typedef struct {
     int32_t k;
     int32_t n_surr;
     uint64_t seed;
     double alpha;
     int32_t timeout_ms;
-    int32_t reserved;
+    int32_t mode;
 } idtx_settings;
 
 /* Create a context bound to CUDA device `device`.  *ctx receives the handle. */

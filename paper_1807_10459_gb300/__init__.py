@@ -27,6 +27,7 @@ _lib = None
 _default_ctx = {}
 
 IDTX_OK, IDTX_EINVAL, IDTX_ENOMEM, IDTX_ECUDA, IDTX_ETIMEOUT, IDTX_EINTERNAL = range(6)
+MODE_BATCHED, MODE_PLAIN = 0, 1
 _ERR_NAMES = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EINTERNAL"}
 
 
@@ -39,7 +40,7 @@ class IdtxError(RuntimeError):
 class Settings(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("n_surr", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("alpha", ctypes.c_double), ("timeout_ms", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("mode", ctypes.c_int32)]
 
 
 class Problem(ctypes.Structure):
@@ -212,13 +213,14 @@ def _out(shape, dtype, like):
     return a, a.ctypes.data
 
 
-def _settings(k, n_surr, seed, alpha=0.05, timeout_ms=0):
+def _settings(k, n_surr, seed, alpha=0.05, timeout_ms=0, mode=MODE_BATCHED):
     return Settings(int(k), int(n_surr), ctypes.c_uint64(int(seed) & (2**64 - 1)).value,
-                    float(alpha), int(timeout_ms), 0)
+                    float(alpha), int(timeout_ms), int(mode))
 
 
 def cmi_ksg(x, y, z=None, k: int = 4, n_surr: int = 0, seed: int = 0, want_eps: bool = False,
-            want_counts: bool = False, timeout_ms: int = 0, ctx: Context | None = None):
+            want_counts: bool = False, timeout_ms: int = 0, mode: int = MODE_BATCHED,
+            ctx: Context | None = None):
     """One KSG estimate of I(X;Y|Z) plus ``n_surr`` surrogates.
 
     x, y, z: [d][N] float32 (1-D means d = 1; z may be None).  Returns the
@@ -234,7 +236,7 @@ def cmi_ksg(x, y, z=None, k: int = 4, n_surr: int = 0, seed: int = 0, want_eps: 
     cmi, p_cmi = _out((1 + n_surr,), np.float64, x)
     eps, p_eps = _out((1 + n_surr, n), np.float32, x) if want_eps else (None, None)
     cnt, p_cnt = _out((1 + n_surr, 3, n), np.int32, x) if want_counts else (None, None)
-    s = _settings(k, n_surr, seed, timeout_ms=timeout_ms)
+    s = _settings(k, n_surr, seed, timeout_ms=timeout_ms, mode=mode)
     _check(load().idtx_cmi_ksg(ctx.handle, ax.ptr, ax.d, ay.ptr, ay.d, az.ptr, az.d, n, n,
                                ctypes.byref(s), p_cmi, p_eps, p_cnt, _stream_for(x, y, z)))
     if want_eps or want_counts:
@@ -279,14 +281,14 @@ def cmi_batch(problems, k: int = 4, ctx: Context | None = None):
 def mte_step(series, target: int, n_past: int, min_lag: int, max_lag: int, selected=(),
              step_index: int = 0, k: int = 4, n_surr: int = 200, alpha: float = 0.05,
              seed: int = 0, want_estimates: bool = False, timeout_ms: int = 0,
-             ctx: Context | None = None):
+             mode: int = MODE_BATCHED, ctx: Context | None = None):
     """One greedy selection step; returns (cand, significant, stat, pval) and,
     if asked, the [n_proc*n_lags][1+n_surr] estimates (NaN rows: not evaluated)."""
     a = _Arr(series, name="series")
     dev = series.device.index if (_is_torch(series) and series.is_cuda) else 0
     ctx = ctx or default_context(dev or 0)
     sel = np.ascontiguousarray(np.asarray(list(selected), np.int32))
-    s = _settings(k, n_surr, seed, alpha, timeout_ms)
+    s = _settings(k, n_surr, seed, alpha, timeout_ms, mode)
     step = Step()
     est, p_est = (None, None)
     if want_estimates:

@@ -295,6 +295,72 @@ __global__ void k_finalize(const double *partial, int n_jobs, int n_qt, const do
     cmi[job] = psi[k] + s / (double)n;
 }
 
+// One estimate per launch, the "plain" schedule: thread per query, brute
+// force over every reference in sample order, no sharing with other
+// estimates, no ordering and no pruning.  Same definitions as the fused
+// kernel: the (k+1) smallest joint distances including the sample itself,
+// strict-radius counts with the self pair removed.  The job's X values are
+// read from column g of its xi group (stride xw), its Y/Z from sh.
+constexpr int kPlainThreads = 128;
+
+__global__ void __launch_bounds__(kPlainThreads)
+    k_ksg_plain(const float *sh, int dsp, int dz, int dzb, int dy, const float *xg, int xw,
+                int dx, int64_t n, int k, const double *psi, double *partial)
+{
+    __shared__ double s_red[kPlainThreads / 32];
+    const int64_t i = blockIdx.x * (int64_t)kPlainThreads + threadIdx.x;
+    const bool valid = i < n;
+    auto row = [&](int64_t j) { return sh + ((j / kTJ) * kTileRows + (j % kTJ)) * dsp; };
+    float q[IDTX_MAX_DZ + IDTX_MAX_DY], xq[IDTX_MAX_DX];
+    const int ndz = dz > 0 ? dz : 1;  // dz = 0 uses the bucket's zero column
+    for (int d = 0; d < ndz; ++d) q[d] = valid ? row(i)[d] : 0.0f;
+    for (int d = 0; d < dy; ++d) q[ndz + d] = valid ? row(i)[dzb + d] : 0.0f;
+    for (int d = 0; d < dx; ++d) xq[d] = valid ? xg[i * xw + d] : 0.0f;
+    float h[IDTX_MAX_K + 1];
+    for (int t = 0; t <= k; ++t) h[t] = INFINITY;
+    auto dists = [&](int64_t j, float &dzv, float &dyv, float &dxv) {
+        const float *r = row(j);
+        dzv = 0.0f;
+        for (int d = 0; d < ndz; ++d) dzv = fmaxf(dzv, fabsf(q[d] - r[d]));
+        dyv = 0.0f;
+        for (int d = 0; d < dy; ++d) dyv = fmaxf(dyv, fabsf(q[ndz + d] - r[dzb + d]));
+        dxv = 0.0f;
+        for (int d = 0; d < dx; ++d) dxv = fmaxf(dxv, fabsf(xq[d] - xg[j * xw + d]));
+    };
+    for (int64_t j = 0; j < n; ++j) {
+        float a, b, c;
+        dists(j, a, b, c);
+        const float dd = fmaxf(fmaxf(a, b), c);
+        if (dd < h[k]) {
+            int t = k;
+            while (t > 0 && h[t - 1] > dd) {
+                h[t] = h[t - 1];
+                --t;
+            }
+            h[t] = dd;
+        }
+    }
+    const float e = h[k];
+    int cxz = 0, cyz = 0, cz = 0;
+    for (int64_t j = 0; j < n; ++j) {
+        float a, b, c;
+        dists(j, a, b, c);
+        cz += a < e ? 1 : 0;
+        cyz += fmaxf(a, b) < e ? 1 : 0;
+        cxz += fmaxf(a, c) < e ? 1 : 0;
+    }
+    const int self = e > 0.0f ? 1 : 0;
+    double t = valid ? psi[cz - self + 1] - psi[cxz - self + 1] - psi[cyz - self + 1] : 0.0;
+    for (int off = 16; off >= 1; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sum = 0.0;
+        for (int w = 0; w < kPlainThreads / 32; ++w) sum += s_red[w];
+        partial[blockIdx.x] = sum;
+    }
+}
+
 // Max-statistic gate over est[c][1+S] (candidates in ascending id order).
 __global__ void k_gate(const double *est, const int32_t *ids, int n_cand, int n_surr,
                        double alpha, idtx_step *out)
@@ -489,6 +555,7 @@ struct Group {
     size_t off_x = 0, off_y = 0, off_z = 0, off_jobs = 0, off_streams = 0, off_seeds = 0;
     size_t off_cmi = 0;  // index of the group's first job in the call's cmi buffer
     bool sort = false;   // order the samples along a Morton curve first
+    bool plain = false;  // one launch per estimate (IDTX_MODE_PLAIN)
     int work_slot = 0;   // index of the group's work counters in the call
 };
 
@@ -501,7 +568,8 @@ int plan(idtx_ctx *c, Group &g)
     g.n_qt = (int)(g.n_pad / g.v->qc);
     g.n_groups = (int)((g.jobs.size() + g.v->gb - 1) / g.v->gb);
     if (g.n_groups > 65535) return fail(IDTX_EINVAL, "too many estimates in one group");
-    g.sort = g.n > 2 * kTJ;
+    g.sort = !g.plain && g.n > 2 * kTJ;
+    if (g.plain) g.n_qt = (int)(g.n_pad / kPlainThreads);
     return IDTX_OK;
 }
 
@@ -653,12 +721,26 @@ int enqueue_group(idtx_ctx *c, const Group &g, cudaStream_t st, double *cmi, flo
         IDTX_TRY(take_event(c, &ev1));
         IDTX_CUDA(cudaEventRecord(ev0, st));
     }
-    IDTX_CUDA(v.fn(a, g.n_groups, st));
+    if (g.plain) {
+        const int xw = v.gb * v.dx;
+        for (int jb = 0; jb < n_jobs; ++jb) {
+            const float *xg = xi + (size_t)(jb / v.gb) * g.n_pad * xw + (jb % v.gb) * v.dx;
+            k_ksg_plain<<<(unsigned)g.n_qt, kPlainThreads, 0, st>>>(
+                sh, v.dsp, g.dz, v.dz, g.dy, xg, xw, g.dx, g.n, g.k, c->psi,
+                partial + (size_t)jb * g.n_qt);
+            IDTX_CUDA(cudaGetLastError());
+        }
+    } else {
+        IDTX_CUDA(v.fn(a, g.n_groups, st));
+    }
     if (c->profiling) {
         IDTX_CUDA(cudaEventRecord(ev1, st));
         c->pending.emplace_back(ev0, ev1);
     }
-    {
+    if (g.plain) {
+        c->stats.fused_launches += n_jobs;
+        c->stats.kernel_launches += launches - 1 + n_jobs;
+    } else {
         WorkShape ws;
         ws.dx = g.dx;
         ws.dy = g.dy;
@@ -850,6 +932,8 @@ int idtx_cmi_ksg(idtx_ctx *c, const float *x, int dx, const float *y, int dy, co
     if (s->k < 1 || s->k > IDTX_MAX_K || s->k > n - 1)
         return fail(IDTX_EINVAL, "k=%d out of range for n=%lld", s->k, (long long)n);
     if (s->n_surr < 0) return fail(IDTX_EINVAL, "n_surr < 0");
+    if (s->mode != IDTX_MODE_BATCHED && s->mode != IDTX_MODE_PLAIN)
+        return fail(IDTX_EINVAL, "unknown mode %d", s->mode);
     IDTX_TRY(check_cols(x, dx, "x"));
     IDTX_TRY(check_cols(y, dy, "y"));
     IDTX_TRY(check_cols(z, dz, "z"));
@@ -901,6 +985,7 @@ int idtx_cmi_ksg(idtx_ctx *c, const float *x, int dx, const float *y, int dy, co
         g.slot_stream.push_back((uint64_t)sidx);
         g.slot_seed.push_back(s->seed);
     }
+    g.plain = s->mode == IDTX_MODE_PLAIN;
     IDTX_TRY(plan(c, g));
     std::vector<unsigned char> arena;
     pack_desc(gs, arena);
@@ -1057,6 +1142,8 @@ int idtx_mte_step(idtx_ctx *c, const float *series, int n_proc, int64_t T, int t
     if (s->k < 1 || s->k > IDTX_MAX_K || s->k > n - 1) return fail(IDTX_EINVAL, "bad k");
     if (s->n_surr < 1 || s->n_surr >= (1 << 24)) return fail(IDTX_EINVAL, "n_surr out of range");
     if (!(s->alpha > 0.0 && s->alpha < 1.0)) return fail(IDTX_EINVAL, "alpha out of (0,1)");
+    if (s->mode != IDTX_MODE_BATCHED && s->mode != IDTX_MODE_PLAIN)
+        return fail(IDTX_EINVAL, "unknown mode %d", s->mode);
     const int dz = n_past + n_selected;
     if (dz > IDTX_MAX_DZ) return fail(IDTX_EINVAL, "dz=%d exceeds %d", dz, IDTX_MAX_DZ);
     std::vector<char> alive(n_cand_total, 1);
@@ -1110,6 +1197,7 @@ int idtx_mte_step(idtx_ctx *c, const float *series, int n_proc, int64_t T, int t
             g.slot_seed.push_back(s->seed);
         }
     }
+    g.plain = s->mode == IDTX_MODE_PLAIN;
     IDTX_TRY(plan(c, g));
     std::vector<unsigned char> arena;
     pack_desc(gs, arena);

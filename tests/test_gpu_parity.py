@@ -118,6 +118,37 @@ def test_nonfinite_input_is_rejected_and_context_survives(idtx):
     _check_problem(idtx, g.x, g.y, g.z, 4, 2, 1)
 
 
+def test_plain_mode_matches_batched_and_oracle(idtx):
+    g = synth.gaussian_problem(700, 1, 1, 3, seed=21)
+    args = (_dev(g.x), _dev(g.y), _dev(g.z))
+    plain = idtx.cmi_ksg(*args, k=4, n_surr=9, seed=3, mode=idtx.MODE_PLAIN).cpu().numpy()
+    batched = idtx.cmi_ksg(*args, k=4, n_surr=9, seed=3).cpu().numpy()
+    ref = oracle.cmi_surrogates(g.x, g.y, g.z, 4, 9, 3)
+    assert np.max(np.abs(plain - ref)) < TOL
+    assert np.max(np.abs(plain - batched)) < TOL
+    g = synth.gaussian_problem(300, 2, 2, 0, seed=22)
+    plain = idtx.cmi_ksg(_dev(g.x), _dev(g.y), None, k=7, n_surr=3, seed=4,
+                         mode=idtx.MODE_PLAIN).cpu().numpy()
+    assert np.max(np.abs(plain - oracle.cmi_surrogates(g.x, g.y, None, 7, 3, 4))) < TOL
+
+
+def test_plain_greedy_step_matches_batched(idtx):
+    net = synth.var_network(n_nodes=4, order=2, T=500, density=0.5, weight=0.6, seed=5)
+    a, ea = idtx.mte_step(_dev(net.series), 1, 1, 1, 2, (), 0, k=4, n_surr=10, seed=2,
+                          want_estimates=True)
+    b, eb = idtx.mte_step(_dev(net.series), 1, 1, 1, 2, (), 0, k=4, n_surr=10, seed=2,
+                          want_estimates=True, mode=idtx.MODE_PLAIN)
+    ok = ~np.isnan(ea[:, 0])
+    assert np.max(np.abs(ea[ok] - eb[ok])) < TOL
+    assert a[0] == b[0] and a[1] == b[1] and a[3] == b[3]
+
+
+def test_unknown_mode_is_rejected(idtx):
+    g = synth.gaussian_problem(100, 1, 1, 1, seed=1)
+    with pytest.raises(idtx.IdtxError):
+        idtx.cmi_ksg(_dev(g.x), _dev(g.y), _dev(g.z), k=4, n_surr=1, mode=7)
+
+
 def test_batch_uneven(idtx):
     probs = synth.batch_problems(n_probs=6, n_min=150, n_max=900, n_surr=5, dz_max=8, seed=77)
     out = idtx.cmi_batch([dict(x=_dev(p.x), y=_dev(p.y), z=_dev(p.z), n_surr=p.n_surr,
