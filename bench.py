@@ -29,6 +29,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "KSG CMI estimates/s incl. surrogates (N=1e4,k=4); batched/screened vs plain"
 N_SMS = 152
+# DRAM bytes (read + write) of one fused-kernel launch of the 200-surrogate step,
+# from the ncu capture summarised in profiles/ksg_fused_kernel_greedy_step_small.md
+# (15-surrogate case, 31.37 MB, scaled by job groups 296/24).  Set to None when the
+# kernel changes until it is captured again.
+FUSED_TRAFFIC_BYTES = 386.9e6
 LANES_PER_SM = 128  # 4 sub-partitions x 32 lanes: one warp instruction per clock each
 
 WORKLOAD = dict(n_proc=10, order=5, T=10000, n_past=3, min_lag=1, max_lag=5, k=4, n_surr=200,
@@ -160,7 +165,7 @@ def run_reference(args):
 def _config():
     w = WORKLOAD
     return {"workload": "greedy mTE step: 10-node sparse VAR(5), T=10000, target 0, "
-                        "lags 1..5, history 3, k=4, 200 surrogates",
+                        f"lags 1..5, history 3, k=4, {w['n_surr']} surrogates",
             "n_proc": w["n_proc"], "T": w["T"], "N": w["T"] - max(w["max_lag"], w["n_past"]),
             "candidates": 47, "n_surr": w["n_surr"], "k": w["k"], "joint_dim": 5,
             "estimates_per_step": 47 * (1 + w["n_surr"]),
@@ -269,8 +274,10 @@ def run_ours(args):
     peak = N_SMS * LANES_PER_SM * sm_mhz * 1e6 / 1e12
     achieved = st["fused_lane_ops"] / (st["fused_ms"] / 1e3) / 1e12 if st["fused_ms"] else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": None,
-                "kernel": "ksg_fused_kernel<1,1,4,5,true,16>",
+                "frac": (achieved / peak) if achieved else None,
+                "traffic": FUSED_TRAFFIC_BYTES if w["n_surr"] == 200 else None,
+                "traffic_unit": "bytes per launch (ncu, scaled from the 15-surrogate case)",
+                "kernel": "ksg_fused_kernel<DX=1,DY=1,DZ=3,K1=5,exact,QW=2,NW=16>",
                 "peak_basis": f"{N_SMS} SMs x {LANES_PER_SM} lanes x median SM clock "
                               f"{sm_mhz:.0f} MHz under load (issue-slot peak)",
                 "fused_share_of_step": st["fused_ms"] / ms if ms else None,
@@ -304,7 +311,11 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n-surr", type=int, default=WORKLOAD["n_surr"],
+                    help="surrogates per candidate (200 is the benchmarked workload; smaller "
+                         "values give a small case for profiling)")
     args = ap.parse_args()
+    WORKLOAD["n_surr"] = args.n_surr
     if args.impl == "reference":
         run_reference(args)
     else:
