@@ -77,6 +77,12 @@ def _load():
                                           ctypes.c_int, ctypes.POINTER(OrcStep),
                                           ctypes.POINTER(ctypes.c_int), _I32P,
                                           ctypes.POINTER(ctypes.c_int), _F64P]
+        lib.orc_bf16_round.argtypes = [ctypes.c_float]
+        lib.orc_bf16_round.restype = ctypes.c_float
+        lib.orc_mlp_forward.argtypes = [_F32P, ctypes.c_int, ctypes.c_int, _F32P, _F32P, _F32P,
+                                        ctypes.c_int64, ctypes.c_int, _F64P]
+        lib.orc_mlp_loss_grad.argtypes = [_F32P, ctypes.c_int, ctypes.c_int, _F32P, _F32P, _F32P,
+                                          _F32P, ctypes.c_int64, ctypes.c_int, _F64P, _F64P]
         lib.orc_num_threads.restype = ctypes.c_int
         lib.orc_set_num_threads.argtypes = [ctypes.c_int]
         _lib = lib
@@ -224,3 +230,43 @@ def num_threads() -> int:
 
 def set_num_threads(t: int) -> None:
     _load().orc_set_num_threads(int(t))
+
+
+# ----------------------------------------------------------------- learned screen
+def mlp_nparams(f: int, h: int) -> int:
+    return h * f + h + h * h + h + h + 1
+
+
+def bf16_round(v: float) -> float:
+    """Round an fp32 value to bfloat16 (nearest, ties to even), returned as fp32."""
+    return float(_load().orc_bf16_round(float(v)))
+
+
+def mlp_forward(params, f, h, mean, scale, x, bf16: bool = True) -> np.ndarray:
+    """Predictions of the screen network (weight matrices rounded to bf16 unless
+    bf16=False; fp64 math)."""
+    p = np.ascontiguousarray(np.asarray(params, np.float32))
+    x = np.ascontiguousarray(np.asarray(x, np.float32).reshape(-1, f))
+    mean = np.ascontiguousarray(np.asarray(mean, np.float32))
+    scale = np.ascontiguousarray(np.asarray(scale, np.float32))
+    y = np.empty(x.shape[0], np.float64)
+    if _load().orc_mlp_forward(_fp(p), f, h, _fp(mean), _fp(scale), _fp(x), x.shape[0],
+                               1 if bf16 else 0, y.ctypes.data_as(_F64P)) != 0:
+        raise ValueError("orc_mlp_forward: invalid arguments")
+    return y
+
+
+def mlp_loss_grad(params, f, h, mean, scale, x, t, bf16: bool = True):
+    """(mean squared error, gradient [n_params]) in fp64."""
+    p = np.ascontiguousarray(np.asarray(params, np.float32))
+    x = np.ascontiguousarray(np.asarray(x, np.float32).reshape(-1, f))
+    t = np.ascontiguousarray(np.asarray(t, np.float32))
+    mean = np.ascontiguousarray(np.asarray(mean, np.float32))
+    scale = np.ascontiguousarray(np.asarray(scale, np.float32))
+    loss = ctypes.c_double()
+    g = np.empty(mlp_nparams(f, h), np.float64)
+    if _load().orc_mlp_loss_grad(_fp(p), f, h, _fp(mean), _fp(scale), _fp(x), _fp(t),
+                                 x.shape[0], 1 if bf16 else 0, ctypes.byref(loss),
+                                 g.ctypes.data_as(_F64P)) != 0:
+        raise ValueError("orc_mlp_loss_grad: invalid arguments")
+    return loss.value, g

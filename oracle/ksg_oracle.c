@@ -422,3 +422,157 @@ void orc_set_num_threads(int t)
     (void)t;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* Learned screen: a 3-layer perceptron F -> H -> H -> 1 with ReLU, used to   */
+/* predict a candidate's largest surrogate estimate (no counterpart in the    */
+/* paper; the network and its training are the build's own addition).        */
+/* Parameters, flat: W1[H][F], b1[H], W2[H][H], b2[H], w3[H], b3.             */
+/* The forward pass uses the weights rounded to bfloat16 (round to nearest,  */
+/* ties to even, from the format: keep the top 16 bits of the fp32 pattern    */
+/* after adding 0x7FFF plus the lowest kept bit); biases stay fp32.  This     */
+/* oracle computes in double.  Inputs are normalised x' = (x - mean) * scale. */
+/* Pinned by: finite differences of the loss; bfloat16 rounding against a    */
+/* library conversion.                                                        */
+/* ------------------------------------------------------------------------ */
+float orc_bf16_round(float v)
+{
+    uint32_t u;
+    memcpy(&u, &v, 4);
+    if ((u & 0x7F800000u) == 0x7F800000u) return v; /* inf / nan unchanged */
+    uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7FFFu + lsb;
+    u &= 0xFFFF0000u;
+    float r;
+    memcpy(&r, &u, 4);
+    return r;
+}
+
+static int orc_mlp_nparams(int f, int h) { return h * f + h + h * h + h + h + 1; }
+
+/* Weights as the forward pass sees them: matrices rounded to bf16 (when bf16 is
+ * set), biases kept. */
+static double orc_w(float v, int bf16) { return (double)(bf16 ? orc_bf16_round(v) : v); }
+
+static void orc_mlp_effective(const float *p, int f, int h, double *q, int bf16)
+{
+    int o = 0;
+    for (int i = 0; i < h * f; ++i, ++o) q[o] = orc_w(p[o], bf16);
+    for (int i = 0; i < h; ++i, ++o) q[o] = (double)p[o];
+    for (int i = 0; i < h * h; ++i, ++o) q[o] = orc_w(p[o], bf16);
+    for (int i = 0; i < h; ++i, ++o) q[o] = (double)p[o];
+    for (int i = 0; i < h; ++i, ++o) q[o] = orc_w(p[o], bf16);
+    q[o] = (double)p[o];
+}
+
+/* y[n] = network(normalised x[n][f]); bf16 selects bf16-rounded weight matrices. */
+int orc_mlp_forward(const float *p, int f, int h, const float *mean, const float *scale,
+                    const float *x, int64_t n, int bf16, double *y)
+{
+    if (!p || !x || !y || f < 1 || h < 1 || n < 0) return -1;
+    int np = orc_mlp_nparams(f, h);
+    double *q = (double *)malloc(sizeof(double) * (size_t)np);
+    double *a1 = (double *)malloc(sizeof(double) * (size_t)h);
+    double *a2 = (double *)malloc(sizeof(double) * (size_t)h);
+    double *xn = (double *)malloc(sizeof(double) * (size_t)f);
+    orc_mlp_effective(p, f, h, q, bf16);
+    const double *W1 = q, *b1 = q + h * f, *W2 = b1 + h, *b2 = W2 + h * h, *w3 = b2 + h,
+                 *b3 = w3 + h;
+    for (int64_t s = 0; s < n; ++s) {
+        for (int i = 0; i < f; ++i)
+            xn[i] = ((double)x[s * f + i] - (double)mean[i]) * (double)scale[i];
+        for (int j = 0; j < h; ++j) {
+            double acc = b1[j];
+            for (int i = 0; i < f; ++i) acc += W1[j * f + i] * xn[i];
+            a1[j] = acc > 0.0 ? acc : 0.0;
+        }
+        for (int j = 0; j < h; ++j) {
+            double acc = b2[j];
+            for (int i = 0; i < h; ++i) acc += W2[j * h + i] * a1[i];
+            a2[j] = acc > 0.0 ? acc : 0.0;
+        }
+        double out = b3[0];
+        for (int j = 0; j < h; ++j) out += w3[j] * a2[j];
+        y[s] = out;
+    }
+    free(q);
+    free(a1);
+    free(a2);
+    free(xn);
+    return 0;
+}
+
+/* Mean squared error L = (1/n) sum (y - t)^2 and its gradient with respect to
+ * every parameter (derivatives taken through the bf16-rounded weights, i.e.
+ * d L / d p evaluated at the rounded values, the rounding treated as identity). */
+int orc_mlp_loss_grad(const float *p, int f, int h, const float *mean, const float *scale,
+                      const float *x, const float *t, int64_t n, int bf16, double *loss,
+                      double *grad)
+{
+    if (!p || !x || !t || !loss || !grad || f < 1 || h < 1 || n < 1) return -1;
+    int np = orc_mlp_nparams(f, h);
+    double *q = (double *)malloc(sizeof(double) * (size_t)np);
+    double *z1 = (double *)malloc(sizeof(double) * (size_t)h);
+    double *a1 = (double *)malloc(sizeof(double) * (size_t)h);
+    double *z2 = (double *)malloc(sizeof(double) * (size_t)h);
+    double *a2 = (double *)malloc(sizeof(double) * (size_t)h);
+    double *d2 = (double *)malloc(sizeof(double) * (size_t)h);
+    double *d1 = (double *)malloc(sizeof(double) * (size_t)h);
+    double *xn = (double *)malloc(sizeof(double) * (size_t)f);
+    orc_mlp_effective(p, f, h, q, bf16);
+    const double *W1 = q, *b1 = q + h * f, *W2 = b1 + h, *b2 = W2 + h * h, *w3 = b2 + h,
+                 *b3 = w3 + h;
+    double *gW1 = grad, *gb1 = grad + h * f, *gW2 = gb1 + h, *gb2 = gW2 + h * h, *gw3 = gb2 + h,
+           *gb3 = gw3 + h;
+    for (int i = 0; i < np; ++i) grad[i] = 0.0;
+    double l = 0.0;
+    for (int64_t s = 0; s < n; ++s) {
+        for (int i = 0; i < f; ++i)
+            xn[i] = ((double)x[s * f + i] - (double)mean[i]) * (double)scale[i];
+        for (int j = 0; j < h; ++j) {
+            double acc = b1[j];
+            for (int i = 0; i < f; ++i) acc += W1[j * f + i] * xn[i];
+            z1[j] = acc;
+            a1[j] = acc > 0.0 ? acc : 0.0;
+        }
+        for (int j = 0; j < h; ++j) {
+            double acc = b2[j];
+            for (int i = 0; i < h; ++i) acc += W2[j * h + i] * a1[i];
+            z2[j] = acc;
+            a2[j] = acc > 0.0 ? acc : 0.0;
+        }
+        double y = b3[0];
+        for (int j = 0; j < h; ++j) y += w3[j] * a2[j];
+        double r = y - (double)t[s];
+        l += r * r;
+        double dy = 2.0 * r / (double)n;
+        gb3[0] += dy;
+        for (int j = 0; j < h; ++j) {
+            gw3[j] += dy * a2[j];
+            d2[j] = z2[j] > 0.0 ? dy * w3[j] : 0.0;
+        }
+        for (int j = 0; j < h; ++j) {
+            gb2[j] += d2[j];
+            for (int i = 0; i < h; ++i) gW2[j * h + i] += d2[j] * a1[i];
+        }
+        for (int i = 0; i < h; ++i) {
+            double acc = 0.0;
+            for (int j = 0; j < h; ++j) acc += W2[j * h + i] * d2[j];
+            d1[i] = z1[i] > 0.0 ? acc : 0.0;
+        }
+        for (int j = 0; j < h; ++j) {
+            gb1[j] += d1[j];
+            for (int i = 0; i < f; ++i) gW1[j * f + i] += d1[j] * xn[i];
+        }
+    }
+    *loss = l / (double)n;
+    free(q);
+    free(z1);
+    free(a1);
+    free(z2);
+    free(a2);
+    free(d2);
+    free(d1);
+    free(xn);
+    return 0;
+}

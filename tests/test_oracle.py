@@ -278,3 +278,82 @@ def test_greedy_first_step_gate_from_estimates():
     assert cand == c_best and stat == t_obs
     assert pval == np.count_nonzero(t_s >= t_obs) / S
     assert sig == (pval < 0.05)
+
+
+# ---------------------------------------------------------------- learned screen network
+def _rand_net(f, h, seed):
+    rng = np.random.default_rng(seed)
+    p = (rng.standard_normal(oracle.mlp_nparams(f, h)) * 0.4).astype(np.float32)
+    x = rng.standard_normal((37, f)).astype(np.float32)
+    t = rng.standard_normal(37).astype(np.float32)
+    mean = rng.standard_normal(f).astype(np.float32) * 0.1
+    scale = (1.0 + rng.random(f)).astype(np.float32)
+    return p, x, t, mean, scale
+
+
+def test_bf16_rounding_matches_library_conversion():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(3)
+    v = np.concatenate([rng.standard_normal(5000).astype(np.float32) * 10.0 ** rng.integers(-5, 5, 5000),
+                        # exact ties: a bf16 value plus half an ulp of bf16
+                        np.array([1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, -3.0 - 2.0 ** -7], np.float32)])
+    ref = torch.from_numpy(v).to(torch.bfloat16).to(torch.float32).numpy()
+    got = np.array([oracle.bf16_round(float(a)) for a in v], np.float32)
+    assert np.array_equal(got, ref)
+
+
+def test_mlp_gradient_matches_finite_differences():
+    f, h = 3, 5
+    p, x, t, mean, scale = _rand_net(f, h, 1)
+    loss, g = oracle.mlp_loss_grad(p, f, h, mean, scale, x, t, bf16=False)
+
+    def fd(idx, eps):
+        hi, lo = p.copy(), p.copy()
+        hi[idx] += np.float32(eps)
+        lo[idx] -= np.float32(eps)
+        step = float(hi[idx]) - float(lo[idx])
+        lh, _ = oracle.mlp_loss_grad(hi, f, h, mean, scale, x, t, bf16=False)
+        ll, _ = oracle.mlp_loss_grad(lo, f, h, mean, scale, x, t, bf16=False)
+        return (lh - ll) / step
+
+    checked = 0
+    for idx in range(len(p)):
+        a, b = fd(idx, 1e-3), fd(idx, 5e-4)
+        if abs(a - b) > 1e-6:      # a ReLU kink inside the interval: not differentiable there
+            continue
+        assert abs(a - g[idx]) <= 1e-5 * max(1.0, abs(g[idx])), (idx, a, g[idx])
+        checked += 1
+    assert checked >= 0.8 * len(p)
+
+
+def test_mlp_bf16_forward_equals_exact_forward_on_rounded_weights():
+    f, h = 10, 64
+    p, x, t, mean, scale = _rand_net(f, h, 4)
+    pr = p.copy()
+    nw = [(0, h * f), (h * f + h, h * f + h + h * h), (h * f + 2 * h + h * h, h * f + 3 * h + h * h)]
+    for a, b in nw:
+        pr[a:b] = [oracle.bf16_round(float(v)) for v in p[a:b]]
+    y1 = oracle.mlp_forward(p, f, h, mean, scale, x, bf16=True)
+    y2 = oracle.mlp_forward(pr, f, h, mean, scale, x, bf16=False)
+    assert np.array_equal(y1, y2)
+    l1, g1 = oracle.mlp_loss_grad(p, f, h, mean, scale, x, t, bf16=True)
+    l2, g2 = oracle.mlp_loss_grad(pr, f, h, mean, scale, x, t, bf16=False)
+    assert l1 == l2 and np.array_equal(g1, g2)
+
+
+def test_mlp_forward_closed_form_linear_case():
+    # with all hidden pre-activations positive the network is affine: check by hand
+    f, h = 2, 2
+    W1 = np.array([[1.0, 0.5], [0.25, 2.0]], np.float32)
+    b1 = np.array([3.0, 3.0], np.float32)
+    W2 = np.array([[1.0, 0.0], [0.5, 0.5]], np.float32)
+    b2 = np.array([0.0, 1.0], np.float32)
+    w3 = np.array([2.0, -1.0], np.float32)
+    b3 = np.array([0.5], np.float32)
+    p = np.concatenate([W1.ravel(), b1, W2.ravel(), b2, w3, b3])
+    x = np.array([[1.0, 0.0], [0.0, 1.0]], np.float32)
+    y = oracle.mlp_forward(p, f, h, np.zeros(2, np.float32), np.ones(2, np.float32), x)
+    for s in range(2):
+        a1 = W1 @ x[s] + b1
+        a2 = W2 @ a1 + b2
+        assert abs(y[s] - (w3 @ a2 + b3[0])) < 1e-12
