@@ -77,6 +77,13 @@ typedef struct idtx_ctx idtx_ctx;
  *   no sharing between estimates (the reference point for batching). */
 #define IDTX_MODE_BATCHED 0
 #define IDTX_MODE_PLAIN 1
+/* IDTX_MODE_SCREENED (greedy calls only, no counterpart in the paper): every
+ *   candidate first gets its estimate and the screen's s0 cheap surrogates; a
+ *   small network (idtx_screen) predicts each candidate's largest surrogate
+ *   estimate q, and only candidates with q + delta >= T_obs get the remaining
+ *   surrogates.  Whenever the prediction bound holds for the skipped
+ *   candidates the gate's count, and so the decision, equals batched mode's. */
+#define IDTX_MODE_SCREENED 2
 
 /* Estimation settings.  k: neighbours (1 <= k <= min(N-1, IDTX_MAX_K));
  * n_surr: surrogates per estimate (>= 0; the greedy calls need >= 1);
@@ -180,6 +187,9 @@ typedef struct {
     int32_t significant; /* 1 if p < alpha */
     double stat;         /* T_obs = max over candidates of I(X_c;Y|Z) */
     double pval;         /* #{s : max_c I(X_c o pi_{c,s};Y|Z) >= T_obs} / n_surr */
+    int32_t n_cand;      /* candidates evaluated */
+    int32_t n_full;      /* candidates given all n_surr surrogates (screened mode:
+                            the others got only the screen's s0) */
 } idtx_step;
 
 /* One step of the greedy parent selection for one target (Summary, paragraph
@@ -210,6 +220,55 @@ int idtx_mte_select_target(idtx_ctx *ctx, const float *series, int n_proc, int64
                            int n_past, int min_lag, int max_lag, const idtx_settings *settings,
                            int max_parents, int32_t *parents_out, int *n_parents,
                            idtx_step *steps_out, int *n_steps, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Learned screen (no counterpart in the paper).                            */
+/* A perceptron F -> H -> H -> 1 with ReLU.  Parameters, flat fp32 master    */
+/* values: W1[H][F], b1[H], W2[H][H], b2[H], w3[H], b3.  The forward pass     */
+/* uses the weight matrices rounded to bfloat16 (round to nearest even) with */
+/* fp32 arithmetic; biases stay fp32.  Features of candidate c, with I_c its */
+/* estimate and I_c,0..s0-1 its first s0 surrogate estimates (streams of the */
+/* step): x = (I_c, ln N, dx, dy, dz, k, mean_s I_c,s, std_s I_c,s (divisor   */
+/* s0), max_s I_c,s, ln n_surr), normalised as (x - feat_mean) * feat_scale. */
+/* The network predicts max over all n_surr surrogates of I_c,s.             */
+/* ------------------------------------------------------------------------ */
+#define IDTX_SCREEN_F 10
+#define IDTX_SCREEN_H 64
+#define IDTX_SCREEN_NPARAMS                                                              \
+    (IDTX_SCREEN_H * IDTX_SCREEN_F + IDTX_SCREEN_H + IDTX_SCREEN_H * IDTX_SCREEN_H +      \
+     IDTX_SCREEN_H + IDTX_SCREEN_H + 1)
+
+typedef struct {
+    float params[IDTX_SCREEN_NPARAMS];
+    float feat_mean[IDTX_SCREEN_F];
+    float feat_scale[IDTX_SCREEN_F];
+    float delta;   /* margin added to the prediction before the comparison with T_obs */
+    int32_t s0;    /* cheap surrogates per candidate (1 <= s0 < n_surr) */
+} idtx_screen;
+
+/* Predictions (without delta) for n feature rows feats[n][IDTX_SCREEN_F]
+ * (host or device memory); out[n] fp32 (host or device). */
+int idtx_screen_predict(idtx_ctx *ctx, const idtx_screen *screen, const float *feats, int n,
+                        float *out, void *stream);
+
+/* Mean squared error over n rows and its gradient grad[IDTX_SCREEN_NPARAMS]
+ * (host memory) with respect to the master parameters, taken through the
+ * bf16-rounded weights (rounding treated as the identity). */
+int idtx_screen_loss_grad(idtx_ctx *ctx, const idtx_screen *screen, const float *feats,
+                          const float *targets, int n, double *loss, float *grad, void *stream);
+
+/* Train screen->params in place on the GPU: `epochs` passes of Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8, step size lr) over mini-batches of
+ * `batch` rows in an order reshuffled every epoch (the Fisher-Yates shuffle
+ * of the surrogates, seed `seed`, stream = epoch).  *final_loss (nullable)
+ * receives the full-data loss after training.  feat_mean, feat_scale, delta
+ * and s0 are left as given. */
+int idtx_screen_train(idtx_ctx *ctx, idtx_screen *screen, const float *feats,
+                      const float *targets, int n, int epochs, int batch, float lr, uint64_t seed,
+                      double *final_loss, void *stream);
+
+/* Install the screen used by IDTX_MODE_SCREENED on this context (copied). */
+int idtx_screen_set(idtx_ctx *ctx, const idtx_screen *screen);
 
 /* Allocation-free estimate (no counterpart in the paper; it exists for
  * callers that cannot allocate device memory -- code whose memory pool owns

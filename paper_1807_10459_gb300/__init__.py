@@ -18,7 +18,8 @@ import threading
 import numpy as np
 
 __all__ = ["IdtxError", "Settings", "Context", "load", "cmi_ksg", "cmi_batch", "mte_step",
-           "mte_select_target", "library_path"]
+           "mte_select_target", "library_path", "Screen", "screen_predict", "screen_loss_grad",
+           "screen_train", "screen_set", "StepResult"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libidtx.so")
@@ -27,7 +28,9 @@ _lib = None
 _default_ctx = {}
 
 IDTX_OK, IDTX_EINVAL, IDTX_ENOMEM, IDTX_ECUDA, IDTX_ETIMEOUT, IDTX_EINTERNAL = range(6)
-MODE_BATCHED, MODE_PLAIN = 0, 1
+MODE_BATCHED, MODE_PLAIN, MODE_SCREENED = 0, 1, 2
+SCREEN_F, SCREEN_H = 10, 64
+SCREEN_NPARAMS = SCREEN_H * SCREEN_F + SCREEN_H + SCREEN_H * SCREEN_H + SCREEN_H + SCREEN_H + 1
 _ERR_NAMES = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EINTERNAL"}
 
 
@@ -61,7 +64,15 @@ class Stats(ctypes.Structure):
 
 class Step(ctypes.Structure):
     _fields_ = [("cand", ctypes.c_int32), ("significant", ctypes.c_int32),
-                ("stat", ctypes.c_double), ("pval", ctypes.c_double)]
+                ("stat", ctypes.c_double), ("pval", ctypes.c_double),
+                ("n_cand", ctypes.c_int32), ("n_full", ctypes.c_int32)]
+
+
+class ScreenC(ctypes.Structure):
+    _fields_ = [("params", ctypes.c_float * SCREEN_NPARAMS),
+                ("feat_mean", ctypes.c_float * SCREEN_F),
+                ("feat_scale", ctypes.c_float * SCREEN_F),
+                ("delta", ctypes.c_float), ("s0", ctypes.c_int32)]
 
 
 def library_path() -> str:
@@ -91,10 +102,18 @@ def load():
                                                ctypes.POINTER(Settings), i32, vp,
                                                ctypes.POINTER(i32), ctypes.POINTER(Step),
                                                ctypes.POINTER(i32), vp]
+        lib.idtx_screen_predict.argtypes = [vp, ctypes.POINTER(ScreenC), vp, i32, vp, vp]
+        lib.idtx_screen_loss_grad.argtypes = [vp, ctypes.POINTER(ScreenC), vp, vp, i32,
+                                              ctypes.POINTER(ctypes.c_double), vp, vp]
+        lib.idtx_screen_train.argtypes = [vp, ctypes.POINTER(ScreenC), vp, vp, i32, i32, i32,
+                                          ctypes.c_float, u64, ctypes.POINTER(ctypes.c_double),
+                                          vp]
+        lib.idtx_screen_set.argtypes = [vp, ctypes.POINTER(ScreenC)]
         lib.idtx_ctx_set_profiling.argtypes = [vp, i32]
         lib.idtx_ctx_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
         lib.idtx_ctx_reset_stats.argtypes = [vp]
-        for name in ("idtx_ctx_set_profiling", "idtx_ctx_get_stats", "idtx_ctx_reset_stats",
+        for name in ("idtx_screen_predict", "idtx_screen_loss_grad", "idtx_screen_train",
+                     "idtx_screen_set", "idtx_ctx_set_profiling", "idtx_ctx_get_stats", "idtx_ctx_reset_stats",
                      "idtx_ctx_create", "idtx_ctx_destroy", "idtx_cmi_ksg", "idtx_cmi_batch",
                      "idtx_mte_step", "idtx_mte_select_target", "idtx_version"):
             getattr(lib, name).restype = ctypes.c_int
@@ -154,6 +173,104 @@ def default_context(device: int = 0) -> Context:
         with _lock:
             _default_ctx[device] = ctx
     return ctx
+
+
+class StepResult(tuple):
+    """(cand, significant, stat, pval) of one greedy step, with .n_cand and .n_full."""
+
+    def __new__(cls, cand, significant, stat, pval, n_cand=0, n_full=0):
+        obj = super().__new__(cls, (cand, significant, stat, pval))
+        obj.n_cand = n_cand
+        obj.n_full = n_full
+        return obj
+
+
+class Screen:
+    """Learned screen: network parameters (fp32 master values), feature
+    normalisation, margin delta and cheap-surrogate count s0 (idtx_screen)."""
+
+    def __init__(self, params=None, feat_mean=None, feat_scale=None, delta=0.0, s0=8,
+                 seed=0):
+        if params is None:
+            rng = np.random.default_rng(seed)
+            params = np.zeros(SCREEN_NPARAMS, np.float32)
+            # He-style initial weights, zero biases
+            o = 0
+            for (fan_in, fan_out) in ((SCREEN_F, SCREEN_H), (SCREEN_H, SCREEN_H), (SCREEN_H, 1)):
+                params[o:o + fan_in * fan_out] = rng.standard_normal(fan_in * fan_out) * \
+                    np.sqrt(2.0 / fan_in)
+                o += fan_in * fan_out + fan_out
+        self.params = np.ascontiguousarray(np.asarray(params, np.float32))
+        self.feat_mean = np.asarray(feat_mean if feat_mean is not None else np.zeros(SCREEN_F),
+                                    np.float32)
+        self.feat_scale = np.asarray(feat_scale if feat_scale is not None else np.ones(SCREEN_F),
+                                     np.float32)
+        self.delta = float(delta)
+        self.s0 = int(s0)
+
+    def to_c(self) -> ScreenC:
+        c = ScreenC()
+        ctypes.memmove(c.params, self.params.ctypes.data, self.params.nbytes)
+        ctypes.memmove(c.feat_mean, self.feat_mean.ctypes.data, self.feat_mean.nbytes)
+        ctypes.memmove(c.feat_scale, self.feat_scale.ctypes.data, self.feat_scale.nbytes)
+        c.delta = self.delta
+        c.s0 = self.s0
+        return c
+
+    def save(self, path: str, **meta):
+        np.savez(path, params=self.params, feat_mean=self.feat_mean, feat_scale=self.feat_scale,
+                 delta=np.float32(self.delta), s0=np.int32(self.s0),
+                 meta=np.array(repr(meta)))
+
+    @classmethod
+    def load(cls, path: str) -> "Screen":
+        d = np.load(path)
+        return cls(d["params"], d["feat_mean"], d["feat_scale"], float(d["delta"]), int(d["s0"]))
+
+
+def screen_predict(screen: Screen, feats, ctx: Context | None = None) -> np.ndarray:
+    f = np.ascontiguousarray(np.asarray(feats, np.float32).reshape(-1, SCREEN_F))
+    out = np.empty(f.shape[0], np.float32)
+    ctx = ctx or default_context(0)
+    sc = screen.to_c()
+    _check(load().idtx_screen_predict(ctx.handle, ctypes.byref(sc), f.ctypes.data, f.shape[0],
+                                      out.ctypes.data, None))
+    return out
+
+
+def screen_loss_grad(screen: Screen, feats, targets, ctx: Context | None = None):
+    f = np.ascontiguousarray(np.asarray(feats, np.float32).reshape(-1, SCREEN_F))
+    t = np.ascontiguousarray(np.asarray(targets, np.float32))
+    g = np.empty(SCREEN_NPARAMS, np.float32)
+    loss = ctypes.c_double()
+    ctx = ctx or default_context(0)
+    sc = screen.to_c()
+    _check(load().idtx_screen_loss_grad(ctx.handle, ctypes.byref(sc), f.ctypes.data,
+                                        t.ctypes.data, f.shape[0], ctypes.byref(loss),
+                                        g.ctypes.data, None))
+    return loss.value, g
+
+
+def screen_train(screen: Screen, feats, targets, epochs=100, batch=256, lr=1e-3, seed=0,
+                 ctx: Context | None = None) -> float:
+    """Train screen.params in place on the GPU; returns the final full-data loss."""
+    f = np.ascontiguousarray(np.asarray(feats, np.float32).reshape(-1, SCREEN_F))
+    t = np.ascontiguousarray(np.asarray(targets, np.float32))
+    ctx = ctx or default_context(0)
+    sc = screen.to_c()
+    loss = ctypes.c_double()
+    _check(load().idtx_screen_train(ctx.handle, ctypes.byref(sc), f.ctypes.data, t.ctypes.data,
+                                    f.shape[0], int(epochs), int(batch), float(lr),
+                                    ctypes.c_uint64(int(seed)).value, ctypes.byref(loss), None))
+    screen.params = np.ctypeslib.as_array(sc.params).astype(np.float32).copy()
+    return loss.value
+
+
+def screen_set(screen: Screen, ctx: Context | None = None) -> None:
+    """Install the screen used by MODE_SCREENED greedy calls on the context."""
+    ctx = ctx or default_context(0)
+    sc = screen.to_c()
+    _check(load().idtx_screen_set(ctx.handle, ctypes.byref(sc)))
 
 
 # ------------------------------------------------------------------ marshalling
@@ -299,7 +416,8 @@ def mte_step(series, target: int, n_past: int, min_lag: int, max_lag: int, selec
                                 sel.ctypes.data if sel.size else None, int(sel.size),
                                 int(step_index), ctypes.byref(s), ctypes.byref(step), p_est,
                                 _stream_for(series)))
-    res = (int(step.cand), bool(step.significant), float(step.stat), float(step.pval))
+    res = StepResult(int(step.cand), bool(step.significant), float(step.stat),
+                     float(step.pval), int(step.n_cand), int(step.n_full))
     return (res, est) if want_estimates else res
 
 
@@ -320,5 +438,7 @@ def mte_select_target(series, target: int, n_past: int, min_lag: int, max_lag: i
                                          ctypes.byref(n_par), steps, ctypes.byref(n_steps),
                                          _stream_for(series)))
     return dict(parents=[int(p) for p in parents[:n_par.value]],
-                steps=[(int(steps[i].cand), bool(steps[i].significant), float(steps[i].stat),
-                        float(steps[i].pval)) for i in range(n_steps.value)])
+                steps=[StepResult(int(steps[i].cand), bool(steps[i].significant),
+                                  float(steps[i].stat), float(steps[i].pval),
+                                  int(steps[i].n_cand), int(steps[i].n_full))
+                       for i in range(n_steps.value)])

@@ -21,6 +21,7 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 namespace idtx {
@@ -78,6 +79,24 @@ struct KsgVariant {
 cudaError_t sort_pairs_u32(void *tmp, size_t &tmp_bytes, const uint32_t *keys_in,
                            uint32_t *keys_out, const int32_t *vals_in, int32_t *vals_out, int n,
                            int end_bit, cudaStream_t stream);
+
+// Learned-screen network kernels (screen.cu).  A work area holds the batch
+// activations (B rows), the gradient and the bf16 copy of the parameters.
+struct MlpWork {
+    float *xn, *z1, *a1, *z2, *a2, *d2, *d1, *y, *dy, *grad;
+    __nv_bfloat16 *wbf;
+};
+size_t mlp_work_floats(int B);
+void mlp_work_carve(float *base, int B, MlpWork *w);
+cudaError_t mlp_round(const float *params, MlpWork &w, cudaStream_t st);
+cudaError_t mlp_forward(const float *params, MlpWork &w, const float *feats,
+                        const int32_t *order, int64_t start, int B, const float *mean,
+                        const float *scale, cudaStream_t st);
+cudaError_t mlp_loss(MlpWork &w, const float *targets, const int32_t *order, int64_t start, int B,
+                     float dy_scale, bool want_dy, double *loss_acc, cudaStream_t st);
+cudaError_t mlp_backward(MlpWork &w, int B, bool accumulate, cudaStream_t st);
+cudaError_t mlp_adam(float *params, const float *grad, float *m, float *v, int step, float lr,
+                     cudaStream_t st);
 
 // Registries filled by the instantiation units.
 int ksg_variants_d11(KsgVariant *out);

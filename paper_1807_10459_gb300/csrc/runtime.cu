@@ -361,19 +361,25 @@ __global__ void __launch_bounds__(kPlainThreads)
     }
 }
 
-// Max-statistic gate over est[c][1+S] (candidates in ascending id order).
-__global__ void k_gate(const double *est, const int32_t *ids, int n_cand, int n_surr,
-                       double alpha, idtx_step *out)
+// Max-statistic gate.  est_a [n_cand][1 + sa]: every candidate's estimate and
+// its first sa surrogates; est_b [n_keep][n_surr - sa]: the remaining
+// surrogates of the candidates listed in keep (screened mode; n_keep = 0 and
+// sa = n_surr otherwise).  T_obs = largest estimate (ties to the lowest
+// candidate, which comes first); surrogate s's maximum runs over all
+// candidates for s < sa and over the kept ones for s >= sa.
+__global__ void k_gate(const double *est_a, int n_cand, int sa, const double *est_b, int n_keep,
+                       int n_surr, const int32_t *ids, double alpha, idtx_step *out)
 {
     __shared__ double s_tobs;
     __shared__ int s_best;
     __shared__ int s_cnt[32];
     const int tid = threadIdx.x;
+    const int row_a = 1 + sa, row_b = n_surr - sa;
     if (tid == 0) {
         double t = -INFINITY;
         int b = -1;
         for (int c = 0; c < n_cand; ++c) {
-            const double v = est[(int64_t)c * (1 + n_surr)];
+            const double v = est_a[(int64_t)c * row_a];
             if (v > t) {
                 t = v;
                 b = c;
@@ -386,7 +392,11 @@ __global__ void k_gate(const double *est, const int32_t *ids, int n_cand, int n_
     int cnt = 0;
     for (int s = tid; s < n_surr; s += blockDim.x) {
         double ts = -INFINITY;
-        for (int c = 0; c < n_cand; ++c) ts = fmax(ts, est[(int64_t)c * (1 + n_surr) + 1 + s]);
+        if (s < sa) {
+            for (int c = 0; c < n_cand; ++c) ts = fmax(ts, est_a[(int64_t)c * row_a + 1 + s]);
+        } else {
+            for (int c = 0; c < n_keep; ++c) ts = fmax(ts, est_b[(int64_t)c * row_b + s - sa]);
+        }
         cnt += ts >= s_tobs ? 1 : 0;
     }
     for (int off = 16; off >= 1; off >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
@@ -400,7 +410,53 @@ __global__ void k_gate(const double *est, const int32_t *ids, int n_cand, int n_
         out->significant = (s_best >= 0 && p < alpha) ? 1 : 0;
         out->stat = s_tobs;
         out->pval = p;
+        out->n_cand = n_cand;
+        out->n_full = sa == n_surr ? n_cand : n_keep;
     }
+}
+
+// Screen features of every candidate from its estimate and first s0 surrogate
+// estimates (est [n_cand][1+s0]); the definition is the one in idtx.h.
+__global__ void k_screen_features(const double *est, int n_cand, int s0, float ln_n, int dx,
+                                  int dy, int dz, int k, float ln_s, float *feats)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_cand) return;
+    const double *r = est + (int64_t)c * (1 + s0);
+    double mean = 0.0, mx = -INFINITY;
+    for (int s = 0; s < s0; ++s) {
+        mean += r[1 + s];
+        mx = fmax(mx, r[1 + s]);
+    }
+    mean /= s0;
+    double var = 0.0;
+    for (int s = 0; s < s0; ++s) var += (r[1 + s] - mean) * (r[1 + s] - mean);
+    var /= s0;
+    float *f = feats + (int64_t)c * IDTX_SCREEN_F;
+    f[0] = (float)r[0];
+    f[1] = ln_n;
+    f[2] = (float)dx;
+    f[3] = (float)dy;
+    f[4] = (float)dz;
+    f[5] = (float)k;
+    f[6] = (float)mean;
+    f[7] = (float)sqrt(var);
+    f[8] = (float)mx;
+    f[9] = ln_s;
+}
+
+// Keep candidate c iff pred[c] + delta >= T_obs; kept candidates listed in
+// ascending order in keep[], their count in *n_keep (one thread, in order).
+__global__ void k_screen_keep(const double *est, int n_cand, int s0, const float *pred,
+                              float delta, int32_t *keep, int32_t *n_keep)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double t = -INFINITY;
+    for (int c = 0; c < n_cand; ++c) t = fmax(t, est[(int64_t)c * (1 + s0)]);
+    int n = 0;
+    for (int c = 0; c < n_cand; ++c)
+        if ((double)pred[c] + (double)delta >= t) keep[n++] = c;
+    *n_keep = n;
 }
 
 static int grid_for(int64_t total, int block)
@@ -428,6 +484,9 @@ enum {
     B_ORDER,    // sample order along the Morton curve, sort keys, column ranges
     B_SORT,     // radix-sort temporary storage
     B_WORK,     // fused-kernel work counters, kNumWork per group
+    B_SCREEN,   // screen parameters, normalisation, features, predictions, keep list
+    B_MLP,      // screen network work area
+    B_TRAIN,    // screen training data, order, Adam moments
     kNumBufs
 };
 
@@ -455,6 +514,8 @@ struct idtx_ctx {
     std::vector<WorkShape> call_shapes;  // launches of the current call, by work slot
     unsigned long long *h_work = nullptr;  // pinned copy of the counters
     size_t h_work_cap = 0;
+    bool has_screen = false;
+    idtx_screen screen;  // installed by idtx_screen_set
 };
 
 namespace {
@@ -1142,8 +1203,15 @@ int idtx_mte_step(idtx_ctx *c, const float *series, int n_proc, int64_t T, int t
     if (s->k < 1 || s->k > IDTX_MAX_K || s->k > n - 1) return fail(IDTX_EINVAL, "bad k");
     if (s->n_surr < 1 || s->n_surr >= (1 << 24)) return fail(IDTX_EINVAL, "n_surr out of range");
     if (!(s->alpha > 0.0 && s->alpha < 1.0)) return fail(IDTX_EINVAL, "alpha out of (0,1)");
-    if (s->mode != IDTX_MODE_BATCHED && s->mode != IDTX_MODE_PLAIN)
+    if (s->mode != IDTX_MODE_BATCHED && s->mode != IDTX_MODE_PLAIN &&
+        s->mode != IDTX_MODE_SCREENED)
         return fail(IDTX_EINVAL, "unknown mode %d", s->mode);
+    const bool screened = s->mode == IDTX_MODE_SCREENED;
+    if (screened && !c->has_screen)
+        return fail(IDTX_EINVAL, "screened mode needs a screen (idtx_screen_set)");
+    const int s0 = screened ? c->screen.s0 : s->n_surr;
+    if (screened && (s0 < 1 || s0 >= s->n_surr))
+        return fail(IDTX_EINVAL, "screen s0=%d must be in [1, n_surr)", s0);
     const int dz = n_past + n_selected;
     if (dz > IDTX_MAX_DZ) return fail(IDTX_EINVAL, "dz=%d exceeds %d", dz, IDTX_MAX_DZ);
     std::vector<char> alive(n_cand_total, 1);
@@ -1159,71 +1227,139 @@ int idtx_mte_step(idtx_ctx *c, const float *series, int n_proc, int64_t T, int t
         if (alive[cid]) ids.push_back(cid);
     if (ids.empty()) return fail(IDTX_EINVAL, "no candidate left");
     const int n_alive = (int)ids.size();
-    const int n_jobs = n_alive * (1 + s->n_surr);
+    const size_t jobs_a = (size_t)n_alive * (1 + s0);
+    const size_t jobs_b_max = screened ? (size_t)n_alive * (s->n_surr - s0) : 0;
 
     DeviceGuard guard(c->device);
     cudaStream_t st = (cudaStream_t)stream;
     const float *ser = series;
     const bool host_series = !device_accessible(series);
     IDTX_TRY(ensure(c, B_IN, host_series ? (size_t)n_proc * T * sizeof(float) : 0));
-    IDTX_TRY(begin_call(c, 1, st));
+    IDTX_TRY(begin_call(c, screened ? 2 : 1, st));
     if (host_series) {
         IDTX_CUDA(cudaMemcpyAsync(c->buf[B_IN], series, (size_t)n_proc * T * sizeof(float),
                                   cudaMemcpyHostToDevice, st));
         ser = (const float *)c->buf[B_IN];
     }
 
-    std::vector<Group> gs(1);
-    Group &g = gs[0];
-    g.n = n;
-    g.dx = 1;
-    g.dy = 1;
-    g.dz = dz;
-    g.k = s->k;
     // Sample i is time L + i; the variable (p, lag) at sample i is series[p][L + i - lag].
     auto col = [&](int p, int lag) { return Col{ser + (int64_t)p * T, L - lag}; };
-    g.ycols.push_back(col(target, 0));
-    for (int lag = 1; lag <= n_past; ++lag) g.zcols.push_back(col(target, lag));
-    for (int t = 0; t < n_selected; ++t)
-        g.zcols.push_back(col(selected[t] / n_lags, min_lag + selected[t] % n_lags));
-    for (int a = 0; a < n_alive; ++a) {
-        const int cid = ids[a];
-        g.xcols.push_back(col(cid / n_lags, min_lag + cid % n_lags));
-        g.jobs.push_back(Job{a, -1});
-        for (int sidx = 0; sidx < s->n_surr; ++sidx) {
-            g.jobs.push_back(Job{a, (int32_t)g.slot_stream.size()});
-            g.slot_stream.push_back(((uint64_t)step_index << 48) | ((uint64_t)cid << 24) |
-                                    (uint64_t)sidx);
-            g.slot_seed.push_back(s->seed);
+    auto stream_of = [&](int cid, int sidx) {
+        return ((uint64_t)step_index << 48) | ((uint64_t)cid << 24) | (uint64_t)sidx;
+    };
+    // One group of jobs over candidates cand[] (indices into ids), surrogates [s_lo, s_hi);
+    // with_orig adds each candidate's estimate before its surrogates.
+    auto make_group = [&](Group &g, const std::vector<int> &cand, bool with_orig, int s_lo,
+                          int s_hi) {
+        g.n = n;
+        g.dx = 1;
+        g.dy = 1;
+        g.dz = dz;
+        g.k = s->k;
+        g.ycols.push_back(col(target, 0));
+        for (int lag = 1; lag <= n_past; ++lag) g.zcols.push_back(col(target, lag));
+        for (int t = 0; t < n_selected; ++t)
+            g.zcols.push_back(col(selected[t] / n_lags, min_lag + selected[t] % n_lags));
+        for (size_t a = 0; a < cand.size(); ++a) {
+            const int cid = ids[cand[a]];
+            g.xcols.push_back(col(cid / n_lags, min_lag + cid % n_lags));
+            if (with_orig) g.jobs.push_back(Job{(int32_t)a, -1});
+            for (int sidx = s_lo; sidx < s_hi; ++sidx) {
+                g.jobs.push_back(Job{(int32_t)a, (int32_t)g.slot_stream.size()});
+                g.slot_stream.push_back(stream_of(cid, sidx));
+                g.slot_seed.push_back(s->seed);
+            }
+        }
+        g.plain = s->mode == IDTX_MODE_PLAIN;
+    };
+    auto upload = [&](std::vector<Group> &gs, std::vector<unsigned char> &arena,
+                      size_t cmi_bytes) -> int {
+        pack_desc(gs, arena);
+        CallBuffers b;
+        for (const Group &g : gs) sizes_of(g, b);
+        IDTX_TRY(ensure(c, B_DESC, arena.size()));
+        IDTX_TRY(ensure(c, B_SH, b.sh));
+        IDTX_TRY(ensure(c, B_XI, b.xi));
+        IDTX_TRY(ensure(c, B_PERM, b.perm));
+        IDTX_TRY(ensure(c, B_PARTIAL, b.partial));
+        IDTX_TRY(ensure(c, B_ORDER, b.order));
+        IDTX_TRY(ensure(c, B_SORT, b.sort_tmp));
+        IDTX_TRY(ensure(c, B_CMI, cmi_bytes));
+        IDTX_CUDA(cudaMemcpyAsync(c->buf[B_DESC], arena.data(), arena.size(),
+                                  cudaMemcpyHostToDevice, st));
+        return IDTX_OK;
+    };
+
+    std::vector<int> all(n_alive);
+    for (int a = 0; a < n_alive; ++a) all[a] = a;
+    std::vector<Group> ga(1);
+    make_group(ga[0], all, true, 0, s0);
+    IDTX_TRY(plan(c, ga[0]));
+    const size_t cmi_bytes = (jobs_a + jobs_b_max) * sizeof(double);
+    IDTX_TRY(ensure(c, B_STEP, sizeof(idtx_step) + (size_t)n_cand_total * sizeof(int32_t) + 64));
+    IDTX_TRY(ensure_psi(c, std::max<int64_t>(n, s->k) + 1, st));
+    std::vector<unsigned char> arena;
+    IDTX_TRY(upload(ga, arena, cmi_bytes));
+    double *cmi_a = (double *)c->buf[B_CMI];
+    double *cmi_b = cmi_a + jobs_a;
+    IDTX_TRY(enqueue_group(c, ga[0], st, cmi_a, nullptr, nullptr, timeout_of(s)));
+
+    // ids (and, in screened mode, the keep list) live in the step buffer
+    unsigned char *stepbuf = (unsigned char *)c->buf[B_STEP];
+    idtx_step *step_d = (idtx_step *)stepbuf;
+    int32_t *ids_d = (int32_t *)(stepbuf + align_up(sizeof(idtx_step), 16));
+    IDTX_CUDA(cudaMemcpyAsync(ids_d, ids.data(), ids.size() * sizeof(int32_t),
+                              cudaMemcpyHostToDevice, st));
+    int n_keep = 0;
+    std::vector<int32_t> keep;
+    if (screened) {
+        // Features, predictions and the keep list of the screen.
+        const int nc = n_alive;
+        const size_t scr_floats = IDTX_SCREEN_NPARAMS + 2 * IDTX_SCREEN_F +
+                                  (size_t)nc * IDTX_SCREEN_F + nc + 2 * (size_t)nc + 64;
+        IDTX_TRY(ensure(c, B_SCREEN, scr_floats * sizeof(float)));
+        IDTX_TRY(ensure(c, B_MLP, mlp_work_floats(nc) * sizeof(float)));
+        float *sp = (float *)c->buf[B_SCREEN];
+        float *params = sp, *mean = params + IDTX_SCREEN_NPARAMS, *scale = mean + IDTX_SCREEN_F;
+        float *feats = scale + IDTX_SCREEN_F;
+        int32_t *keep_d = (int32_t *)(feats + (size_t)nc * IDTX_SCREEN_F);
+        int32_t *nkeep_d = keep_d + nc;
+        IDTX_CUDA(cudaMemcpyAsync(params, c->screen.params, sizeof(c->screen.params),
+                                  cudaMemcpyHostToDevice, st));
+        IDTX_CUDA(cudaMemcpyAsync(mean, c->screen.feat_mean, sizeof(c->screen.feat_mean),
+                                  cudaMemcpyHostToDevice, st));
+        IDTX_CUDA(cudaMemcpyAsync(scale, c->screen.feat_scale, sizeof(c->screen.feat_scale),
+                                  cudaMemcpyHostToDevice, st));
+        k_screen_features<<<(nc + 127) / 128, 128, 0, st>>>(
+            cmi_a, nc, s0, (float)std::log((double)n), 1, 1, dz, s->k,
+            (float)std::log((double)s->n_surr), feats);
+        IDTX_CUDA(cudaGetLastError());
+        MlpWork w;
+        mlp_work_carve((float *)c->buf[B_MLP], nc, &w);
+        IDTX_CUDA(mlp_round(params, w, st));
+        IDTX_CUDA(mlp_forward(params, w, feats, nullptr, 0, nc, mean, scale, st));
+        k_screen_keep<<<1, 1, 0, st>>>(cmi_a, nc, s0, w.y, c->screen.delta, keep_d, nkeep_d);
+        IDTX_CUDA(cudaGetLastError());
+        c->stats.kernel_launches += 7;
+        keep.resize(nc + 1);
+        IDTX_CUDA(cudaMemcpyAsync(keep.data(), keep_d, (size_t)(nc + 1) * sizeof(int32_t),
+                                  cudaMemcpyDeviceToHost, st));
+        IDTX_CUDA(cudaStreamSynchronize(st));
+        n_keep = keep[nc];
+        if (n_keep > 0) {
+            // The remaining surrogates of the kept candidates.
+            std::vector<int> kc(keep.begin(), keep.begin() + n_keep);
+            std::vector<Group> gb(1);
+            make_group(gb[0], kc, false, s0, s->n_surr);
+            gb[0].work_slot = 1;
+            IDTX_TRY(plan(c, gb[0]));
+            std::vector<unsigned char> arena_b;
+            IDTX_TRY(upload(gb, arena_b, cmi_bytes));
+            IDTX_TRY(enqueue_group(c, gb[0], st, cmi_b, nullptr, nullptr, timeout_of(s)));
         }
     }
-    g.plain = s->mode == IDTX_MODE_PLAIN;
-    IDTX_TRY(plan(c, g));
-    std::vector<unsigned char> arena;
-    pack_desc(gs, arena);
-    // ids after the descriptors
-    size_t ids_off = align_up(arena.size(), 16);
-    arena.resize(ids_off + ids.size() * sizeof(int32_t));
-    memcpy(arena.data() + ids_off, ids.data(), ids.size() * sizeof(int32_t));
-    CallBuffers b;
-    sizes_of(g, b);
-    IDTX_TRY(ensure(c, B_DESC, arena.size()));
-    IDTX_TRY(ensure(c, B_SH, b.sh));
-    IDTX_TRY(ensure(c, B_XI, b.xi));
-    IDTX_TRY(ensure(c, B_PERM, b.perm));
-    IDTX_TRY(ensure(c, B_PARTIAL, b.partial));
-    IDTX_TRY(ensure(c, B_ORDER, b.order));
-    IDTX_TRY(ensure(c, B_SORT, b.sort_tmp));
-    IDTX_TRY(ensure(c, B_CMI, (size_t)n_jobs * sizeof(double)));
-    IDTX_TRY(ensure(c, B_STEP, sizeof(idtx_step)));
-    IDTX_TRY(ensure_psi(c, std::max<int64_t>(n, s->k) + 1, st));
-    IDTX_CUDA(cudaMemcpyAsync(c->buf[B_DESC], arena.data(), arena.size(), cudaMemcpyHostToDevice,
-                              st));
-    double *cmi_d = (double *)c->buf[B_CMI];
-    IDTX_TRY(enqueue_group(c, g, st, cmi_d, nullptr, nullptr, timeout_of(s)));
-    const int32_t *ids_d = (const int32_t *)((const unsigned char *)c->buf[B_DESC] + ids_off);
-    idtx_step *step_d = (idtx_step *)c->buf[B_STEP];
-    k_gate<<<1, 256, 0, st>>>(cmi_d, ids_d, n_alive, s->n_surr, s->alpha, step_d);
+    k_gate<<<1, 256, 0, st>>>(cmi_a, n_alive, s0, cmi_b, n_keep, s->n_surr, ids_d, s->alpha,
+                              step_d);
     IDTX_CUDA(cudaGetLastError());
     c->stats.kernel_launches += 1;
     IDTX_CUDA(cudaMemcpyAsync(result, step_d, sizeof(idtx_step),
@@ -1231,16 +1367,210 @@ int idtx_mte_step(idtx_ctx *c, const float *series, int n_proc, int64_t T, int t
                                                         : cudaMemcpyDeviceToHost,
                               st));
     if (est_out) {
+        // Rows of est_out are [1 + n_surr] per candidate id; columns the kernel
+        // did not compute (screened mode, skipped candidates) are left untouched.
         const bool dev = device_accessible(est_out);
+        const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
         const size_t row = (size_t)(1 + s->n_surr) * sizeof(double);
-        // Candidate rows are contiguous in cmi_d; scatter them to their ids.
         for (int a = 0; a < n_alive; ++a)
             IDTX_CUDA(cudaMemcpyAsync((unsigned char *)est_out + (size_t)ids[a] * row,
-                                      (const unsigned char *)cmi_d + (size_t)a * row, row,
-                                      dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                      cmi_a + (size_t)a * (1 + s0), (size_t)(1 + s0) * 8, kind,
                                       st));
+        for (int t = 0; t < n_keep; ++t)
+            IDTX_CUDA(cudaMemcpyAsync((unsigned char *)est_out + (size_t)ids[keep[t]] * row +
+                                          (size_t)(1 + s0) * 8,
+                                      cmi_b + (size_t)t * (s->n_surr - s0),
+                                      (size_t)(s->n_surr - s0) * 8, kind, st));
     }
     return finish_call(c, st);
+}
+
+// ------------------------------------------------------------------ learned screen
+namespace {
+
+constexpr int kScreenP = IDTX_SCREEN_NPARAMS, kScreenF = IDTX_SCREEN_F;
+
+int check_screen(const idtx_screen *sc)
+{
+    if (!sc) return fail(IDTX_EINVAL, "screen is NULL");
+    for (int i = 0; i < kScreenP; ++i)
+        if (!std::isfinite(sc->params[i])) return fail(IDTX_EINVAL, "non-finite screen parameter");
+    for (int i = 0; i < kScreenF; ++i)
+        if (!std::isfinite(sc->feat_mean[i]) || !std::isfinite(sc->feat_scale[i]))
+            return fail(IDTX_EINVAL, "non-finite screen normalisation");
+    if (!std::isfinite(sc->delta)) return fail(IDTX_EINVAL, "non-finite screen delta");
+    return IDTX_OK;
+}
+
+// Device copies of the screen's parameters and normalisation at the start of
+// B_SCREEN, followed by `extra` floats of room.
+int upload_screen(idtx_ctx *c, const idtx_screen *sc, size_t extra, cudaStream_t st,
+                  float **params, float **mean, float **scale, float **rest)
+{
+    IDTX_TRY(ensure(c, B_SCREEN, (kScreenP + 2 * kScreenF + extra + 64) * sizeof(float)));
+    float *sp = (float *)c->buf[B_SCREEN];
+    *params = sp;
+    *mean = sp + kScreenP;
+    *scale = *mean + kScreenF;
+    *rest = *scale + kScreenF;
+    IDTX_CUDA(cudaMemcpyAsync(*params, sc->params, sizeof(sc->params), cudaMemcpyHostToDevice, st));
+    IDTX_CUDA(cudaMemcpyAsync(*mean, sc->feat_mean, sizeof(sc->feat_mean), cudaMemcpyHostToDevice,
+                              st));
+    IDTX_CUDA(cudaMemcpyAsync(*scale, sc->feat_scale, sizeof(sc->feat_scale),
+                              cudaMemcpyHostToDevice, st));
+    return IDTX_OK;
+}
+
+// Device pointer to n*width floats of `src` (copied into dst when src is host memory).
+int device_floats(const float *src, size_t count, float *dst, cudaStream_t st, const float **out)
+{
+    if (device_accessible(src)) {
+        *out = src;
+        return IDTX_OK;
+    }
+    IDTX_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(float), cudaMemcpyHostToDevice, st));
+    *out = dst;
+    return IDTX_OK;
+}
+
+}  // namespace
+
+extern "C" int idtx_screen_set(idtx_ctx *c, const idtx_screen *sc)
+{
+    if (!c) return fail(IDTX_EINVAL, "ctx is NULL");
+    IDTX_TRY(check_screen(sc));
+    c->screen = *sc;
+    c->has_screen = true;
+    return IDTX_OK;
+}
+
+extern "C" int idtx_screen_predict(idtx_ctx *c, const idtx_screen *sc, const float *feats, int n,
+                                   float *out, void *stream)
+{
+    if (!c) return fail(IDTX_EINVAL, "ctx is NULL");
+    if (!feats || !out || n < 1) return fail(IDTX_EINVAL, "bad features or output");
+    IDTX_TRY(check_screen(sc));
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    IDTX_TRY(begin_call(c, 0, st));
+    float *params, *mean, *scale, *rest;
+    IDTX_TRY(upload_screen(c, sc, (size_t)n * kScreenF, st, &params, &mean, &scale, &rest));
+    IDTX_TRY(ensure(c, B_MLP, mlp_work_floats(n) * sizeof(float)));
+    const float *fd;
+    IDTX_TRY(device_floats(feats, (size_t)n * kScreenF, rest, st, &fd));
+    MlpWork w;
+    mlp_work_carve((float *)c->buf[B_MLP], n, &w);
+    IDTX_CUDA(mlp_round(params, w, st));
+    IDTX_CUDA(mlp_forward(params, w, fd, nullptr, 0, n, mean, scale, st));
+    c->stats.kernel_launches += 5;
+    IDTX_CUDA(cudaMemcpyAsync(out, w.y, (size_t)n * sizeof(float),
+                              device_accessible(out) ? cudaMemcpyDeviceToDevice
+                                                     : cudaMemcpyDeviceToHost,
+                              st));
+    return finish_call(c, st);
+}
+
+extern "C" int idtx_screen_loss_grad(idtx_ctx *c, const idtx_screen *sc, const float *feats,
+                                     const float *targets, int n, double *loss, float *grad,
+                                     void *stream)
+{
+    if (!c) return fail(IDTX_EINVAL, "ctx is NULL");
+    if (!feats || !targets || !loss || !grad || n < 1)
+        return fail(IDTX_EINVAL, "bad features, targets or outputs");
+    IDTX_TRY(check_screen(sc));
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    IDTX_TRY(begin_call(c, 0, st));
+    float *params, *mean, *scale, *rest;
+    IDTX_TRY(upload_screen(c, sc, (size_t)n * (kScreenF + 1) + 16, st, &params, &mean, &scale,
+                           &rest));
+    IDTX_TRY(ensure(c, B_MLP, mlp_work_floats(n) * sizeof(float) + 64));
+    const float *fd, *td;
+    IDTX_TRY(device_floats(feats, (size_t)n * kScreenF, rest, st, &fd));
+    IDTX_TRY(device_floats(targets, (size_t)n, rest + (size_t)n * kScreenF, st, &td));
+    double *loss_d = (double *)((float *)c->buf[B_MLP] + mlp_work_floats(n) + 2);
+    loss_d = (double *)(((uintptr_t)loss_d + 7) & ~(uintptr_t)7);
+    IDTX_CUDA(cudaMemsetAsync(loss_d, 0, sizeof(double), st));
+    MlpWork w;
+    mlp_work_carve((float *)c->buf[B_MLP], n, &w);
+    IDTX_CUDA(mlp_round(params, w, st));
+    IDTX_CUDA(mlp_forward(params, w, fd, nullptr, 0, n, mean, scale, st));
+    IDTX_CUDA(mlp_loss(w, td, nullptr, 0, n, 2.0f / (float)n, true, loss_d, st));
+    IDTX_CUDA(mlp_backward(w, n, false, st));
+    c->stats.kernel_launches += 11;
+    double lsum = 0.0;
+    IDTX_CUDA(cudaMemcpyAsync(&lsum, loss_d, sizeof(double), cudaMemcpyDeviceToHost, st));
+    IDTX_CUDA(cudaMemcpyAsync(grad, w.grad, (size_t)kScreenP * sizeof(float),
+                              cudaMemcpyDeviceToHost, st));
+    const int rc = finish_call(c, st);
+    *loss = lsum / (double)n;
+    return rc;
+}
+
+extern "C" int idtx_screen_train(idtx_ctx *c, idtx_screen *sc, const float *feats,
+                                 const float *targets, int n, int epochs, int batch, float lr,
+                                 uint64_t seed, double *final_loss, void *stream)
+{
+    if (!c) return fail(IDTX_EINVAL, "ctx is NULL");
+    if (!feats || !targets || n < 1 || epochs < 0 || batch < 1 || !(lr > 0.0f))
+        return fail(IDTX_EINVAL, "bad training arguments");
+    IDTX_TRY(check_screen(sc));
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    IDTX_TRY(begin_call(c, 0, st));
+    batch = std::min(batch, n);
+    float *params, *mean, *scale, *rest;
+    IDTX_TRY(upload_screen(c, sc, 0, st, &params, &mean, &scale, &rest));
+    // training area: features, targets, order, Adam moments, loss accumulator
+    const size_t tr_floats = (size_t)n * (kScreenF + 1) + (size_t)n + 2 * (size_t)kScreenP + 16;
+    IDTX_TRY(ensure(c, B_TRAIN, tr_floats * sizeof(float)));
+    const int wb = std::max(batch, std::min(n, 4096));
+    IDTX_TRY(ensure(c, B_MLP, mlp_work_floats(wb) * sizeof(float)));
+    float *tr = (float *)c->buf[B_TRAIN];
+    float *fbuf = tr, *tbuf = fbuf + (size_t)n * kScreenF;
+    int32_t *order = (int32_t *)(tbuf + n);
+    float *m = (float *)(order + n), *v = m + kScreenP;
+    double *loss_d = (double *)(((uintptr_t)(v + kScreenP) + 7) & ~(uintptr_t)7);
+    const float *fd, *td;
+    IDTX_TRY(device_floats(feats, (size_t)n * kScreenF, fbuf, st, &fd));
+    IDTX_TRY(device_floats(targets, (size_t)n, tbuf, st, &td));
+    IDTX_CUDA(cudaMemsetAsync(m, 0, 2 * (size_t)kScreenP * sizeof(float), st));
+    IDTX_TRY(ensure(c, B_DESC, 64));
+    uint64_t *rng = (uint64_t *)c->buf[B_DESC];  // [0] stream, [1] seed of the shuffle
+    MlpWork w;
+    mlp_work_carve((float *)c->buf[B_MLP], wb, &w);
+    int step = 0;
+    for (int ep = 0; ep < epochs; ++ep) {
+        const uint64_t rs[2] = {(uint64_t)ep, seed};
+        IDTX_CUDA(cudaMemcpyAsync(rng, rs, sizeof(rs), cudaMemcpyHostToDevice, st));
+        k_iota<<<grid_for(n, 256), 256, 0, st>>>(order, 1, n);
+        k_fisher_yates<<<1, 32, 0, st>>>(order, rng, rng + 1, 1, n);
+        IDTX_CUDA(cudaGetLastError());
+        for (int start = 0; start < n; start += batch) {
+            const int bsz = std::min(batch, n - start);
+            IDTX_CUDA(mlp_round(params, w, st));
+            IDTX_CUDA(mlp_forward(params, w, fd, order, start, bsz, mean, scale, st));
+            IDTX_CUDA(mlp_loss(w, td, order, start, bsz, 2.0f / (float)bsz, true, loss_d, st));
+            IDTX_CUDA(mlp_backward(w, bsz, false, st));
+            IDTX_CUDA(mlp_adam(params, w.grad, m, v, ++step, lr, st));
+            c->stats.kernel_launches += 12;
+        }
+        IDTX_CUDA(cudaStreamSynchronize(st));  // keep the host copy of rs alive
+    }
+    // full-data loss of the trained parameters
+    IDTX_CUDA(cudaMemsetAsync(loss_d, 0, sizeof(double), st));
+    IDTX_CUDA(mlp_round(params, w, st));
+    for (int start = 0; start < n; start += wb) {
+        const int bsz = std::min(wb, n - start);
+        IDTX_CUDA(mlp_forward(params, w, fd, nullptr, start, bsz, mean, scale, st));
+        IDTX_CUDA(mlp_loss(w, td, nullptr, start, bsz, 0.0f, false, loss_d, st));
+    }
+    double lsum = 0.0;
+    IDTX_CUDA(cudaMemcpyAsync(&lsum, loss_d, sizeof(double), cudaMemcpyDeviceToHost, st));
+    IDTX_CUDA(cudaMemcpyAsync(sc->params, params, sizeof(sc->params), cudaMemcpyDeviceToHost, st));
+    const int rc = finish_call(c, st);
+    if (final_loss) *final_loss = lsum / (double)n;
+    return rc;
 }
 
 int idtx_mte_select_target(idtx_ctx *c, const float *series, int n_proc, int64_t T, int target,

@@ -1,0 +1,128 @@
+"""GPU tests of the learned screen: its forward pass and gradient against the
+fp64 oracle on the same bf16-rounded weights, deterministic training, and the
+screened greedy step against the exact (batched) step."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1807_10459_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def idtx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1807_10459_gb300 as m
+    from paper_1807_10459_gb300 import build
+    build.build()
+    return m
+
+
+def _data(n, seed):
+    rng = np.random.default_rng(seed)
+    x = rng.standard_normal((n, 10)).astype(np.float32)
+    x[:, 1] = 8.0 + rng.random(n)             # ln N-like column with a large offset
+    t = (np.tanh(x[:, 0]) + 0.3 * x[:, 6] * x[:, 8] + 0.1 * x[:, 1]).astype(np.float32)
+    return x, t
+
+
+def _screen(idtx, seed):
+    rng = np.random.default_rng(seed)
+    sc = idtx.Screen(seed=seed)
+    sc.params[:] += (rng.standard_normal(sc.params.size) * 0.05).astype(np.float32)
+    sc.feat_mean[:] = np.array([0, 8.5, 0, 0, 0, 0, 0, 0, 0, 0], np.float32)
+    sc.feat_scale[:] = np.array([1, 3.0, 1, 1, 1, 1, 1, 1, 1, 1], np.float32)
+    return sc
+
+
+def test_forward_matches_oracle(idtx):
+    sc = _screen(idtx, 1)
+    x, _ = _data(300, 2)
+    got = idtx.screen_predict(sc, x)
+    ref = oracle.mlp_forward(sc.params, 10, 64, sc.feat_mean, sc.feat_scale, x, bf16=True)
+    assert np.max(np.abs(got - ref)) <= 1e-5 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_gradient_matches_oracle(idtx):
+    sc = _screen(idtx, 3)
+    x, t = _data(257, 4)
+    loss, g = idtx.screen_loss_grad(sc, x, t)
+    rl, rg = oracle.mlp_loss_grad(sc.params, 10, 64, sc.feat_mean, sc.feat_scale, x, t,
+                                  bf16=True)
+    assert abs(loss - rl) <= 1e-5 * max(1.0, rl)
+    assert np.max(np.abs(g - rg)) <= 1e-4 * max(1.0, np.max(np.abs(rg)))
+
+
+def test_training_lowers_the_loss_and_is_deterministic(idtx):
+    x, t = _data(3000, 5)
+    a = idtx.Screen(seed=7)
+    b = idtx.Screen(seed=7)
+    l0, _ = idtx.screen_loss_grad(a, x, t)
+    la = idtx.screen_train(a, x, t, epochs=40, batch=128, lr=3e-3, seed=11)
+    lb = idtx.screen_train(b, x, t, epochs=40, batch=128, lr=3e-3, seed=11)
+    assert la < 0.2 * l0
+    assert la == lb and np.array_equal(a.params, b.params)
+    # the loss the trainer reports is the oracle's loss of the trained parameters
+    rl, _ = oracle.mlp_loss_grad(a.params, 10, 64, a.feat_mean, a.feat_scale, x, t, bf16=True)
+    assert abs(la - rl) <= 1e-5 * max(1.0, rl)
+
+
+def _net():
+    return synth.var_network(n_nodes=5, order=3, T=900, density=0.4, weight=0.6, seed=21)
+
+
+def test_screened_step_keeping_everything_equals_exact(idtx):
+    net = _net()
+    ctx = idtx.Context(0)
+    sc = idtx.Screen(delta=1e30, s0=4)
+    idtx.screen_set(sc, ctx=ctx)
+    args = (torch.from_numpy(net.series).cuda(), 0, 2, 1, 3, (), 0)
+    ex, e_est = idtx.mte_step(*args, k=4, n_surr=30, seed=3, want_estimates=True, ctx=ctx)
+    sr, s_est = idtx.mte_step(*args, k=4, n_surr=30, seed=3, want_estimates=True,
+                              mode=idtx.MODE_SCREENED, ctx=ctx)
+    assert tuple(sr) == tuple(ex)
+    assert sr.n_full == sr.n_cand == ex.n_cand
+    ok = ~np.isnan(e_est[:, 0])
+    assert np.max(np.abs(e_est[ok] - s_est[ok])) < 1e-10
+
+
+def test_screened_step_skipping_everything_uses_only_cheap_surrogates(idtx):
+    net = _net()
+    ctx = idtx.Context(0)
+    idtx.screen_set(idtx.Screen(delta=-1e30, s0=5), ctx=ctx)
+    args = (torch.from_numpy(net.series).cuda(), 0, 2, 1, 3, (), 0)
+    ex, e_est = idtx.mte_step(*args, k=4, n_surr=30, seed=3, want_estimates=True, ctx=ctx)
+    sr, s_est = idtx.mte_step(*args, k=4, n_surr=30, seed=3, want_estimates=True,
+                              mode=idtx.MODE_SCREENED, ctx=ctx)
+    assert sr.n_full == 0
+    ok = ~np.isnan(e_est[:, 0])
+    assert np.max(np.abs(e_est[ok][:, :6] - s_est[ok][:, :6])) < 1e-10
+    assert np.all(np.isnan(s_est[ok][:, 6:]))
+    # the count only sees the cheap surrogates, over all candidates
+    t_obs = e_est[ok][:, 0].max()
+    cnt = np.count_nonzero(e_est[ok][:, 1:6].max(axis=0) >= t_obs)
+    assert sr[3] == cnt / 30 and sr[0] == ex[0] and abs(sr[2] - ex[2]) < 1e-12
+
+
+def test_screened_step_with_a_sound_screen_agrees_with_exact(idtx):
+    """A screen whose prediction is an upper bound for every skipped candidate
+    (here: a constant prediction plus a margin above every candidate's true
+    surrogate maximum except the ones it keeps) must reproduce the exact count."""
+    net = _net()
+    ctx = idtx.Context(0)
+    args = (torch.from_numpy(net.series).cuda(), 0, 2, 1, 3, (), 0)
+    ex, e_est = idtx.mte_step(*args, k=4, n_surr=30, seed=3, want_estimates=True, ctx=ctx)
+    ok = np.flatnonzero(~np.isnan(e_est[:, 0]))
+    true_max = e_est[ok, 1:].max(axis=1)
+    t_obs = e_est[ok, 0].max()
+    # all-zero network predicts 0: keep iff delta >= T_obs.  Choose delta just
+    # above the largest true surrogate maximum but below T_obs when possible.
+    sc = idtx.Screen(params=np.zeros(idtx.SCREEN_NPARAMS, np.float32), s0=4,
+                     delta=float(true_max.max()) + 1e-6)
+    idtx.screen_set(sc, ctx=ctx)
+    sr = idtx.mte_step(*args, k=4, n_surr=30, seed=3, mode=idtx.MODE_SCREENED, ctx=ctx)
+    assert (sr[0], sr[1], sr[3]) == (ex[0], ex[1], ex[3])
+    assert sr.n_full == (len(ok) if sc.delta >= t_obs else 0)
