@@ -188,8 +188,12 @@ typedef struct {
     double stat;         /* T_obs = max over candidates of I(X_c;Y|Z) */
     double pval;         /* #{s : max_c I(X_c o pi_{c,s};Y|Z) >= T_obs} / n_surr */
     int32_t n_cand;      /* candidates evaluated */
-    int32_t n_full;      /* candidates given all n_surr surrogates (screened mode:
-                            the others got only the screen's s0) */
+    int32_t n_full;      /* candidates given more than the screen's s0 surrogates
+                            (all candidates outside screened mode) */
+    int32_t surr_done;   /* surrogate indices evaluated: n_surr, or fewer when a
+                            screened step stopped early (pval is then a lower
+                            bound that already decides: pval >= alpha) */
+    int32_t reserved;
 } idtx_step;
 
 /* One step of the greedy parent selection for one target (Summary, paragraph
@@ -230,7 +234,8 @@ int idtx_mte_select_target(idtx_ctx *ctx, const float *series, int n_proc, int64
 /* estimate and I_c,0..s0-1 its first s0 surrogate estimates (streams of the */
 /* step): x = (I_c, ln N, dx, dy, dz, k, mean_s I_c,s, std_s I_c,s (divisor   */
 /* s0), max_s I_c,s, ln n_surr), normalised as (x - feat_mean) * feat_scale. */
-/* The network predicts max over all n_surr surrogates of I_c,s.             */
+/* The network predicts the excess of max over all n_surr surrogates of      */
+/* I_c,s over the largest of the s0 cheap ones (never negative).             */
 /* ------------------------------------------------------------------------ */
 #define IDTX_SCREEN_F 10
 #define IDTX_SCREEN_H 64

@@ -65,7 +65,8 @@ class Stats(ctypes.Structure):
 class Step(ctypes.Structure):
     _fields_ = [("cand", ctypes.c_int32), ("significant", ctypes.c_int32),
                 ("stat", ctypes.c_double), ("pval", ctypes.c_double),
-                ("n_cand", ctypes.c_int32), ("n_full", ctypes.c_int32)]
+                ("n_cand", ctypes.c_int32), ("n_full", ctypes.c_int32),
+                ("surr_done", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class ScreenC(ctypes.Structure):
@@ -176,12 +177,14 @@ def default_context(device: int = 0) -> Context:
 
 
 class StepResult(tuple):
-    """(cand, significant, stat, pval) of one greedy step, with .n_cand and .n_full."""
+    """(cand, significant, stat, pval) of one greedy step, with .n_cand, .n_full
+    and .surr_done (surrogate indices evaluated)."""
 
-    def __new__(cls, cand, significant, stat, pval, n_cand=0, n_full=0):
+    def __new__(cls, cand, significant, stat, pval, n_cand=0, n_full=0, surr_done=0):
         obj = super().__new__(cls, (cand, significant, stat, pval))
         obj.n_cand = n_cand
         obj.n_full = n_full
+        obj.surr_done = surr_done
         return obj
 
 
@@ -417,18 +420,19 @@ def mte_step(series, target: int, n_past: int, min_lag: int, max_lag: int, selec
                                 int(step_index), ctypes.byref(s), ctypes.byref(step), p_est,
                                 _stream_for(series)))
     res = StepResult(int(step.cand), bool(step.significant), float(step.stat),
-                     float(step.pval), int(step.n_cand), int(step.n_full))
+                     float(step.pval), int(step.n_cand), int(step.n_full), int(step.surr_done))
     return (res, est) if want_estimates else res
 
 
 def mte_select_target(series, target: int, n_past: int, min_lag: int, max_lag: int, k: int = 4,
                       n_surr: int = 200, alpha: float = 0.05, seed: int = 0,
-                      max_parents: int = 10, timeout_ms: int = 0, ctx: Context | None = None):
+                      max_parents: int = 10, timeout_ms: int = 0, mode: int = MODE_BATCHED,
+                      ctx: Context | None = None):
     """The greedy loop for one target: dict(parents=[ids], steps=[(cand, sig, stat, p)])."""
     a = _Arr(series, name="series")
     dev = series.device.index if (_is_torch(series) and series.is_cuda) else 0
     ctx = ctx or default_context(dev or 0)
-    s = _settings(k, n_surr, seed, alpha, timeout_ms)
+    s = _settings(k, n_surr, seed, alpha, timeout_ms, mode)
     parents = np.zeros(max(1, max_parents), np.int32)
     steps = (Step * (max_parents + 1))()
     n_par, n_steps = ctypes.c_int(), ctypes.c_int()
@@ -440,5 +444,6 @@ def mte_select_target(series, target: int, n_past: int, min_lag: int, max_lag: i
     return dict(parents=[int(p) for p in parents[:n_par.value]],
                 steps=[StepResult(int(steps[i].cand), bool(steps[i].significant),
                                   float(steps[i].stat), float(steps[i].pval),
-                                  int(steps[i].n_cand), int(steps[i].n_full))
+                                  int(steps[i].n_cand), int(steps[i].n_full),
+                                  int(steps[i].surr_done))
                        for i in range(n_steps.value)])

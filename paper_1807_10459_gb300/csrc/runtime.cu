@@ -412,7 +412,65 @@ __global__ void k_gate(const double *est_a, int n_cand, int sa, const double *es
         out->pval = p;
         out->n_cand = n_cand;
         out->n_full = sa == n_surr ? n_cand : n_keep;
+        out->surr_done = n_surr;
+        out->reserved = 0;
     }
+}
+
+// Screened steps: T_obs, its candidate, and the count over the first sa
+// surrogate indices (every candidate has them) into out / *count.
+__global__ void k_gate_begin(const double *est_a, int n_cand, int sa, const int32_t *ids,
+                             idtx_step *out, int *count)
+{
+    __shared__ double s_tobs;
+    __shared__ int s_cnt;
+    if (threadIdx.x == 0) {
+        double t = -INFINITY;
+        int b = -1;
+        for (int c = 0; c < n_cand; ++c) {
+            const double v = est_a[(int64_t)c * (1 + sa)];
+            if (v > t) {
+                t = v;
+                b = c;
+            }
+        }
+        s_tobs = t;
+        s_cnt = 0;
+        out->cand = b >= 0 ? ids[b] : -1;
+        out->stat = t;
+        out->n_cand = n_cand;
+        out->reserved = 0;
+    }
+    __syncthreads();
+    for (int s = threadIdx.x; s < sa; s += blockDim.x) {
+        double ts = -INFINITY;
+        for (int c = 0; c < n_cand; ++c) ts = fmax(ts, est_a[(int64_t)c * (1 + sa) + 1 + s]);
+        if (ts >= s_tobs) atomicAdd(&s_cnt, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *count = s_cnt;
+}
+
+// Adds to *count the surrogate indices of a block est [n_rows][ncol] (one
+// chunk of indices for the kept candidates) whose maximum reaches T_obs.
+__global__ void k_gate_chunk(const double *est, int n_rows, int ncol, const idtx_step *step,
+                             int *count)
+{
+    for (int j = threadIdx.x; j < ncol; j += blockDim.x) {
+        double ts = -INFINITY;
+        for (int r = 0; r < n_rows; ++r) ts = fmax(ts, est[(int64_t)r * ncol + j]);
+        if (ts >= step->stat) atomicAdd(count, 1);
+    }
+}
+
+__global__ void k_gate_end(idtx_step *out, const int *count, int n_surr, int surr_done,
+                           int n_full, double alpha)
+{
+    const double p = (double)*count / (double)n_surr;
+    out->pval = p;
+    out->significant = (out->cand >= 0 && p < alpha) ? 1 : 0;
+    out->n_full = n_full;
+    out->surr_done = surr_done;
 }
 
 // Screen features of every candidate from its estimate and first s0 surrogate
@@ -445,8 +503,10 @@ __global__ void k_screen_features(const double *est, int n_cand, int s0, float l
     f[9] = ln_s;
 }
 
-// Keep candidate c iff pred[c] + delta >= T_obs; kept candidates listed in
-// ascending order in keep[], their count in *n_keep (one thread, in order).
+// Keep candidate c iff m_c + max(pred[c], 0) + delta >= T_obs, m_c the largest of
+// its s0 cheap surrogate estimates (a lower bound of its largest surrogate
+// estimate) and pred[c] the network's prediction of the excess over m_c; kept
+// candidates listed in ascending order in keep[], their count in *n_keep.
 __global__ void k_screen_keep(const double *est, int n_cand, int s0, const float *pred,
                               float delta, int32_t *keep, int32_t *n_keep)
 {
@@ -454,8 +514,11 @@ __global__ void k_screen_keep(const double *est, int n_cand, int s0, const float
     double t = -INFINITY;
     for (int c = 0; c < n_cand; ++c) t = fmax(t, est[(int64_t)c * (1 + s0)]);
     int n = 0;
-    for (int c = 0; c < n_cand; ++c)
-        if ((double)pred[c] + (double)delta >= t) keep[n++] = c;
+    for (int c = 0; c < n_cand; ++c) {
+        double m = -INFINITY;
+        for (int s = 0; s < s0; ++s) m = fmax(m, est[(int64_t)c * (1 + s0) + 1 + s]);
+        if (m + fmax((double)pred[c], 0.0) + (double)delta >= t) keep[n++] = c;
+    }
     *n_keep = n;
 }
 
@@ -1346,22 +1409,61 @@ int idtx_mte_step(idtx_ctx *c, const float *series, int n_proc, int64_t T, int t
                                   cudaMemcpyDeviceToHost, st));
         IDTX_CUDA(cudaStreamSynchronize(st));
         n_keep = keep[nc];
-        if (n_keep > 0) {
-            // The remaining surrogates of the kept candidates.
+    }
+    // chunks of the remaining surrogate indices run for the kept candidates:
+    // (first index, count, offset of the block [n_keep][count] in cmi_b)
+    struct Chunk {
+        int lo, cnt;
+        size_t off;
+    };
+    std::vector<Chunk> chunks;
+    if (!screened) {
+        k_gate<<<1, 256, 0, st>>>(cmi_a, n_alive, s0, cmi_b, n_keep, s->n_surr, ids_d, s->alpha,
+                                  step_d);
+        IDTX_CUDA(cudaGetLastError());
+        c->stats.kernel_launches += 1;
+    } else {
+        // Count over the cheap surrogates, then chunk after chunk of the rest
+        // until the count decides "not significant" or all indices are done.
+        int *count_d = (int *)((unsigned char *)ids_d + align_up((size_t)n_cand_total * 4, 16));
+        k_gate_begin<<<1, 256, 0, st>>>(cmi_a, n_alive, s0, ids_d, step_d, count_d);
+        IDTX_CUDA(cudaGetLastError());
+        c->stats.kernel_launches += 1;
+        int decide = 0;  // smallest count c with c / n_surr >= alpha
+        while ((double)decide / (double)s->n_surr < s->alpha) ++decide;
+        int count = 0;
+        IDTX_CUDA(cudaMemcpyAsync(&count, count_d, sizeof(int), cudaMemcpyDeviceToHost, st));
+        IDTX_CUDA(cudaStreamSynchronize(st));
+        int lo = s0, width = 16;
+        size_t off = 0;
+        while (n_keep > 0 && lo < s->n_surr && count < decide) {
+            const int hi = std::min(s->n_surr, lo + width);
             std::vector<int> kc(keep.begin(), keep.begin() + n_keep);
             std::vector<Group> gb(1);
-            make_group(gb[0], kc, false, s0, s->n_surr);
+            make_group(gb[0], kc, false, lo, hi);
             gb[0].work_slot = 1;
             IDTX_TRY(plan(c, gb[0]));
             std::vector<unsigned char> arena_b;
             IDTX_TRY(upload(gb, arena_b, cmi_bytes));
-            IDTX_TRY(enqueue_group(c, gb[0], st, cmi_b, nullptr, nullptr, timeout_of(s)));
+            IDTX_TRY(enqueue_group(c, gb[0], st, cmi_b + off, nullptr, nullptr, timeout_of(s)));
+            k_gate_chunk<<<1, 256, 0, st>>>(cmi_b + off, n_keep, hi - lo, step_d, count_d);
+            IDTX_CUDA(cudaGetLastError());
+            c->stats.kernel_launches += 1;
+            chunks.push_back(Chunk{lo, hi - lo, off});
+            off += (size_t)n_keep * (hi - lo);
+            IDTX_CUDA(cudaMemcpyAsync(&count, count_d, sizeof(int), cudaMemcpyDeviceToHost, st));
+            IDTX_CUDA(cudaStreamSynchronize(st));
+            lo = hi;
+            width *= 2;
         }
+        // Without kept candidates no index past s0 can add to the count, so the
+        // count is final; otherwise indices from `lo` on were not evaluated.
+        const int surr_done = n_keep == 0 ? s->n_surr : lo;
+        k_gate_end<<<1, 1, 0, st>>>(step_d, count_d, s->n_surr, surr_done,
+                                    chunks.empty() ? 0 : n_keep, s->alpha);
+        IDTX_CUDA(cudaGetLastError());
+        c->stats.kernel_launches += 1;
     }
-    k_gate<<<1, 256, 0, st>>>(cmi_a, n_alive, s0, cmi_b, n_keep, s->n_surr, ids_d, s->alpha,
-                              step_d);
-    IDTX_CUDA(cudaGetLastError());
-    c->stats.kernel_launches += 1;
     IDTX_CUDA(cudaMemcpyAsync(result, step_d, sizeof(idtx_step),
                               device_accessible(result) ? cudaMemcpyDeviceToDevice
                                                         : cudaMemcpyDeviceToHost,
@@ -1376,11 +1478,12 @@ int idtx_mte_step(idtx_ctx *c, const float *series, int n_proc, int64_t T, int t
             IDTX_CUDA(cudaMemcpyAsync((unsigned char *)est_out + (size_t)ids[a] * row,
                                       cmi_a + (size_t)a * (1 + s0), (size_t)(1 + s0) * 8, kind,
                                       st));
-        for (int t = 0; t < n_keep; ++t)
-            IDTX_CUDA(cudaMemcpyAsync((unsigned char *)est_out + (size_t)ids[keep[t]] * row +
-                                          (size_t)(1 + s0) * 8,
-                                      cmi_b + (size_t)t * (s->n_surr - s0),
-                                      (size_t)(s->n_surr - s0) * 8, kind, st));
+        for (const Chunk &ch : chunks)
+            for (int t = 0; t < n_keep; ++t)
+                IDTX_CUDA(cudaMemcpyAsync((unsigned char *)est_out + (size_t)ids[keep[t]] * row +
+                                              (size_t)(1 + ch.lo) * 8,
+                                          cmi_b + ch.off + (size_t)t * ch.cnt, (size_t)ch.cnt * 8,
+                                          kind, st));
     }
     return finish_call(c, st);
 }

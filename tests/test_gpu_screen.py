@@ -108,21 +108,39 @@ def test_screened_step_skipping_everything_uses_only_cheap_surrogates(idtx):
 
 
 def test_screened_step_with_a_sound_screen_agrees_with_exact(idtx):
-    """A screen whose prediction is an upper bound for every skipped candidate
-    (here: a constant prediction plus a margin above every candidate's true
-    surrogate maximum except the ones it keeps) must reproduce the exact count."""
+    """A screen whose bound holds for every candidate it skips must reproduce the
+    exact decision.  With an all-zero network the bound is cheap maximum + delta;
+    delta just above the largest excess of a candidate's surrogate maximum over
+    its cheap maximum makes it sound."""
     net = _net()
     ctx = idtx.Context(0)
     args = (torch.from_numpy(net.series).cuda(), 0, 2, 1, 3, (), 0)
     ex, e_est = idtx.mte_step(*args, k=4, n_surr=30, seed=3, want_estimates=True, ctx=ctx)
     ok = np.flatnonzero(~np.isnan(e_est[:, 0]))
-    true_max = e_est[ok, 1:].max(axis=1)
+    cheap = e_est[ok, 1:5].max(axis=1)
+    excess = e_est[ok, 1:].max(axis=1) - cheap
     t_obs = e_est[ok, 0].max()
-    # all-zero network predicts 0: keep iff delta >= T_obs.  Choose delta just
-    # above the largest true surrogate maximum but below T_obs when possible.
-    sc = idtx.Screen(params=np.zeros(idtx.SCREEN_NPARAMS, np.float32), s0=4,
-                     delta=float(true_max.max()) + 1e-6)
+    delta = float(excess.max()) + 1e-6
+    sc = idtx.Screen(params=np.zeros(idtx.SCREEN_NPARAMS, np.float32), s0=4, delta=delta)
     idtx.screen_set(sc, ctx=ctx)
     sr = idtx.mte_step(*args, k=4, n_surr=30, seed=3, mode=idtx.MODE_SCREENED, ctx=ctx)
     assert (sr[0], sr[1], sr[3]) == (ex[0], ex[1], ex[3])
-    assert sr.n_full == (len(ok) if sc.delta >= t_obs else 0)
+    assert sr.n_full == int(np.count_nonzero(cheap + np.float32(delta) >= t_obs))
+
+
+def test_screened_step_stops_early_on_a_non_significant_step(idtx):
+    rng = np.random.default_rng(8)
+    series = rng.standard_normal((4, 1200)).astype(np.float32)   # no coupling at all
+    ctx = idtx.Context(0)
+    idtx.screen_set(idtx.Screen(delta=1e30, s0=4), ctx=ctx)      # keep every candidate
+    args = (torch.from_numpy(series).cuda(), 0, 1, 1, 3, (), 0)
+    ex = idtx.mte_step(*args, k=4, n_surr=100, seed=5, ctx=ctx)
+    sr, s_est = idtx.mte_step(*args, k=4, n_surr=100, seed=5, want_estimates=True,
+                              mode=idtx.MODE_SCREENED, ctx=ctx)
+    assert not ex[1] and not sr[1]                               # same decision
+    assert sr[0] == ex[0] and abs(sr[2] - ex[2]) < 1e-12
+    assert sr.surr_done < 100                                   # stopped early
+    assert 0.05 <= sr[3] <= ex[3]                               # a deciding lower bound
+    ok = ~np.isnan(s_est[:, 0])
+    assert np.all(np.isnan(s_est[ok][:, 1 + sr.surr_done:]))
+    assert ex.surr_done == 100
