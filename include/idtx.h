@@ -256,21 +256,25 @@ typedef struct {
 int idtx_screen_predict(idtx_ctx *ctx, const idtx_screen *screen, const float *feats, int n,
                         float *out, void *stream);
 
-/* Mean squared error over n rows and its gradient grad[IDTX_SCREEN_NPARAMS]
- * (host memory) with respect to the master parameters, taken through the
- * bf16-rounded weights (rounding treated as the identity). */
+/* Loss over n rows and its gradient grad[IDTX_SCREEN_NPARAMS] (host memory)
+ * with respect to the master parameters, taken through the bf16-rounded
+ * weights (rounding treated as the identity).  quantile == 0: mean squared
+ * error; 0 < quantile < 1: mean pinball loss (t - y)(quantile - [t < y]),
+ * whose minimiser is the conditional quantile of the targets. */
 int idtx_screen_loss_grad(idtx_ctx *ctx, const idtx_screen *screen, const float *feats,
-                          const float *targets, int n, double *loss, float *grad, void *stream);
+                          const float *targets, int n, float quantile, double *loss, float *grad,
+                          void *stream);
 
 /* Train screen->params in place on the GPU: `epochs` passes of Adam
- * (beta1 0.9, beta2 0.999, eps 1e-8, step size lr) over mini-batches of
- * `batch` rows in an order reshuffled every epoch (the Fisher-Yates shuffle
- * of the surrogates, seed `seed`, stream = epoch).  *final_loss (nullable)
- * receives the full-data loss after training.  feat_mean, feat_scale, delta
- * and s0 are left as given. */
+ * (beta1 0.9, beta2 0.999, eps 1e-8, step size lr) on the loss selected by
+ * `quantile` (as in idtx_screen_loss_grad) over mini-batches of `batch` rows
+ * in an order reshuffled every epoch (the Fisher-Yates shuffle of the
+ * surrogates, seed `seed`, stream = epoch).  *final_loss (nullable) receives
+ * the full-data loss after training.  feat_mean, feat_scale, delta and s0 are
+ * left as given. */
 int idtx_screen_train(idtx_ctx *ctx, idtx_screen *screen, const float *feats,
-                      const float *targets, int n, int epochs, int batch, float lr, uint64_t seed,
-                      double *final_loss, void *stream);
+                      const float *targets, int n, int epochs, int batch, float lr, float quantile,
+                      uint64_t seed, double *final_loss, void *stream);
 
 /* Install the screen used by IDTX_MODE_SCREENED on this context (copied). */
 int idtx_screen_set(idtx_ctx *ctx, const idtx_screen *screen);

@@ -82,7 +82,8 @@ def _load():
         lib.orc_mlp_forward.argtypes = [_F32P, ctypes.c_int, ctypes.c_int, _F32P, _F32P, _F32P,
                                         ctypes.c_int64, ctypes.c_int, _F64P]
         lib.orc_mlp_loss_grad.argtypes = [_F32P, ctypes.c_int, ctypes.c_int, _F32P, _F32P, _F32P,
-                                          _F32P, ctypes.c_int64, ctypes.c_int, _F64P, _F64P]
+                                          _F32P, ctypes.c_int64, ctypes.c_int, ctypes.c_double,
+                                          _F64P, _F64P]
         lib.orc_num_threads.restype = ctypes.c_int
         lib.orc_set_num_threads.argtypes = [ctypes.c_int]
         _lib = lib
@@ -256,8 +257,9 @@ def mlp_forward(params, f, h, mean, scale, x, bf16: bool = True) -> np.ndarray:
     return y
 
 
-def mlp_loss_grad(params, f, h, mean, scale, x, t, bf16: bool = True):
-    """(mean squared error, gradient [n_params]) in fp64."""
+def mlp_loss_grad(params, f, h, mean, scale, x, t, bf16: bool = True, quantile: float = 0.0):
+    """(loss, gradient [n_params]) in fp64: mean squared error, or the mean pinball
+    loss of the given quantile when 0 < quantile < 1."""
     p = np.ascontiguousarray(np.asarray(params, np.float32))
     x = np.ascontiguousarray(np.asarray(x, np.float32).reshape(-1, f))
     t = np.ascontiguousarray(np.asarray(t, np.float32))
@@ -266,7 +268,7 @@ def mlp_loss_grad(params, f, h, mean, scale, x, t, bf16: bool = True):
     loss = ctypes.c_double()
     g = np.empty(mlp_nparams(f, h), np.float64)
     if _load().orc_mlp_loss_grad(_fp(p), f, h, _fp(mean), _fp(scale), _fp(x), _fp(t),
-                                 x.shape[0], 1 if bf16 else 0, ctypes.byref(loss),
-                                 g.ctypes.data_as(_F64P)) != 0:
+                                 x.shape[0], 1 if bf16 else 0, float(quantile),
+                                 ctypes.byref(loss), g.ctypes.data_as(_F64P)) != 0:
         raise ValueError("orc_mlp_loss_grad: invalid arguments")
     return loss.value, g

@@ -502,12 +502,15 @@ int orc_mlp_forward(const float *p, int f, int h, const float *mean, const float
     return 0;
 }
 
-/* Mean squared error L = (1/n) sum (y - t)^2 and its gradient with respect to
- * every parameter (derivatives taken through the bf16-rounded weights, i.e.
- * d L / d p evaluated at the rounded values, the rounding treated as identity). */
+/* Loss over n rows and its gradient with respect to every parameter
+ * (derivatives taken through the bf16-rounded weights, i.e. d L / d p evaluated
+ * at the rounded values, the rounding treated as identity).  quantile == 0:
+ * mean squared error L = (1/n) sum (y - t)^2; 0 < quantile < 1: mean pinball
+ * loss L = (1/n) sum rho(t - y), rho(u) = u (quantile - [u < 0]), whose
+ * minimiser is the conditional quantile of t. */
 int orc_mlp_loss_grad(const float *p, int f, int h, const float *mean, const float *scale,
-                      const float *x, const float *t, int64_t n, int bf16, double *loss,
-                      double *grad)
+                      const float *x, const float *t, int64_t n, int bf16, double quantile,
+                      double *loss, double *grad)
 {
     if (!p || !x || !t || !loss || !grad || f < 1 || h < 1 || n < 1) return -1;
     int np = orc_mlp_nparams(f, h);
@@ -544,8 +547,15 @@ int orc_mlp_loss_grad(const float *p, int f, int h, const float *mean, const flo
         double y = b3[0];
         for (int j = 0; j < h; ++j) y += w3[j] * a2[j];
         double r = y - (double)t[s];
-        l += r * r;
-        double dy = 2.0 * r / (double)n;
+        double dy;
+        if (quantile > 0.0) {
+            double u = -r; /* t - y */
+            l += u * (quantile - (u < 0.0 ? 1.0 : 0.0));
+            dy = ((u < 0.0 ? 1.0 : 0.0) - quantile) / (double)n;
+        } else {
+            l += r * r;
+            dy = 2.0 * r / (double)n;
+        }
         gb3[0] += dy;
         for (int j = 0; j < h; ++j) {
             gw3[j] += dy * a2[j];

@@ -105,10 +105,11 @@ def load():
                                                ctypes.POINTER(i32), vp]
         lib.idtx_screen_predict.argtypes = [vp, ctypes.POINTER(ScreenC), vp, i32, vp, vp]
         lib.idtx_screen_loss_grad.argtypes = [vp, ctypes.POINTER(ScreenC), vp, vp, i32,
-                                              ctypes.POINTER(ctypes.c_double), vp, vp]
+                                              ctypes.c_float, ctypes.POINTER(ctypes.c_double),
+                                              vp, vp]
         lib.idtx_screen_train.argtypes = [vp, ctypes.POINTER(ScreenC), vp, vp, i32, i32, i32,
-                                          ctypes.c_float, u64, ctypes.POINTER(ctypes.c_double),
-                                          vp]
+                                          ctypes.c_float, ctypes.c_float, u64,
+                                          ctypes.POINTER(ctypes.c_double), vp]
         lib.idtx_screen_set.argtypes = [vp, ctypes.POINTER(ScreenC)]
         lib.idtx_ctx_set_profiling.argtypes = [vp, i32]
         lib.idtx_ctx_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
@@ -241,7 +242,8 @@ def screen_predict(screen: Screen, feats, ctx: Context | None = None) -> np.ndar
     return out
 
 
-def screen_loss_grad(screen: Screen, feats, targets, ctx: Context | None = None):
+def screen_loss_grad(screen: Screen, feats, targets, quantile: float = 0.0,
+                     ctx: Context | None = None):
     f = np.ascontiguousarray(np.asarray(feats, np.float32).reshape(-1, SCREEN_F))
     t = np.ascontiguousarray(np.asarray(targets, np.float32))
     g = np.empty(SCREEN_NPARAMS, np.float32)
@@ -249,13 +251,13 @@ def screen_loss_grad(screen: Screen, feats, targets, ctx: Context | None = None)
     ctx = ctx or default_context(0)
     sc = screen.to_c()
     _check(load().idtx_screen_loss_grad(ctx.handle, ctypes.byref(sc), f.ctypes.data,
-                                        t.ctypes.data, f.shape[0], ctypes.byref(loss),
-                                        g.ctypes.data, None))
+                                        t.ctypes.data, f.shape[0], float(quantile),
+                                        ctypes.byref(loss), g.ctypes.data, None))
     return loss.value, g
 
 
 def screen_train(screen: Screen, feats, targets, epochs=100, batch=256, lr=1e-3, seed=0,
-                 ctx: Context | None = None) -> float:
+                 quantile: float = 0.0, ctx: Context | None = None) -> float:
     """Train screen.params in place on the GPU; returns the final full-data loss."""
     f = np.ascontiguousarray(np.asarray(feats, np.float32).reshape(-1, SCREEN_F))
     t = np.ascontiguousarray(np.asarray(targets, np.float32))
@@ -264,7 +266,8 @@ def screen_train(screen: Screen, feats, targets, epochs=100, batch=256, lr=1e-3,
     loss = ctypes.c_double()
     _check(load().idtx_screen_train(ctx.handle, ctypes.byref(sc), f.ctypes.data, t.ctypes.data,
                                     f.shape[0], int(epochs), int(batch), float(lr),
-                                    ctypes.c_uint64(int(seed)).value, ctypes.byref(loss), None))
+                                    float(quantile), ctypes.c_uint64(int(seed)).value,
+                                    ctypes.byref(loss), None))
     screen.params = np.ctypeslib.as_array(sc.params).astype(np.float32).copy()
     return loss.value
 

@@ -93,7 +93,8 @@ cudaError_t mlp_forward(const float *params, MlpWork &w, const float *feats,
                         const int32_t *order, int64_t start, int B, const float *mean,
                         const float *scale, cudaStream_t st);
 cudaError_t mlp_loss(MlpWork &w, const float *targets, const int32_t *order, int64_t start, int B,
-                     float dy_scale, bool want_dy, double *loss_acc, cudaStream_t st);
+                     float dy_scale, float quantile, bool want_dy, double *loss_acc,
+                     cudaStream_t st);
 cudaError_t mlp_backward(MlpWork &w, int B, bool accumulate, cudaStream_t st);
 cudaError_t mlp_adam(float *params, const float *grad, float *m, float *v, int step, float lr,
                      cudaStream_t st);

@@ -1574,12 +1574,13 @@ extern "C" int idtx_screen_predict(idtx_ctx *c, const idtx_screen *sc, const flo
 }
 
 extern "C" int idtx_screen_loss_grad(idtx_ctx *c, const idtx_screen *sc, const float *feats,
-                                     const float *targets, int n, double *loss, float *grad,
-                                     void *stream)
+                                     const float *targets, int n, float quantile, double *loss,
+                                     float *grad, void *stream)
 {
     if (!c) return fail(IDTX_EINVAL, "ctx is NULL");
     if (!feats || !targets || !loss || !grad || n < 1)
         return fail(IDTX_EINVAL, "bad features, targets or outputs");
+    if (!(quantile >= 0.0f && quantile < 1.0f)) return fail(IDTX_EINVAL, "quantile not in [0,1)");
     IDTX_TRY(check_screen(sc));
     DeviceGuard guard(c->device);
     cudaStream_t st = (cudaStream_t)stream;
@@ -1598,7 +1599,8 @@ extern "C" int idtx_screen_loss_grad(idtx_ctx *c, const idtx_screen *sc, const f
     mlp_work_carve((float *)c->buf[B_MLP], n, &w);
     IDTX_CUDA(mlp_round(params, w, st));
     IDTX_CUDA(mlp_forward(params, w, fd, nullptr, 0, n, mean, scale, st));
-    IDTX_CUDA(mlp_loss(w, td, nullptr, 0, n, 2.0f / (float)n, true, loss_d, st));
+    IDTX_CUDA(mlp_loss(w, td, nullptr, 0, n, (quantile > 0.0f ? 1.0f : 2.0f) / (float)n, quantile,
+                       true, loss_d, st));
     IDTX_CUDA(mlp_backward(w, n, false, st));
     c->stats.kernel_launches += 11;
     double lsum = 0.0;
@@ -1612,11 +1614,12 @@ extern "C" int idtx_screen_loss_grad(idtx_ctx *c, const idtx_screen *sc, const f
 
 extern "C" int idtx_screen_train(idtx_ctx *c, idtx_screen *sc, const float *feats,
                                  const float *targets, int n, int epochs, int batch, float lr,
-                                 uint64_t seed, double *final_loss, void *stream)
+                                 float quantile, uint64_t seed, double *final_loss, void *stream)
 {
     if (!c) return fail(IDTX_EINVAL, "ctx is NULL");
     if (!feats || !targets || n < 1 || epochs < 0 || batch < 1 || !(lr > 0.0f))
         return fail(IDTX_EINVAL, "bad training arguments");
+    if (!(quantile >= 0.0f && quantile < 1.0f)) return fail(IDTX_EINVAL, "quantile not in [0,1)");
     IDTX_TRY(check_screen(sc));
     DeviceGuard guard(c->device);
     cudaStream_t st = (cudaStream_t)stream;
@@ -1653,7 +1656,9 @@ extern "C" int idtx_screen_train(idtx_ctx *c, idtx_screen *sc, const float *feat
             const int bsz = std::min(batch, n - start);
             IDTX_CUDA(mlp_round(params, w, st));
             IDTX_CUDA(mlp_forward(params, w, fd, order, start, bsz, mean, scale, st));
-            IDTX_CUDA(mlp_loss(w, td, order, start, bsz, 2.0f / (float)bsz, true, loss_d, st));
+            IDTX_CUDA(mlp_loss(w, td, order, start, bsz,
+                               (quantile > 0.0f ? 1.0f : 2.0f) / (float)bsz, quantile, true,
+                               loss_d, st));
             IDTX_CUDA(mlp_backward(w, bsz, false, st));
             IDTX_CUDA(mlp_adam(params, w.grad, m, v, ++step, lr, st));
             c->stats.kernel_launches += 12;
@@ -1666,7 +1671,7 @@ extern "C" int idtx_screen_train(idtx_ctx *c, idtx_screen *sc, const float *feat
     for (int start = 0; start < n; start += wb) {
         const int bsz = std::min(wb, n - start);
         IDTX_CUDA(mlp_forward(params, w, fd, nullptr, start, bsz, mean, scale, st));
-        IDTX_CUDA(mlp_loss(w, td, nullptr, start, bsz, 0.0f, false, loss_d, st));
+        IDTX_CUDA(mlp_loss(w, td, nullptr, start, bsz, 0.0f, quantile, false, loss_d, st));
     }
     double lsum = 0.0;
     IDTX_CUDA(cudaMemcpyAsync(&lsum, loss_d, sizeof(double), cudaMemcpyDeviceToHost, st));

@@ -54,17 +54,25 @@ __global__ void k_dense_fwd(const float *in, const __nv_bfloat16 *W, const float
     a[idx] = relu ? fmaxf(acc, 0.0f) : acc;
 }
 
-// dy[b] = scale * (y[b] - t[row(b)]); loss_acc += sum_b (y - t)^2 (one block, fixed order).
+// Squared error (quantile == 0): dy[b] = scale * (y - t), loss_acc += sum (y - t)^2.
+// Pinball loss of quantile q: dy[b] = scale * ([t < y] - q), loss_acc += sum
+// (t - y)(q - [t < y]).  One block, fixed order.
 __global__ void k_loss(const float *y, const float *targets, const int32_t *order, int64_t start,
-                       int B, float scale, float *dy, double *loss_acc)
+                       int B, float scale, float quantile, float *dy, double *loss_acc)
 {
     __shared__ double s_part[256];
     double part = 0.0;
     for (int b = threadIdx.x; b < B; b += blockDim.x) {
         const int64_t r = order ? (int64_t)order[start + b] : start + b;
         const float d = y[b] - targets[r];
-        if (dy) dy[b] = scale * d;
-        part += (double)d * (double)d;
+        if (quantile > 0.0f) {
+            const float below = d > 0.0f ? 1.0f : 0.0f;  // [t < y]
+            if (dy) dy[b] = scale * (below - quantile);
+            part += (double)(-d) * ((double)quantile - (double)below);
+        } else {
+            if (dy) dy[b] = scale * d;
+            part += (double)d * (double)d;
+        }
     }
     s_part[threadIdx.x] = part;
     __syncthreads();
@@ -159,10 +167,11 @@ cudaError_t mlp_forward(const float *params, MlpWork &w, const float *feats,
 }
 
 cudaError_t mlp_loss(MlpWork &w, const float *targets, const int32_t *order, int64_t start, int B,
-                     float dy_scale, bool want_dy, double *loss_acc, cudaStream_t st)
+                     float dy_scale, float quantile, bool want_dy, double *loss_acc,
+                     cudaStream_t st)
 {
-    k_loss<<<1, 256, 0, st>>>(w.y, targets, order, start, B, dy_scale, want_dy ? w.dy : nullptr,
-                              loss_acc);
+    k_loss<<<1, 256, 0, st>>>(w.y, targets, order, start, B, dy_scale, quantile,
+                              want_dy ? w.dy : nullptr, loss_acc);
     return cudaGetLastError();
 }
 

@@ -46,12 +46,13 @@ def test_forward_matches_oracle(idtx):
     assert np.max(np.abs(got - ref)) <= 1e-5 * max(1.0, np.max(np.abs(ref)))
 
 
-def test_gradient_matches_oracle(idtx):
+@pytest.mark.parametrize("quantile", [0.0, 0.95])
+def test_gradient_matches_oracle(idtx, quantile):
     sc = _screen(idtx, 3)
     x, t = _data(257, 4)
-    loss, g = idtx.screen_loss_grad(sc, x, t)
+    loss, g = idtx.screen_loss_grad(sc, x, t, quantile=quantile)
     rl, rg = oracle.mlp_loss_grad(sc.params, 10, 64, sc.feat_mean, sc.feat_scale, x, t,
-                                  bf16=True)
+                                  bf16=True, quantile=quantile)
     assert abs(loss - rl) <= 1e-5 * max(1.0, rl)
     assert np.max(np.abs(g - rg)) <= 1e-4 * max(1.0, np.max(np.abs(rg)))
 

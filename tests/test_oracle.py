@@ -302,18 +302,19 @@ def test_bf16_rounding_matches_library_conversion():
     assert np.array_equal(got, ref)
 
 
-def test_mlp_gradient_matches_finite_differences():
+@pytest.mark.parametrize("quantile", [0.0, 0.9])
+def test_mlp_gradient_matches_finite_differences(quantile):
     f, h = 3, 5
     p, x, t, mean, scale = _rand_net(f, h, 1)
-    loss, g = oracle.mlp_loss_grad(p, f, h, mean, scale, x, t, bf16=False)
+    loss, g = oracle.mlp_loss_grad(p, f, h, mean, scale, x, t, bf16=False, quantile=quantile)
 
     def fd(idx, eps):
         hi, lo = p.copy(), p.copy()
         hi[idx] += np.float32(eps)
         lo[idx] -= np.float32(eps)
         step = float(hi[idx]) - float(lo[idx])
-        lh, _ = oracle.mlp_loss_grad(hi, f, h, mean, scale, x, t, bf16=False)
-        ll, _ = oracle.mlp_loss_grad(lo, f, h, mean, scale, x, t, bf16=False)
+        lh, _ = oracle.mlp_loss_grad(hi, f, h, mean, scale, x, t, bf16=False, quantile=quantile)
+        ll, _ = oracle.mlp_loss_grad(lo, f, h, mean, scale, x, t, bf16=False, quantile=quantile)
         return (lh - ll) / step
 
     checked = 0
@@ -357,3 +358,25 @@ def test_mlp_forward_closed_form_linear_case():
         a1 = W1 @ x[s] + b1
         a2 = W2 @ a1 + b2
         assert abs(y[s] - (w3 @ a2 + b3[0])) < 1e-12
+
+
+def test_pinball_loss_of_a_constant_is_minimised_at_the_quantile():
+    # zero weights: the network is the constant b3; the pinball loss over a
+    # sample is smallest when that constant is the sample's quantile
+    f, h = 2, 3
+    rng = np.random.default_rng(6)
+    t = rng.standard_normal(2001).astype(np.float32)
+    x = np.zeros((2001, f), np.float32)
+    p = np.zeros(oracle.mlp_nparams(f, h), np.float32)
+    q = 0.9
+    best = np.quantile(t, q, method="inverted_cdf")
+    losses = []
+    for c in (best - 0.05, best, best + 0.05):
+        p[-1] = c
+        losses.append(oracle.mlp_loss_grad(p, f, h, np.zeros(f, np.float32),
+                                           np.ones(f, np.float32), x, t, quantile=q)[0])
+    assert losses[1] < losses[0] and losses[1] < losses[2]
+    p[-1] = best
+    _, g = oracle.mlp_loss_grad(p, f, h, np.zeros(f, np.float32), np.ones(f, np.float32), x, t,
+                                quantile=q)
+    assert abs(g[-1] - (np.count_nonzero(t < best) / 2001 - q)) < 1e-12
