@@ -339,18 +339,29 @@ def run_var50(args):
     net = synth.var_network_indegree(n_nodes=50, order=3, indegree=3, T=5000)
     s = torch.from_numpy(net.series).cuda()
     ctx = idtx.Context(0)
-    idtx.screen_set(idtx.Screen.load(os.path.join(ROOT, "paper_1807_10459_gb300",
-                                                  "screen_weights.npz")), ctx=ctx)
+    trained = idtx.Screen.load(os.path.join(ROOT, "paper_1807_10459_gb300",
+                                            "screen_weights.npz"))
+    # the network-free rule the trained network improves on: cheap maximum plus
+    # a constant margin calibrated the same way (an all-zero network)
+    free = idtx.Screen(params=np.zeros(idtx.SCREEN_NPARAMS, np.float32), s0=trained.s0,
+                       delta=float(trained.meta["network_free_margin"]))
+    ctx_free = idtx.Context(0)
+    idtx.screen_set(trained, ctx=ctx)
+    idtx.screen_set(free, ctx=ctx_free)
     kw = dict(k=4, n_surr=200, alpha=0.05, seed=20181031, max_parents=10, ctx=ctx)
     idtx.mte_select_target(s, 0, 3, 1, 3, **kw)      # warm-up
     torch.cuda.synchronize()
     res = {}
-    for mode_name, mode in (("exact", idtx.MODE_BATCHED), ("screened", idtx.MODE_SCREENED)):
+    for mode_name, mode, c in (("exact", idtx.MODE_BATCHED, ctx),
+                               ("screened", idtx.MODE_SCREENED, ctx),
+                               ("network_free", idtx.MODE_SCREENED, ctx_free)):
+        kw["ctx"] = c
         out, t0 = [], time.perf_counter()
         for t in range(50):
             out.append(idtx.mte_select_target(s, t, 3, 1, 3, mode=mode, **kw))
         torch.cuda.synchronize()
         res[mode_name] = (out, time.perf_counter() - t0)
+    nf = res["network_free"][0]
     ex, sc = res["exact"][0], res["screened"][0]
     same = [a["parents"] == b["parents"] for a, b in zip(ex, sc)]
     steps_same = sum(1 for a, b in zip(ex, sc) for u, v in zip(a["steps"], b["steps"])
@@ -367,6 +378,16 @@ def run_var50(args):
             "parent_set_agreement": sum(same) / len(same),
             "step_decision_agreement": steps_same / n_steps,
             "candidates_with_full_surrogates": full, "candidates_evaluated": cands,
+            "network_free": {
+                "seconds": res["network_free"][1],
+                "speedup": res["exact"][1] / res["network_free"][1],
+                "parent_set_agreement": sum(a["parents"] == b["parents"]
+                                            for a, b in zip(ex, nf)) / len(ex),
+                "candidates_with_full_surrogates": sum(st.n_full for b in nf
+                                                       for st in b["steps"]),
+                "margin": free.delta},
+            "screen": {"delta": trained.delta, "s0": trained.s0,
+                       "quantile": trained.meta.get("quantile")},
             "exact_true_positive_edges": len(found & truth), "true_edges": len(truth),
             "exact_false_positive_edges": len(found - truth), "data": "synthetic"}
     print(json.dumps(line), flush=True)

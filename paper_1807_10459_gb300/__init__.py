@@ -222,14 +222,23 @@ class Screen:
         return c
 
     def save(self, path: str, **meta):
+        import json
         np.savez(path, params=self.params, feat_mean=self.feat_mean, feat_scale=self.feat_scale,
                  delta=np.float32(self.delta), s0=np.int32(self.s0),
-                 meta=np.array(repr(meta)))
+                 meta=np.array(json.dumps(meta)))
 
     @classmethod
     def load(cls, path: str) -> "Screen":
+        import ast
+        import json
         d = np.load(path)
-        return cls(d["params"], d["feat_mean"], d["feat_scale"], float(d["delta"]), int(d["s0"]))
+        sc = cls(d["params"], d["feat_mean"], d["feat_scale"], float(d["delta"]), int(d["s0"]))
+        raw = str(d["meta"]) if "meta" in d else "{}"
+        try:
+            sc.meta = json.loads(raw)
+        except ValueError:
+            sc.meta = ast.literal_eval(raw)
+        return sc
 
 
 def screen_predict(screen: Screen, feats, ctx: Context | None = None) -> np.ndarray:
