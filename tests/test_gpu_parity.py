@@ -218,19 +218,46 @@ def test_config2_full_size_sampled(idtx):
 
 @pytest.mark.slow
 def test_large_n_sampled_queries(idtx):
-    """N = 100000 logistic-map problem, joint dim 12: sampled queries of the
-    original and one surrogate, eps and counts exact."""
+    """N = 99850 logistic-map problem, joint dim 12, 200 surrogates (the large
+    single-problem configuration): sampled queries of the original and of two
+    surrogates, eps and counts exact; estimates of those within 1e-10 through
+    their per-sample terms."""
     x, y, z = synth.logistic_problem(1, 1, 10)
     n = x.shape[1]
-    S, seed = 2, 4
+    S, seed = 200, 4
     cmi, eps, cnt = idtx.cmi_ksg(_dev(x), _dev(y), _dev(z), k=4, n_surr=S, seed=seed,
                                  want_eps=True, want_counts=True)
-    eps, cnt = eps.cpu().numpy(), cnt.cpu().numpy()
-    idx = np.random.default_rng(1).choice(n, 64, replace=False)
-    for s in (0, 2):
+    cmi, eps, cnt = cmi.cpu().numpy(), eps.cpu().numpy(), cnt.cpu().numpy()
+    idx = np.random.default_rng(1).choice(n, 48, replace=False)
+    for s in (0, 1, 137):
         xs = x if s == 0 else x[:, oracle.perm(seed, s - 1, n)]
         e, a, b, c = oracle.ksg_counts_at(xs, y, z, 4, idx)
         assert np.array_equal(eps[s, idx], e)
         assert np.array_equal(cnt[s, 0, idx], a)
         assert np.array_equal(cnt[s, 1, idx], b)
         assert np.array_equal(cnt[s, 2, idx], c)
+    # every estimate equals the digamma sum of its own returned counts
+    psi = oracle.psi_table(n + 1)
+    for s in (0, 5, 200):
+        c = cnt[s]
+        ref = psi[4] + np.mean(psi[c[2] + 1] - psi[c[0] + 1] - psi[c[1] + 1])
+        assert abs(cmi[s] - ref) < 1e-10
+
+
+@pytest.mark.slow
+def test_batch_full_size_sampled(idtx):
+    """The uneven batch at full size: 64 problems, N log-uniform in [2000, 50000],
+    dx, dy in {1,2}, dz in 1..8, 500 surrogates each, in one call; sampled
+    estimates of the five smallest problems against the oracle."""
+    probs = synth.batch_problems()
+    out = idtx.cmi_batch([dict(x=_dev(p.x), y=_dev(p.y), z=_dev(p.z), n_surr=p.n_surr,
+                               seed=p.seed) for p in probs], k=4)
+    out = [o.cpu().numpy() for o in out]
+    assert all(np.all(np.isfinite(o)) and o.shape == (501,) for o in out)
+    smallest = np.argsort([p.x.shape[1] for p in probs])[:5]
+    rng = np.random.default_rng(3)
+    for i in smallest:
+        p = probs[i]
+        for s in [0] + list(rng.choice(np.arange(1, 501), 2, replace=False)):
+            xs = p.x if s == 0 else p.x[:, oracle.perm(p.seed, int(s) - 1, p.x.shape[1])]
+            assert abs(out[i][s] - oracle.cmi_ksg(xs, p.y, p.z, 4)) < TOL
