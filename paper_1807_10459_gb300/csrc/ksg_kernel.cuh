@@ -8,35 +8,42 @@
 //   n_xz, n_yz, n_z = strict-radius counts in the subspaces,
 // then the per-query digamma term and its sum over the CTA's queries.
 //
-// Design (GB300).  A CTA holds 32 jobs, one per lane, and NW*QW queries; each
-// of its NW warps takes QW consecutive queries and works on one query at a time
+// Design (GB300).  A CTA holds 32 jobs, one per lane, and QC queries; the
+// unit of work is one (query, reference tile) pair, which a warp processes
 // with all 32 jobs in parallel.
 //   * All jobs of a group share Y and Z (a surrogate only permutes X, and the
-//     candidates of one greedy step differ only in X).  For a (query, tile)
-//     the warp computes the Y/Z distances of the tile's 128 references once,
-//     four per lane, and a ballot marks the references below the query's
-//     bound (the largest current threshold over the 32 jobs).  The per-job
-//     work then runs only for those references, warp-uniformly, every lane
-//     doing its own job: no divergence and no idle lanes.
+//     candidates of one greedy step differ only in X).  For a unit the warp
+//     computes the Y/Z distances of the tile's 128 references once, four per
+//     lane, and a ballot marks the references below the query's bound (the
+//     largest current threshold over the 32 jobs).  The per-job work then
+//     runs only for those references, warp-uniformly, every lane doing its
+//     own job: no divergence and no idle lanes.
 //   * Pass A keeps, per (query, job), the k+1 smallest joint distances in a
-//     sorted register array.  The sample itself is never skipped: its own
-//     distance 0 occupies one slot, so the (k+1)-th smallest including it is
-//     the k-th smallest over j != i.
+//     sorted array.  The sample itself is never skipped: its own distance 0
+//     occupies one slot, so the (k+1)-th smallest including it is the k-th
+//     smallest over j != i.
 //   * Pass B counts with the same tiles; the pair (i,i) is counted when
 //     eps_i > 0 and is subtracted at the end.  A pair can only count when its
 //     Z distance is below the largest eps of the query's jobs.
+//   * Load balance.  Queries differ widely in work (dense regions pass many
+//     references), so units are not owned statically: for each staged tile,
+//     warps take the next query from a shared counter.  The per-(query, job)
+//     state (heaps, counts, bounds) lives in shared memory; a query's heaps
+//     are updated under a per-query lock (the final k+1 smallest do not
+//     depend on the order of updates), its counts with shared atomics, and
+//     its count units wait until all its heap units are done.
 //   * Samples are stored along a Morton curve of the shared coordinates, so a
-//     warp's queries and a tile's references are spatial neighbours; tiles are
-//     visited in a spiral from the CTA's own tile, and a warp (then a query)
-//     skips a tile whose bounding box (stored with the tile) is at least the
+//     CTA's queries and a tile's references are spatial neighbours; tiles are
+//     visited in a spiral from the CTA's own tile, and a unit is skipped when
+//     the tile's bounding box (stored with the tile) is at least the query's
 //     bound away.  Skipping never changes a result.
 //   * Reference tiles (128 samples of sh with the box, and of xi) are staged
 //     into shared memory by 1-D TMA bulk copies (cp.async.bulk) completing on
 //     per-stage mbarriers, 2-4 stages deep; both passes stream the same tiles.
-//     Warps walk the tiles independently; the last warp to finish a stage
-//     refills it, so there is no CTA-wide barrier per tile.  Every mbarrier
-//     wait is bounded by %globaltimer; on expiry the CTA records kErrTimeout,
-//     waits (bounded) for its own copies in flight and exits without output.
+//     The unit that finishes a tile refills its stage; there is no CTA-wide
+//     barrier per tile.  Every wait (mbarrier, lock, pass order) is bounded by
+//     %globaltimer; on expiry the CTA records kErrTimeout, waits (bounded) for
+//     its own copies in flight and exits without output.
 //   * Padding samples (j >= n) are +inf in every column, so they never enter
 //     a heap or a count; padding queries and padding jobs are kept out of
 //     every bound and masked out of all outputs.
@@ -49,19 +56,19 @@
 
 // Launch-shape knobs (compile-time; the defaults are the tuned values).
 #ifndef IDTX_STAGE_BUDGET_KB
-#define IDTX_STAGE_BUDGET_KB 80
+#define IDTX_STAGE_BUDGET_KB 60
 #endif
 #ifndef IDTX_MAX_STAGES
 #define IDTX_MAX_STAGES 4
 #endif
-#ifndef IDTX_ROWREG_MAX_DS
-#define IDTX_ROWREG_MAX_DS 0
-#endif
-#ifndef IDTX_FAST_QW
-#define IDTX_FAST_QW 2
+#ifndef IDTX_FAST_QC
+#define IDTX_FAST_QC 32
 #endif
 #ifndef IDTX_FAST_NW
-#define IDTX_FAST_NW 16
+#define IDTX_FAST_NW 8
+#endif
+#ifndef IDTX_QUERY_GROUP
+#define IDTX_QUERY_GROUP 4
 #endif
 
 namespace idtx {
@@ -215,17 +222,17 @@ __device__ __forceinline__ float point_gap(const float *rs, const float (&q)[DS]
     return gap;
 }
 
-template <int DX, int DY, int DZ, int K1, bool EXACT, int QW, int NWARPS>
+template <int DX, int DY, int DZ, int K1, bool EXACT, int QCTA, int NWARPS>
 struct KsgShape {
     static constexpr int GB = 32;  // jobs per CTA: one per lane
     static constexpr int NW = NWARPS;  // warps per CTA
     static constexpr int THREADS = NW * 32;
-    static constexpr int QC = NW * QW;  // queries per CTA
+    static constexpr int QC = QCTA;  // queries per CTA
+    static constexpr int QG = QC < IDTX_QUERY_GROUP ? QC : IDTX_QUERY_GROUP;  // per claim
     static constexpr int DS = DZ + DY;
     static constexpr int DSP = (DS + 3) & ~3;
     static constexpr int XW = GB * DX;
     static constexpr int RPL = kTJ / 32;  // references per lane in a tile
-    static constexpr bool ROWREG = DS <= IDTX_ROWREG_MAX_DS;  // lane's tile rows in registers
     static constexpr uint32_t SH_BYTES = kTileRows * DSP * sizeof(float);
     static constexpr uint32_t X_BYTES = kTJ * XW * sizeof(float);
     static constexpr uint32_t STAGE_BYTES = SH_BYTES + X_BYTES;
@@ -233,64 +240,90 @@ struct KsgShape {
     static constexpr int STAGES_RAW = (IDTX_STAGE_BUDGET_KB * 1024) / STAGE_BYTES;
     static constexpr int STAGES =
         STAGES_RAW < 2 ? 2 : (STAGES_RAW > IDTX_MAX_STAGES ? IDTX_MAX_STAGES : STAGES_RAW);
-    static constexpr size_t Q_OFF = (size_t)STAGES * STAGE_BYTES + STAGES * sizeof(uint64_t);
-    static constexpr size_t SMEM = Q_OFF + (size_t)QC * DSP * sizeof(float);
+    // dynamic shared memory: stages | barriers | query rows | heaps | k-th
+    // values (!EXACT) | counts | query X values | per-warp event lists
+    static constexpr size_t BAR_OFF = (size_t)STAGES * STAGE_BYTES;
+    static constexpr size_t Q_OFF = (BAR_OFF + STAGES * sizeof(uint64_t) + 15) & ~size_t(15);
+    static constexpr size_t H_OFF = Q_OFF + (size_t)QC * DSP * sizeof(float);
+    static constexpr size_t KTH_OFF = H_OFF + (size_t)QC * K1 * 32 * sizeof(float);
+    static constexpr size_t CNT_OFF = KTH_OFF + (EXACT ? 0 : (size_t)QC * 32 * sizeof(float));
+    static constexpr size_t XQ_OFF = CNT_OFF + (size_t)QC * 3 * 32 * sizeof(int);
+    static constexpr size_t EV_OFF = XQ_OFF + (size_t)QC * DX * 32 * sizeof(float);
+    static constexpr int EV_CAP = kTJ + 4;  // a tile's references + sentinel padding
+    static constexpr size_t SMEM = EV_OFF + (size_t)NW * EV_CAP * sizeof(float4);
     static_assert(kTJ % QC == 0, "query tiles nest in reference tiles");
-    static_assert(DS <= 32, "one lane per shared dimension in the box test");
+    static_assert(QC % QG == 0 && QG <= 32, "query groups tile the CTA's queries");
+    static_assert(DS <= 32, "one lane per shared dimension");
     static_assert(STAGE_BYTES % 16 == 0, "bulk copies need 16-byte multiples");
+    static_assert(EV_OFF % 16 == 0, "event lists are read as float4");
 };
 
-template <int DX, int DY, int DZ, int K1, bool EXACT, int QW, int NWARPS>
-__global__ void __launch_bounds__(KsgShape<DX, DY, DZ, K1, EXACT, QW, NWARPS>::THREADS)
+template <int DX, int DY, int DZ, int K1, bool EXACT, int QCTA, int NWARPS>
+__global__ void __launch_bounds__(KsgShape<DX, DY, DZ, K1, EXACT, QCTA, NWARPS>::THREADS)
     ksg_fused_kernel(const KsgLaunch a)
 {
-    using S = KsgShape<DX, DY, DZ, K1, EXACT, QW, NWARPS>;
+    using S = KsgShape<DX, DY, DZ, K1, EXACT, QCTA, NWARPS>;
     constexpr int DS = S::DS, DSP = S::DSP, XW = S::XW, NW = S::NW, GB = S::GB, QC = S::QC;
-    constexpr int ST = S::STAGES, RPL = S::RPL;
+    constexpr int ST = S::STAGES, RPL = S::RPL, QG = S::QG;
     constexpr int kShStage = kTileRows * DSP;  // floats of one sh tile
-    // The lane's tile rows live in registers r[RR][RD] when S::ROWREG, else
-    // they are read from shared memory each time (r is then a 1x1 dummy).
-    constexpr int RR = S::ROWREG ? RPL : 1, RD = S::ROWREG ? DSP : 1;
-    auto RI = [](int k) { return S::ROWREG ? k : 0; };
-    auto RJ = [](int d) { return S::ROWREG ? d : 0; };
+    constexpr unsigned kFull = 0xffffffffu;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem_raw + (size_t)ST * S::STAGE_BYTES);
-    float *s_q = reinterpret_cast<float *>(smem_raw + S::Q_OFF);  // [QC][DSP] query rows
+    uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem_raw + S::BAR_OFF);
+    float *s_q = reinterpret_cast<float *>(smem_raw + S::Q_OFF);      // [QC][DSP]
+    float *s_h = reinterpret_cast<float *>(smem_raw + S::H_OFF);      // [QC][K1][32]
+    float *s_kth = reinterpret_cast<float *>(smem_raw + S::KTH_OFF);  // [QC][32]
+    int *s_cnt = reinterpret_cast<int *>(smem_raw + S::CNT_OFF);      // [QC][3][32]
+    float *s_xq = reinterpret_cast<float *>(smem_raw + S::XQ_OFF);    // [QC][DX][32]
+    __shared__ float s_b[QC];    // per query: pass-A bound (largest job threshold)
+    __shared__ int s_lock[QC];   // per query: owner of its heaps (pass A)
+    __shared__ int s_next;       // next unit to take
+    __shared__ int s_items_a;    // pass-A items finished
+    __shared__ int s_fin[ST];    // units finished of the stage's current item
     __shared__ int s_abort;
-    __shared__ int s_done[ST];  // warps finished with the stage's current item
-    __shared__ int s_last[ST];  // last item issued into the stage
+    __shared__ int s_last[ST];   // item last issued into the stage
     __shared__ double s_red[NW][GB];
     volatile int *abort_flag = &s_abort;
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
+    // this warp's event list: the references of a unit below the bound
+    float4 *s_ev = reinterpret_cast<float4 *>(smem_raw + S::EV_OFF) + warp * S::EV_CAP;
     const int qt = blockIdx.x;
     const int grp = blockIdx.y;
-    const int64_t q0 = static_cast<int64_t>(qt) * QC;        // CTA's first query (sorted)
-    const int64_t qw0 = q0 + warp * QW;                      // warp's first query
+    const int64_t q0 = static_cast<int64_t>(qt) * QC;  // CTA's first query (sorted)
     const int n_tiles = static_cast<int>(a.n_pad / kTJ);
     const int total = 2 * n_tiles;  // items: pass A tiles, then pass B tiles
     const int home = static_cast<int>(q0 / kTJ);
+    const int qv = static_cast<int>(a.n - q0 < QC ? a.n - q0 : QC);  // valid queries
     const int job = grp * GB + lane;
     const bool job_ok = job < a.n_jobs;
     const float *xi_grp = a.xi + static_cast<int64_t>(grp) * a.n_pad * XW;
+    if (qv <= 0) {
+        // Only padding queries (n_pad is a multiple of the reference tile, not
+        // of QC): zero partial sums, and no copy is ever issued.
+        if (tid < GB && job_ok) a.partial[static_cast<int64_t>(job) * a.n_qt + qt] = 0.0;
+        return;
+    }
 
-    // Query rows of the CTA into shared memory (zeros for padding queries).
+    // ---------------- set-up: query rows and X values, empty heaps, zero counts
     for (int idx = tid; idx < QC * DSP; idx += S::THREADS) {
         const int m = idx / DSP, d = idx - m * DSP;
         const int64_t qi = q0 + m;
         s_q[idx] = qi < a.n ? a.sh[(qi / kTJ) * kShStage + (qi % kTJ) * DSP + d] : 0.0f;
     }
-    // This lane's job's X value at each of the warp's queries.
-    float xq[QW][DX];
-    bool qv[QW];
-#pragma unroll
-    for (int m = 0; m < QW; ++m) {
-        qv[m] = qw0 + m < a.n;
-#pragma unroll
-        for (int d = 0; d < DX; ++d)
-            xq[m][d] = qv[m] ? xi_grp[(qw0 + m) * XW + lane * DX + d] : 0.0f;
+    for (int idx = tid; idx < QC * DX * 32; idx += S::THREADS) {
+        const int m = idx / (DX * 32), r = idx - m * (DX * 32), d = r >> 5, l = r & 31;
+        const int64_t qi = q0 + m;
+        s_xq[idx] = qi < a.n ? xi_grp[qi * XW + l * DX + d] : 0.0f;
+    }
+    for (int idx = tid; idx < QC * K1 * 32; idx += S::THREADS) s_h[idx] = CUDART_INF_F;
+    if (!EXACT)
+        for (int idx = tid; idx < QC * 32; idx += S::THREADS) s_kth[idx] = CUDART_INF_F;
+    for (int idx = tid; idx < QC * 3 * 32; idx += S::THREADS) s_cnt[idx] = 0;
+    for (int m = tid; m < QC; m += S::THREADS) {
+        s_b[m] = CUDART_INF_F;
+        s_lock[m] = 0;
     }
 
     auto stage_sh = [&](int st) {
@@ -312,9 +345,11 @@ __global__ void __launch_bounds__(KsgShape<DX, DY, DZ, K1, EXACT, QW, NWARPS>::T
     if (tid == 0) {
         for (int st = 0; st < ST; ++st) {
             mbar_init(&s_bar[st], 1);
-            s_done[st] = 0;
             s_last[st] = -1;
+            s_fin[st] = 0;
         }
+        s_next = 0;
+        s_items_a = 0;
         s_abort = 0;
         fence_mbar_init();
     }
@@ -322,253 +357,279 @@ __global__ void __launch_bounds__(KsgShape<DX, DY, DZ, K1, EXACT, QW, NWARPS>::T
     if (tid == 0)
         for (int u = 0; u < ST && u < total; ++u) issue(u);
 
-    // Bounding box of the warp's valid queries: lane d holds dimension d.
-    float qlo = CUDART_INF_F, qhi = -CUDART_INF_F;
-    if (lane < DS) {
-#pragma unroll
-        for (int m = 0; m < QW; ++m)
-            if (qv[m]) {
-                const float v = s_q[(warp * QW + m) * DSP + lane];
-                qlo = fminf(qlo, v);
-                qhi = fmaxf(qhi, v);
-            }
-    }
-
-    // Each warp walks the items on its own; the last warp to finish an item
-    // refills its stage with item u + ST.  No CTA-wide barrier per tile.
     long long wait_cycles = 0;
     const long long t_begin = clock64();
+    auto fail = [&]() {
+        *abort_flag = 1;
+        atomicOr(a.err, kErrTimeout);
+    };
+    // Control decisions that read shared state other warps may change are
+    // taken by lane 0 and broadcast, so the warp never diverges around the
+    // full-mask shuffles and ballots.
+    auto aborting = [&]() { return __shfl_sync(kFull, *abort_flag, 0) != 0; };
+    // Lane 0 waits (bounded) until try() holds, then the warp proceeds with
+    // acquire ordering.  False: timed out or the CTA is aborting.
+    auto warp_wait = [&](auto try_once) {
+        int ok = 1;
+        if (lane == 0) {
+            if (!try_once()) {
+                const long long t0 = global_ns(), c0 = clock64();
+                while (!try_once()) {
+                    if (*abort_flag || global_ns() - t0 > a.timeout_ns) {
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+                wait_cycles += clock64() - c0;
+            }
+            __threadfence_block();
+        }
+        ok = __shfl_sync(kFull, ok, 0);
+        if (!ok && lane == 0) fail();
+        return ok != 0;
+    };
+    // The stage of item u holds its tiles.  The copy of item u is issued only
+    // after item u - ST is finished (so its copy has landed); waiting for the
+    // issue first keeps the parity test from matching a phase two behind.
     auto acquire = [&](int u) {
+        volatile int *last = s_last;
+        if (!warp_wait([&] { return last[u % ST] == u; })) return false;
         const long long t0 = clock64();
         const bool got = mbar_wait_bounded(&s_bar[u % ST], static_cast<uint32_t>((u / ST) & 1),
                                            a.timeout_ns);
         wait_cycles += clock64() - t0;
-        if (!got) {
-            *abort_flag = 1;
-            atomicOr(a.err, kErrTimeout);
-        }
-        return *abort_flag == 0;
+        const bool all = __all_sync(kFull, got);
+        if (!all && lane == 0) fail();
+        return all && !aborting();
     };
-    auto release = [&](int u) {
+
+    unsigned long long scanned_a = 0, scanned_b = 0, events_a = 0, events_b = 0;  // per warp
+
+    // ---------------- pass-A unit: query m against the tile of item u
+    // The k+1 smallest joint distances of every job.  The heaps of a query are
+    // updated under its lock; the set they end with does not depend on the
+    // order of the updates.  The bound only filters candidates: any value at
+    // least the largest job threshold is correct.
+    auto unit_a = [&](int m, int u) {
+        const float *rs = stage_sh(u % ST);
+        const float *rx = stage_x(u % ST);
+        const float *qrow = s_q + m * DSP;
+        float qc[DS];
+#pragma unroll
+        for (int d = 0; d < DS; ++d) qc[d] = qrow[d];
+        // Phase 1 (no lock needed): the query's joint Y/Z distance to the lane's references.
+        float dv[RPL];
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) {
+            const float *row = rs + (k * 32 + lane) * DSP;
+            float dd = fabsf(qc[0] - row[0]);
+#pragma unroll
+            for (int d = 1; d < DS; ++d) dd = fmaxf(dd, fabsf(qc[d] - row[d]));
+            dv[k] = dd;
+        }
+        scanned_a += kTJ;
+        if (!warp_wait([&] { return atomicCAS(&s_lock[m], 0, 1) == 0; })) return false;
+        const float bound = s_b[m];
+        // Compact the references below the bound into the warp's event list
+        // (entry: offset of the reference's X row, Y/Z distance), padded with
+        // +inf sentinels to a multiple of four.
+        float2 *ev = reinterpret_cast<float2 *>(s_ev);
+        const uint32_t lt = (1u << lane) - 1u;
+        int n_ev = 0;
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) {
+            const bool p = dv[k] < bound;
+            const uint32_t b = __ballot_sync(kFull, p);
+            if (p) ev[n_ev + __popc(b & lt)] = make_float2(__int_as_float((k * 32 + lane) * XW), dv[k]);
+            n_ev += __popc(b);
+        }
+        if (lane < 3) ev[n_ev + lane] = make_float2(__int_as_float(0), CUDART_INF_F);
+        __syncwarp();
+        events_a += n_ev;
+        if (n_ev) {
+            // The events, all lanes, one job each, four per iteration; a lane
+            // inserts an event into its job's k+1 smallest when it is below
+            // the job's threshold.
+            float *hq = s_h + m * K1 * 32 + lane;  // slot t: hq[t * 32]
+            float h[K1];
+#pragma unroll
+            for (int t = 0; t < K1; ++t) h[t] = hq[t * 32];
+            float th = EXACT ? h[K1 - 1] : s_kth[m * 32 + lane];
+            float xq[DX];
+#pragma unroll
+            for (int d = 0; d < DX; ++d) xq[d] = s_xq[(m * DX + d) * 32 + lane];
+            const float *rxl = rx + lane * DX;
+            for (int e = 0; e < n_ev; e += 4) {
+                const float4 p01 = s_ev[e / 2], p23 = s_ev[e / 2 + 1];
+                const int o[4] = {__float_as_int(p01.x), __float_as_int(p01.z),
+                                  __float_as_int(p23.x), __float_as_int(p23.z)};
+                const float dyz[4] = {p01.y, p01.w, p23.y, p23.w};
+                float dd[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    float dx = fabsf(xq[0] - rxl[o[i]]);
+#pragma unroll
+                    for (int d = 1; d < DX; ++d) dx = fmaxf(dx, fabsf(xq[d] - rxl[o[i] + d]));
+                    dd[i] = fmaxf(dx, dyz[i]);
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    if (dd[i] < th) {
+                        sorted_insert<K1>(h, dd[i]);
+                        th = EXACT ? h[K1 - 1] : select_kth<K1>(h, a.k);
+                    }
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < K1; ++t) hq[t * 32] = h[t];
+            if (!EXACT) s_kth[m * 32 + lane] = th;
+            const float nb = warp_max(job_ok ? th : -1.0f);
+            if (lane == 0) reinterpret_cast<volatile float *>(s_b)[m] = nb;
+        }
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence_block();
+            atomicExch(&s_lock[m], 0);
+        }
+        return true;
+    };
+
+    // ---------------- pass-B unit: strict-radius counts in the subspaces
+    // Runs once every pass-A item is finished.  The query's bound is then its
+    // final pass-A bound, the largest eps over its jobs.  The counts are
+    // integer sums, added with shared atomics in any order.
+    auto unit_b = [&](int m, int u) {
+        const float *rs = stage_sh(u % ST);
+        const float *rx = stage_x(u % ST);
+        const float e = EXACT ? s_h[(m * K1 + K1 - 1) * 32 + lane] : s_kth[m * 32 + lane];
+        const float bound = s_b[m];
+        const float *qrow = s_q + m * DSP;
+        float qc[DS];
+#pragma unroll
+        for (int d = 0; d < DS; ++d) qc[d] = qrow[d];
+        // Compact the references whose Z distance is below the bound into the
+        // warp's event list (entry: X row offset, Z distance, Y/Z distance),
+        // padded with +inf sentinels to a multiple of four.
+        const uint32_t lt = (1u << lane) - 1u;
+        int n_ev = 0;
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) {
+            const float *row = rs + (k * 32 + lane) * DSP;
+            float dz = fabsf(qc[0] - row[0]);
+#pragma unroll
+            for (int d = 1; d < DZ; ++d) dz = fmaxf(dz, fabsf(qc[d] - row[d]));
+            float dyz = dz;
+#pragma unroll
+            for (int d = DZ; d < DS; ++d) dyz = fmaxf(dyz, fabsf(qc[d] - row[d]));
+            const bool p = dz < bound;
+            const uint32_t b = __ballot_sync(kFull, p);
+            if (p)
+                s_ev[n_ev + __popc(b & lt)] =
+                    make_float4(__int_as_float((k * 32 + lane) * XW), dz, dyz, 0.0f);
+            n_ev += __popc(b);
+        }
+        scanned_b += kTJ;
+        events_b += n_ev;
+        if (n_ev == 0) return true;
+        if (lane < 3)
+            s_ev[n_ev + lane] = make_float4(__int_as_float(0), CUDART_INF_F, CUDART_INF_F, 0.0f);
+        __syncwarp();
+        float xq[DX];
+#pragma unroll
+        for (int d = 0; d < DX; ++d) xq[d] = s_xq[(m * DX + d) * 32 + lane];
+        const float *rxl = rx + lane * DX;
+        int cz = 0, cyz = 0, cxz = 0;
+        for (int ei = 0; ei < n_ev; ei += 4) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float4 v = s_ev[ei + i];
+                const int o = __float_as_int(v.x);
+                float dx = fabsf(xq[0] - rxl[o]);
+#pragma unroll
+                for (int d = 1; d < DX; ++d) dx = fmaxf(dx, fabsf(xq[d] - rxl[o + d]));
+                // max(dX, dZ) < e  <=>  dX < e and dZ < e
+                const bool pz = v.y < e;
+                cz += pz ? 1 : 0;
+                cyz += v.z < e ? 1 : 0;
+                cxz += (pz && dx < e) ? 1 : 0;
+            }
+        }
+        int *c = s_cnt + m * 3 * 32 + lane;
+        if (cz) atomicAdd(c, cz);
+        if (cyz) atomicAdd(c + 32, cyz);
+        if (cxz) atomicAdd(c + 64, cxz);
+        __syncwarp();
+        return true;
+    };
+
+    // ---------------- work loop: query groups taken dynamically
+    // Unit t is query group t % ng of item t / ng (groups of QG valid
+    // queries), so units are taken in item order and any warp takes the next
+    // one.  Every unit waits for its item's tiles before it counts as
+    // finished, so no finish is counted against the stage's previous item.
+    // The group's lanes test its queries against the tile's box in parallel;
+    // the warp then runs the queries that pass one by one.  The unit that
+    // finishes an item refills the item's stage with item u + ST.
+    const int ng = (qv + QG - 1) / QG;
+    const int n_units = total * ng;
+    int cur = -1;        // item whose stage this warp has acquired
+    bool b_ready = false;
+    while (true) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(&s_next, 1);
+        t = __shfl_sync(kFull, t, 0);
+        if (t >= n_units) break;
+        const int u = t / ng, m0 = (t - u * ng) * QG;
+        bool ok = true;
+        if (u != cur) {
+            ok = acquire(u);
+            cur = u;
+        }
+        const bool pass_b = u >= n_tiles;
+        if (ok && pass_b && !b_ready) {
+            volatile int *items_a = &s_items_a;
+            ok = b_ready = warp_wait([&] { return *items_a == n_tiles; });
+        }
+        if (ok) {
+            const float *rs = stage_sh(u % ST);
+            const int mq = m0 + lane;
+            bool live = false;
+            if (lane < QG && mq < qv) {
+                // A bound read without the lock is never below the query's
+                // current bound (bounds only shrink), so a skip is safe.
+                const float bnd = reinterpret_cast<volatile float *>(s_b)[mq];
+                const float *qrow = s_q + mq * DSP;
+                float qc[DS];
+#pragma unroll
+                for (int d = 0; d < DS; ++d) qc[d] = qrow[d];
+                const float gap =
+                    pass_b ? point_gap<DZ, DSP>(rs, qc) : point_gap<DS, DSP>(rs, qc);
+                live = gap < bnd;
+            }
+            uint32_t todo = __ballot_sync(kFull, live);
+            while (todo && ok) {
+                const int m = m0 + __ffs(todo) - 1;
+                todo &= todo - 1;
+                ok = pass_b ? unit_b(m, u) : unit_a(m, u);
+            }
+        }
         __syncwarp();
         if (lane == 0) {
             __threadfence_block();
             const int st = u % ST;
-            if (atomicAdd(&s_done[st], 1) == NW - 1) {
-                s_done[st] = 0;
+            if (atomicAdd(&s_fin[st], 1) == ng - 1) {
+                s_fin[st] = 0;
+                if (u < n_tiles) atomicAdd(&s_items_a, 1);
                 if (u + ST < total && *abort_flag == 0) {
+                    __threadfence_block();
                     fence_proxy_async_smem();
                     issue(u + ST);
                 }
             }
         }
         __syncwarp();
-    };
-
-    unsigned long long scanned_a = 0, scanned_b = 0, events_a = 0, events_b = 0;  // per warp
-
-    int u = 0;
-    bool ok = true;
-    float e[QW];
-    {
-        // ---------------- pass A: per (query, job) the k+1 smallest joint distances
-        float h[QW][K1];
-        float kth[QW];
-        float b[QW];  // per query: largest threshold over the valid jobs (warp-uniform)
-#pragma unroll
-        for (int m = 0; m < QW; ++m) {
-#pragma unroll
-            for (int t = 0; t < K1; ++t) h[m][t] = CUDART_INF_F;
-            kth[m] = CUDART_INF_F;
-            b[m] = qv[m] ? CUDART_INF_F : -1.0f;
-        }
-        for (; u < n_tiles; ++u) {
-            if (!(ok = acquire(u))) break;
-            const float *rs = stage_sh(u % ST);
-            const float *rx = stage_x(u % ST);
-            float bw = b[0];
-#pragma unroll
-            for (int m = 1; m < QW; ++m) bw = fmaxf(bw, b[m]);
-            if (box_gap<DS, DSP>(rs, qlo, qhi, lane) < bw) {
-                float r[RR][RD];
-                if (S::ROWREG) {
-#pragma unroll
-                    for (int k = 0; k < RPL; ++k)
-#pragma unroll
-                        for (int t = 0; t < DSP / 4; ++t) {
-                            const float4 v =
-                                reinterpret_cast<const float4 *>(rs + (k * 32 + lane) * DSP)[t];
-                            r[RI(k)][RJ(4 * t + 0)] = v.x;
-                            r[RI(k)][RJ(4 * t + 1)] = v.y;
-                            r[RI(k)][RJ(4 * t + 2)] = v.z;
-                            r[RI(k)][RJ(4 * t + 3)] = v.w;
-                        }
-                }
-#pragma unroll
-                for (int m = 0; m < QW; ++m) {
-                    if (!qv[m]) continue;
-                    const float *qrow = s_q + (warp * QW + m) * DSP;
-                    float qc[DS];
-#pragma unroll
-                    for (int d = 0; d < DS; ++d) qc[d] = qrow[d];
-                    if (point_gap<DS, DSP>(rs, qc) >= b[m]) continue;
-                    // Phase 1: the query's distance to the lane's references.
-                    float dv[RPL];
-                    uint32_t ball[RPL];
-#pragma unroll
-                    for (int k = 0; k < RPL; ++k) {
-                        float dd = 0.0f;
-#pragma unroll
-                        for (int d = 0; d < DS; ++d) {
-                            const float rv = S::ROWREG ? r[RI(k)][RJ(d)]
-                                                       : rs[(k * 32 + lane) * DSP + d];
-                            dd = d == 0 ? fabsf(qc[0] - rv) : fmaxf(dd, fabsf(qc[d] - rv));
-                        }
-                        dv[k] = dd;
-                        ball[k] = __ballot_sync(0xffffffffu, dd < b[m]);
-                    }
-                    scanned_a += kTJ;
-                    // Phase 2: the passing references, all lanes, one job each; two
-                    // references per iteration so their loads overlap.
-                    bool any = false;
-#pragma unroll
-                    for (int k = 0; k < RPL; ++k) {
-                        uint32_t msk = ball[k];
-                        events_a += __popc(msk);
-                        any |= msk != 0;
-                        while (msk) {
-                            const int l0 = __ffs(msk) - 1;
-                            msk &= msk - 1;
-                            const bool two = msk != 0;
-                            const int l1 = two ? __ffs(msk) - 1 : l0;
-                            msk &= msk - 1;
-                            const float dyz0 = __shfl_sync(0xffffffffu, dv[k], l0);
-                            const float dyz1 = __shfl_sync(0xffffffffu, dv[k], l1);
-                            const float *xr0 = rx + (k * 32 + l0) * XW + lane * DX;
-                            const float *xr1 = rx + (k * 32 + l1) * XW + lane * DX;
-                            float dx0 = fabsf(xq[m][0] - xr0[0]), dx1 = fabsf(xq[m][0] - xr1[0]);
-#pragma unroll
-                            for (int d = 1; d < DX; ++d) {
-                                dx0 = fmaxf(dx0, fabsf(xq[m][d] - xr0[d]));
-                                dx1 = fmaxf(dx1, fabsf(xq[m][d] - xr1[d]));
-                            }
-                            const float dd0 = fmaxf(dx0, dyz0), dd1 = fmaxf(dx1, dyz1);
-                            if (dd0 < (EXACT ? h[m][K1 - 1] : kth[m])) {
-                                sorted_insert<K1>(h[m], dd0);
-                                if (!EXACT) kth[m] = select_kth<K1>(h[m], a.k);
-                            }
-                            if (two && dd1 < (EXACT ? h[m][K1 - 1] : kth[m])) {
-                                sorted_insert<K1>(h[m], dd1);
-                                if (!EXACT) kth[m] = select_kth<K1>(h[m], a.k);
-                            }
-                        }
-                    }
-                    if (any) b[m] = warp_max(job_ok ? (EXACT ? h[m][K1 - 1] : kth[m]) : -1.0f);
-                }
-            }
-            release(u);
-        }
-#pragma unroll
-        for (int m = 0; m < QW; ++m) e[m] = EXACT ? h[m][K1 - 1] : kth[m];
-    }
-
-    int cxz[QW], cyz[QW], cz[QW];
-#pragma unroll
-    for (int m = 0; m < QW; ++m) {
-        cxz[m] = 0;
-        cyz[m] = 0;
-        cz[m] = 0;
-    }
-    if (ok) {
-        // ---------------- pass B: strict-radius counts in the subspaces
-        float b[QW];
-        float bw = -1.0f;
-#pragma unroll
-        for (int m = 0; m < QW; ++m) {
-            b[m] = qv[m] ? warp_max(job_ok ? e[m] : -1.0f) : -1.0f;
-            bw = fmaxf(bw, b[m]);
-        }
-        for (; u < total; ++u) {
-            if (!(ok = acquire(u))) break;
-            const float *rs = stage_sh(u % ST);
-            const float *rx = stage_x(u % ST);
-            if (box_gap<DZ, DSP>(rs, qlo, qhi, lane) < bw) {
-                float r[RR][RD];
-                if (S::ROWREG) {
-#pragma unroll
-                    for (int k = 0; k < RPL; ++k)
-#pragma unroll
-                        for (int t = 0; t < DSP / 4; ++t) {
-                            const float4 v =
-                                reinterpret_cast<const float4 *>(rs + (k * 32 + lane) * DSP)[t];
-                            r[RI(k)][RJ(4 * t + 0)] = v.x;
-                            r[RI(k)][RJ(4 * t + 1)] = v.y;
-                            r[RI(k)][RJ(4 * t + 2)] = v.z;
-                            r[RI(k)][RJ(4 * t + 3)] = v.w;
-                        }
-                }
-#pragma unroll
-                for (int m = 0; m < QW; ++m) {
-                    if (!qv[m]) continue;
-                    const float *qrow = s_q + (warp * QW + m) * DSP;
-                    float qc[DS];
-#pragma unroll
-                    for (int d = 0; d < DS; ++d) qc[d] = qrow[d];
-                    if (point_gap<DZ, DSP>(rs, qc) >= b[m]) continue;
-                    float dzv[RPL], dyzv[RPL];
-                    uint32_t ball[RPL];
-#pragma unroll
-                    for (int k = 0; k < RPL; ++k) {
-                        float dz = 0.0f, dy = 0.0f;
-#pragma unroll
-                        for (int d = 0; d < DS; ++d) {
-                            const float rv = S::ROWREG ? r[RI(k)][RJ(d)]
-                                                       : rs[(k * 32 + lane) * DSP + d];
-                            const float ad = fabsf(qc[d] - rv);
-                            if (d < DZ)
-                                dz = d == 0 ? ad : fmaxf(dz, ad);
-                            else
-                                dy = d == DZ ? ad : fmaxf(dy, ad);
-                        }
-                        dzv[k] = dz;
-                        dyzv[k] = fmaxf(dz, dy);
-                        ball[k] = __ballot_sync(0xffffffffu, dz < b[m]);
-                    }
-                    scanned_b += kTJ;
-#pragma unroll
-                    for (int k = 0; k < RPL; ++k) {
-                        uint32_t msk = ball[k];
-                        events_b += __popc(msk);
-                        while (msk) {
-                            const int l0 = __ffs(msk) - 1;
-                            msk &= msk - 1;
-                            const bool two = msk != 0;
-                            const int l1 = two ? __ffs(msk) - 1 : l0;
-                            msk &= msk - 1;
-                            const float dz0 = __shfl_sync(0xffffffffu, dzv[k], l0);
-                            const float dz1 = __shfl_sync(0xffffffffu, dzv[k], l1);
-                            const float dyz0 = __shfl_sync(0xffffffffu, dyzv[k], l0);
-                            const float dyz1 = __shfl_sync(0xffffffffu, dyzv[k], l1);
-                            const float *xr0 = rx + (k * 32 + l0) * XW + lane * DX;
-                            const float *xr1 = rx + (k * 32 + l1) * XW + lane * DX;
-                            float dx0 = fabsf(xq[m][0] - xr0[0]), dx1 = fabsf(xq[m][0] - xr1[0]);
-#pragma unroll
-                            for (int d = 1; d < DX; ++d) {
-                                dx0 = fmaxf(dx0, fabsf(xq[m][d] - xr0[d]));
-                                dx1 = fmaxf(dx1, fabsf(xq[m][d] - xr1[d]));
-                            }
-                            // max(dX, dZ) < e  <=>  dX < e and dZ < e
-                            const float em = e[m];
-                            const bool pz0 = dz0 < em, pz1 = two && dz1 < em;
-                            cz[m] += (pz0 ? 1 : 0) + (pz1 ? 1 : 0);
-                            cyz[m] += (dyz0 < em ? 1 : 0) + ((two && dyz1 < em) ? 1 : 0);
-                            cxz[m] += ((pz0 && dx0 < em) ? 1 : 0) + ((pz1 && dx1 < em) ? 1 : 0);
-                        }
-                    }
-                }
-            }
-            release(u);
-        }
+        if (!ok) break;
     }
 
     __syncthreads();
@@ -584,22 +645,23 @@ __global__ void __launch_bounds__(KsgShape<DX, DY, DZ, K1, EXACT, QW, NWARPS>::T
         return;
     }
 
-    // ---------------- epilogue: self pair, outputs, digamma terms
+    // ---------------- epilogue: self pair, outputs, digamma terms (fixed order)
     double tsum = 0.0;
-#pragma unroll
-    for (int m = 0; m < QW; ++m) {
-        if (!qv[m] || !job_ok) continue;
-        const int self = e[m] > 0.0f ? 1 : 0;
-        const int nxz = cxz[m] - self, nyz = cyz[m] - self, nz = cz[m] - self;
+    for (int m = warp; m < QC; m += NW) {
+        const int64_t qi = q0 + m;
+        if (qi >= a.n || !job_ok) continue;
+        const float e = EXACT ? s_h[(m * K1 + K1 - 1) * 32 + lane] : s_kth[m * 32 + lane];
+        const int *c = s_cnt + m * 3 * 32 + lane;
+        const int self = e > 0.0f ? 1 : 0;
+        const int nz = c[0] - self, nyz = c[32] - self, nxz = c[64] - self;
         tsum += a.psi[nz + 1] - a.psi[nxz + 1] - a.psi[nyz + 1];
-        const int64_t qi = qw0 + m;
         const int64_t orig = a.order ? static_cast<int64_t>(a.order[qi]) : qi;
-        if (a.eps_out) a.eps_out[static_cast<int64_t>(job) * a.n + orig] = e[m];
+        if (a.eps_out) a.eps_out[static_cast<int64_t>(job) * a.n + orig] = e;
         if (a.cnt_out) {
-            int32_t *c = a.cnt_out + static_cast<int64_t>(job) * 3 * a.n;
-            c[orig] = nxz;
-            c[a.n + orig] = nyz;
-            c[2 * a.n + orig] = nz;
+            int32_t *co = a.cnt_out + static_cast<int64_t>(job) * 3 * a.n;
+            co[orig] = nxz;
+            co[a.n + orig] = nyz;
+            co[2 * a.n + orig] = nz;
         }
     }
     s_red[warp][lane] = tsum;
@@ -620,11 +682,11 @@ __global__ void __launch_bounds__(KsgShape<DX, DY, DZ, K1, EXACT, QW, NWARPS>::T
     }
 }
 
-template <int DX, int DY, int DZ, int K1, bool EXACT, int QW, int NWARPS>
+template <int DX, int DY, int DZ, int K1, bool EXACT, int QC, int NWARPS>
 cudaError_t launch_ksg(const KsgLaunch &a, int n_groups, cudaStream_t stream)
 {
-    using S = KsgShape<DX, DY, DZ, K1, EXACT, QW, NWARPS>;
-    auto kern = ksg_fused_kernel<DX, DY, DZ, K1, EXACT, QW, NWARPS>;
+    using S = KsgShape<DX, DY, DZ, K1, EXACT, QC, NWARPS>;
+    auto kern = ksg_fused_kernel<DX, DY, DZ, K1, EXACT, QC, NWARPS>;
     static bool attr_set = false;  // per process; the attribute is per function
     if (!attr_set) {
         cudaError_t e =
@@ -638,12 +700,12 @@ cudaError_t launch_ksg(const KsgLaunch &a, int n_groups, cudaStream_t stream)
     return cudaGetLastError();
 }
 
-template <int DX, int DY, int DZ, int K1, bool EXACT, int QW, int NWARPS>
+template <int DX, int DY, int DZ, int K1, bool EXACT, int QC, int NWARPS>
 KsgVariant make_variant()
 {
-    using S = KsgShape<DX, DY, DZ, K1, EXACT, QW, NWARPS>;
+    using S = KsgShape<DX, DY, DZ, K1, EXACT, QC, NWARPS>;
     return KsgVariant{DX, DY, DZ, K1, EXACT ? 1 : 0, S::GB, S::DSP, S::QC,
-                      &launch_ksg<DX, DY, DZ, K1, EXACT, QW, NWARPS>};
+                      &launch_ksg<DX, DY, DZ, K1, EXACT, QC, NWARPS>};
 }
 
 }  // namespace idtx
