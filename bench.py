@@ -31,9 +31,9 @@ METRIC = "KSG CMI estimates/s incl. surrogates (N=1e4,k=4); batched/screened vs 
 N_SMS = 152
 # DRAM bytes (read + write) of one fused-kernel launch of the 200-surrogate step,
 # from the ncu capture summarised in profiles/ksg_fused_kernel_greedy_step_small.md
-# (15-surrogate case, 31.37 MB, scaled by job groups 296/24).  Set to None when the
+# (15-surrogate case, 31.68 MB, scaled by job groups 296/24).  Set to None when the
 # kernel changes until it is captured again.
-FUSED_TRAFFIC_BYTES = 386.9e6
+FUSED_TRAFFIC_BYTES = 390.7e6
 LANES_PER_SM = 128  # 4 sub-partitions x 32 lanes: one warp instruction per clock each
 
 WORKLOAD = dict(n_proc=10, order=5, T=10000, n_past=3, min_lag=1, max_lag=5, k=4, n_surr=200,
@@ -298,9 +298,9 @@ def run_ours(args):
     achieved = st["fused_lane_ops"] / (st["fused_ms"] / 1e3) / 1e12 if st["fused_ms"] else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                 "frac": (achieved / peak) if achieved else None,
-                "traffic": FUSED_TRAFFIC_BYTES if w["n_surr"] == 200 else None,
+                "traffic": FUSED_TRAFFIC_BYTES if w["n_surr"] == 200 and FUSED_TRAFFIC_BYTES else None,
                 "traffic_unit": "bytes per launch (ncu, scaled from the 15-surrogate case)",
-                "kernel": "ksg_fused_kernel<DX=1,DY=1,DZ=3,K1=5,exact,QW=2,NW=16>",
+                "kernel": "ksg_fused_kernel<DX=1,DY=1,DZ=3,K1=5,exact,QC=64,NW=8>",
                 "peak_basis": f"{N_SMS} SMs x {LANES_PER_SM} lanes x median SM clock "
                               f"{sm_mhz:.0f} MHz under load (issue-slot peak)",
                 "fused_share_of_step": st["fused_ms"] / ms if ms else None,

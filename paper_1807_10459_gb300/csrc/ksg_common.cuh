@@ -26,8 +26,11 @@
 
 namespace idtx {
 
-constexpr int kTQ = 128;  // sample padding granularity (= kTJ)
-constexpr int kTJ = 128;  // reference samples per staged tile
+#ifndef IDTX_TILE
+#define IDTX_TILE 128
+#endif
+constexpr int kTJ = IDTX_TILE;  // reference samples per staged tile (a multiple of 32)
+constexpr int kTQ = kTJ;        // sample padding granularity
 
 // Device error word bits.
 enum : int {

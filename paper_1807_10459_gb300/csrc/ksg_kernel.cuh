@@ -56,19 +56,19 @@
 
 // Launch-shape knobs (compile-time; the defaults are the tuned values).
 #ifndef IDTX_STAGE_BUDGET_KB
-#define IDTX_STAGE_BUDGET_KB 60
+#define IDTX_STAGE_BUDGET_KB 40
 #endif
 #ifndef IDTX_MAX_STAGES
 #define IDTX_MAX_STAGES 4
 #endif
 #ifndef IDTX_FAST_QC
-#define IDTX_FAST_QC 32
+#define IDTX_FAST_QC 64
 #endif
 #ifndef IDTX_FAST_NW
 #define IDTX_FAST_NW 8
 #endif
 #ifndef IDTX_QUERY_GROUP
-#define IDTX_QUERY_GROUP 4
+#define IDTX_QUERY_GROUP 8
 #endif
 
 namespace idtx {
@@ -240,14 +240,14 @@ struct KsgShape {
     static constexpr int STAGES_RAW = (IDTX_STAGE_BUDGET_KB * 1024) / STAGE_BYTES;
     static constexpr int STAGES =
         STAGES_RAW < 2 ? 2 : (STAGES_RAW > IDTX_MAX_STAGES ? IDTX_MAX_STAGES : STAGES_RAW);
-    // dynamic shared memory: stages | barriers | query rows | heaps | k-th
-    // values (!EXACT) | counts | query X values | per-warp event lists
+    // dynamic shared memory: stages | barriers | query rows | heaps (pass B:
+    // slots 0-2 hold the counts) | k-th values (!EXACT) | query X values |
+    // per-warp event lists
     static constexpr size_t BAR_OFF = (size_t)STAGES * STAGE_BYTES;
     static constexpr size_t Q_OFF = (BAR_OFF + STAGES * sizeof(uint64_t) + 15) & ~size_t(15);
     static constexpr size_t H_OFF = Q_OFF + (size_t)QC * DSP * sizeof(float);
     static constexpr size_t KTH_OFF = H_OFF + (size_t)QC * K1 * 32 * sizeof(float);
-    static constexpr size_t CNT_OFF = KTH_OFF + (EXACT ? 0 : (size_t)QC * 32 * sizeof(float));
-    static constexpr size_t XQ_OFF = CNT_OFF + (size_t)QC * 3 * 32 * sizeof(int);
+    static constexpr size_t XQ_OFF = KTH_OFF + (EXACT ? 0 : (size_t)QC * 32 * sizeof(float));
     static constexpr size_t EV_OFF = XQ_OFF + (size_t)QC * DX * 32 * sizeof(float);
     static constexpr int EV_CAP = kTJ + 4;  // a tile's references + sentinel padding
     static constexpr size_t SMEM = EV_OFF + (size_t)NW * EV_CAP * sizeof(float4);
@@ -273,12 +273,12 @@ __global__ void __launch_bounds__(KsgShape<DX, DY, DZ, K1, EXACT, QCTA, NWARPS>:
     float *s_q = reinterpret_cast<float *>(smem_raw + S::Q_OFF);      // [QC][DSP]
     float *s_h = reinterpret_cast<float *>(smem_raw + S::H_OFF);      // [QC][K1][32]
     float *s_kth = reinterpret_cast<float *>(smem_raw + S::KTH_OFF);  // [QC][32]
-    int *s_cnt = reinterpret_cast<int *>(smem_raw + S::CNT_OFF);      // [QC][3][32]
     float *s_xq = reinterpret_cast<float *>(smem_raw + S::XQ_OFF);    // [QC][DX][32]
     __shared__ float s_b[QC];    // per query: pass-A bound (largest job threshold)
     __shared__ int s_lock[QC];   // per query: owner of its heaps (pass A)
     __shared__ int s_next;       // next unit to take
     __shared__ int s_items_a;    // pass-A items finished
+    __shared__ int s_open_b;     // pass B may start: pass A done, counts zeroed
     __shared__ int s_fin[ST];    // units finished of the stage's current item
     __shared__ int s_abort;
     __shared__ int s_last[ST];   // item last issued into the stage
@@ -320,7 +320,6 @@ __global__ void __launch_bounds__(KsgShape<DX, DY, DZ, K1, EXACT, QCTA, NWARPS>:
     for (int idx = tid; idx < QC * K1 * 32; idx += S::THREADS) s_h[idx] = CUDART_INF_F;
     if (!EXACT)
         for (int idx = tid; idx < QC * 32; idx += S::THREADS) s_kth[idx] = CUDART_INF_F;
-    for (int idx = tid; idx < QC * 3 * 32; idx += S::THREADS) s_cnt[idx] = 0;
     for (int m = tid; m < QC; m += S::THREADS) {
         s_b[m] = CUDART_INF_F;
         s_lock[m] = 0;
@@ -350,6 +349,7 @@ __global__ void __launch_bounds__(KsgShape<DX, DY, DZ, K1, EXACT, QCTA, NWARPS>:
         }
         s_next = 0;
         s_items_a = 0;
+        s_open_b = 0;
         s_abort = 0;
         fence_mbar_init();
     }
@@ -497,8 +497,9 @@ __global__ void __launch_bounds__(KsgShape<DX, DY, DZ, K1, EXACT, QCTA, NWARPS>:
 
     // ---------------- pass-B unit: strict-radius counts in the subspaces
     // Runs once every pass-A item is finished.  The query's bound is then its
-    // final pass-A bound, the largest eps over its jobs.  The counts are
-    // integer sums, added with shared atomics in any order.
+    // final pass-A bound, the largest eps over its jobs.  The counts live in
+    // heap slots 0-2 (n_z, n_yz, n_xz; slot K1-1 keeps eps) and are integer
+    // sums, added with shared atomics in any order.
     auto unit_b = [&](int m, int u) {
         const float *rs = stage_sh(u % ST);
         const float *rx = stage_x(u % ST);
@@ -555,7 +556,7 @@ __global__ void __launch_bounds__(KsgShape<DX, DY, DZ, K1, EXACT, QCTA, NWARPS>:
                 cxz += (pz && dx < e) ? 1 : 0;
             }
         }
-        int *c = s_cnt + m * 3 * 32 + lane;
+        int *c = reinterpret_cast<int *>(s_h) + m * K1 * 32 + lane;
         if (cz) atomicAdd(c, cz);
         if (cyz) atomicAdd(c + 32, cyz);
         if (cxz) atomicAdd(c + 64, cxz);
@@ -564,15 +565,15 @@ __global__ void __launch_bounds__(KsgShape<DX, DY, DZ, K1, EXACT, QCTA, NWARPS>:
     };
 
     // ---------------- work loop: query groups taken dynamically
-    // Unit t is query group t % ng of item t / ng (groups of QG valid
-    // queries), so units are taken in item order and any warp takes the next
-    // one.  Every unit waits for its item's tiles before it counts as
+    // Unit t is query group t % NG of item t / NG, so units are taken in item
+    // order and any warp takes the next one.  Every unit (one made only of
+    // padding queries too) waits for its item's tiles before it counts as
     // finished, so no finish is counted against the stage's previous item.
     // The group's lanes test its queries against the tile's box in parallel;
     // the warp then runs the queries that pass one by one.  The unit that
     // finishes an item refills the item's stage with item u + ST.
-    const int ng = (qv + QG - 1) / QG;
-    const int n_units = total * ng;
+    constexpr int NG = QC / QG;
+    const int n_units = total * NG;
     int cur = -1;        // item whose stage this warp has acquired
     bool b_ready = false;
     while (true) {
@@ -580,7 +581,7 @@ __global__ void __launch_bounds__(KsgShape<DX, DY, DZ, K1, EXACT, QCTA, NWARPS>:
         if (lane == 0) t = atomicAdd(&s_next, 1);
         t = __shfl_sync(kFull, t, 0);
         if (t >= n_units) break;
-        const int u = t / ng, m0 = (t - u * ng) * QG;
+        const int u = t / NG, m0 = (t - u * NG) * QG;
         bool ok = true;
         if (u != cur) {
             ok = acquire(u);
@@ -588,8 +589,8 @@ __global__ void __launch_bounds__(KsgShape<DX, DY, DZ, K1, EXACT, QCTA, NWARPS>:
         }
         const bool pass_b = u >= n_tiles;
         if (ok && pass_b && !b_ready) {
-            volatile int *items_a = &s_items_a;
-            ok = b_ready = warp_wait([&] { return *items_a == n_tiles; });
+            volatile int *open_b = &s_open_b;
+            ok = b_ready = warp_wait([&] { return *open_b != 0; });
         }
         if (ok) {
             const float *rs = stage_sh(u % ST);
@@ -615,17 +616,31 @@ __global__ void __launch_bounds__(KsgShape<DX, DY, DZ, K1, EXACT, QCTA, NWARPS>:
             }
         }
         __syncwarp();
+        int last_a = 0;  // this unit finished the last pass-A item
         if (lane == 0) {
             __threadfence_block();
             const int st = u % ST;
-            if (atomicAdd(&s_fin[st], 1) == ng - 1) {
+            if (atomicAdd(&s_fin[st], 1) == NG - 1) {
                 s_fin[st] = 0;
-                if (u < n_tiles) atomicAdd(&s_items_a, 1);
+                if (u < n_tiles) last_a = atomicAdd(&s_items_a, 1) == n_tiles - 1;
                 if (u + ST < total && *abort_flag == 0) {
                     __threadfence_block();
                     fence_proxy_async_smem();
                     issue(u + ST);
                 }
+            }
+        }
+        if (__shfl_sync(kFull, last_a, 0)) {
+            // Every heap is final: zero the count slots, then open pass B.
+            int *hi = reinterpret_cast<int *>(s_h);
+            for (int idx = lane; idx < qv * 3 * 32; idx += 32) {
+                const int m = idx / 96, r = idx - m * 96;
+                hi[m * K1 * 32 + r] = 0;
+            }
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence_block();
+                *reinterpret_cast<volatile int *>(&s_open_b) = 1;
             }
         }
         __syncwarp();
@@ -651,7 +666,7 @@ __global__ void __launch_bounds__(KsgShape<DX, DY, DZ, K1, EXACT, QCTA, NWARPS>:
         const int64_t qi = q0 + m;
         if (qi >= a.n || !job_ok) continue;
         const float e = EXACT ? s_h[(m * K1 + K1 - 1) * 32 + lane] : s_kth[m * 32 + lane];
-        const int *c = s_cnt + m * 3 * 32 + lane;
+        const int *c = reinterpret_cast<const int *>(s_h) + m * K1 * 32 + lane;
         const int self = e > 0.0f ? 1 : 0;
         const int nz = c[0] - self, nyz = c[32] - self, nxz = c[64] - self;
         tsum += a.psi[nz + 1] - a.psi[nxz + 1] - a.psi[nyz + 1];
