@@ -393,15 +393,84 @@ def run_var50(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batch64(args):
+    """The uneven batch: 64 problems, N log-uniform in [2000, 50000], dx, dy in
+    {1, 2}, dz in 1..8, 500 surrogates each (32 064 estimates) through
+    idtx_cmi_batch (one persistent fused launch per kernel variant).  Plain
+    mode (one launch per estimate) is timed on two estimates of every problem
+    and scaled to the batch's 501 per problem."""
+    import torch
+    import paper_1807_10459_gb300 as idtx
+    from paper_1807_10459_gb300 import synth
+    probs = synth.batch_problems()
+    dev = [dict(x=torch.from_numpy(p.x).cuda(), y=torch.from_numpy(p.y).cuda(),
+                z=torch.from_numpy(p.z).cuda(), n_surr=p.n_surr, seed=p.seed) for p in probs]
+    n_est = sum(1 + p.n_surr for p in probs)
+    ctx = idtx.Context(0)
+    for _ in range(max(args.warmup, 1)):
+        idtx.cmi_batch(dev, k=4, ctx=ctx)
+    torch.cuda.synchronize()
+    ctx.set_profiling(True)
+    ctx.reset_stats()
+    sampler = ClockSampler(0)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        idtx.cmi_batch(dev, k=4, ctx=ctx)
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    st = ctx.stats()
+    ctx.set_profiling(False)
+    # the same estimates as 64 separate calls (one fused launch per problem)
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record()
+    for p, d in zip(probs, dev):
+        idtx.cmi_ksg(d["x"], d["y"], d["z"], k=4, n_surr=p.n_surr, seed=p.seed, ctx=ctx)
+    s1.record()
+    torch.cuda.synchronize()
+    ms_sep = s0.elapsed_time(s1)
+    # plain mode: two estimates per problem, one launch each
+    t_plain = 0.0
+    for p, d in zip(probs, dev):
+        for _ in range(2):   # the second pass is timed (the first builds buffers)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            idtx.cmi_ksg(d["x"], d["y"], d["z"], k=4, n_surr=1, seed=p.seed,
+                         mode=idtx.MODE_PLAIN, ctx=ctx)
+            b.record()
+            torch.cuda.synchronize()
+        t_plain += a.elapsed_time(b) / 2.0 * (1 + p.n_surr) / 1e3
+    line = {"metric": "KSG CMI estimates/s, 64-problem uneven batch (N 2e3-5e4, k=4, "
+                      "500 surrogates)", "value": n_est / (ms / 1e3), "unit": "estimates/s",
+            "n_gpus": 1, "steps": args.steps, "ms_per_call": ms, "estimates_per_call": n_est,
+            "fused_launches_per_call": st["fused_launches"] / args.steps,
+            "fused_share_of_call": st["fused_ms"] / (ms * args.steps) if ms else None,
+            "modes": {"batched": n_est / (ms / 1e3),
+                      "separate_calls": n_est / (ms_sep / 1e3),
+                      "plain_estimated": n_est / t_plain,
+                      "batched_over_plain": t_plain / (ms / 1e3),
+                      "plain_sample": "2 estimates of every problem, one launch each, "
+                                      "scaled to 501 per problem"},
+            "clocks": clocks, "dtype": "f32", "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="var10-step", choices=["var10-step", "var50-greedy"],
+    ap.add_argument("--workload", default="var10-step",
+                    choices=["var10-step", "var50-greedy", "batch64"],
                     help="var10-step: the benchmarked greedy step (default); var50-greedy: "
-                         "full inference on a 50-node VAR(3), exact vs screened")
+                         "full inference on a 50-node VAR(3), exact vs screened; batch64: "
+                         "the 64-problem uneven batch")
     ap.add_argument("--n-surr", type=int, default=WORKLOAD["n_surr"],
                     help="surrogates per candidate (200 is the benchmarked workload; smaller "
                          "values give a small case for profiling)")
@@ -409,6 +478,9 @@ def main():
     WORKLOAD["n_surr"] = args.n_surr
     if args.workload == "var50-greedy":
         run_var50(args)
+        return
+    if args.workload == "batch64":
+        run_batch64(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -66,6 +66,20 @@ struct KsgLaunch {
 
 typedef cudaError_t (*KsgLaunchFn)(const KsgLaunch &, int n_groups, cudaStream_t);
 
+// Several problems of one kernel variant in one persistent launch.  Task t
+// (0 <= t < n_tasks) belongs to the problem p with start[p] <= t < start[p+1];
+// its local index l = t - start[p] is query tile l % n_qt of job group
+// l / n_qt.  CTAs take tasks in order from *next (zero before the launch).
+struct KsgTable {
+    const KsgLaunch *probs;  // device [n_probs]
+    const int64_t *start;    // device [n_probs + 1]
+    int *next;               // device counter
+    int n_probs;
+    int64_t n_tasks;
+};
+
+typedef cudaError_t (*KsgTableFn)(const KsgTable &, cudaStream_t);
+
 // One compiled specialisation of the fused estimator kernel.
 struct KsgVariant {
     int dx, dy, dz;   // bucket dimensions (inputs are zero-padded up to them)
@@ -75,6 +89,7 @@ struct KsgVariant {
     int dsp;          // floats per row of sh
     int qc;           // queries per CTA
     KsgLaunchFn fn;
+    KsgTableFn fn_table;  // persistent multi-problem form
 };
 
 // Radix sort of (key, index) pairs on the low end_bit key bits (sort.cu).

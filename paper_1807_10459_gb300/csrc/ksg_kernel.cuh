@@ -84,6 +84,11 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
                  : "memory");
 }
 
+__device__ __forceinline__ void mbar_inval(uint64_t *bar)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 __device__ __forceinline__ void fence_mbar_init()
 {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -258,9 +263,11 @@ struct KsgShape {
     static_assert(EV_OFF % 16 == 0, "event lists are read as float4");
 };
 
+// One CTA's work: query tile qt of job group grp.  Returns false when the
+// CTA aborted (a bounded wait ran out).  Shared memory is set up afresh on
+// every call, so a persistent CTA may run it repeatedly.
 template <int DX, int DY, int DZ, int K1, bool EXACT, int QCTA, int NWARPS>
-__global__ void __launch_bounds__(KsgShape<DX, DY, DZ, K1, EXACT, QCTA, NWARPS>::THREADS)
-    ksg_fused_kernel(const KsgLaunch a)
+__device__ __forceinline__ bool ksg_cta(const KsgLaunch &a, const int qt, const int grp)
 {
     using S = KsgShape<DX, DY, DZ, K1, EXACT, QCTA, NWARPS>;
     constexpr int DS = S::DS, DSP = S::DSP, XW = S::XW, NW = S::NW, GB = S::GB, QC = S::QC;
@@ -289,8 +296,6 @@ __global__ void __launch_bounds__(KsgShape<DX, DY, DZ, K1, EXACT, QCTA, NWARPS>:
     const int warp = tid >> 5, lane = tid & 31;
     // this warp's event list: the references of a unit below the bound
     float4 *s_ev = reinterpret_cast<float4 *>(smem_raw + S::EV_OFF) + warp * S::EV_CAP;
-    const int qt = blockIdx.x;
-    const int grp = blockIdx.y;
     const int64_t q0 = static_cast<int64_t>(qt) * QC;  // CTA's first query (sorted)
     const int n_tiles = static_cast<int>(a.n_pad / kTJ);
     const int total = 2 * n_tiles;  // items: pass A tiles, then pass B tiles
@@ -303,7 +308,7 @@ __global__ void __launch_bounds__(KsgShape<DX, DY, DZ, K1, EXACT, QCTA, NWARPS>:
         // Only padding queries (n_pad is a multiple of the reference tile, not
         // of QC): zero partial sums, and no copy is ever issued.
         if (tid < GB && job_ok) a.partial[static_cast<int64_t>(job) * a.n_qt + qt] = 0.0;
-        return;
+        return true;
     }
 
     // ---------------- set-up: query rows and X values, empty heaps, zero counts
@@ -657,8 +662,11 @@ __global__ void __launch_bounds__(KsgShape<DX, DY, DZ, K1, EXACT, QCTA, NWARPS>:
                                             static_cast<uint32_t>((s_last[st] / ST) & 1),
                                             a.timeout_ns);
         __syncthreads();
-        return;
+        return false;
     }
+    // Every issued copy has landed (each item was waited for by its units).
+    if (tid == 0)
+        for (int st = 0; st < ST; ++st) mbar_inval(&s_bar[st]);
 
     // ---------------- epilogue: self pair, outputs, digamma terms (fixed order)
     double tsum = 0.0;
@@ -695,6 +703,55 @@ __global__ void __launch_bounds__(KsgShape<DX, DY, DZ, K1, EXACT, QCTA, NWARPS>:
         for (int w = 0; w < NW; ++w) s += s_red[w][tid];
         a.partial[static_cast<int64_t>(job) * a.n_qt + qt] = s;
     }
+    __syncthreads();  // shared state may be reused by the CTA's next task
+    return true;
+}
+
+template <int DX, int DY, int DZ, int K1, bool EXACT, int QCTA, int NWARPS>
+__global__ void __launch_bounds__(KsgShape<DX, DY, DZ, K1, EXACT, QCTA, NWARPS>::THREADS)
+    ksg_fused_kernel(const KsgLaunch a)
+{
+    (void)ksg_cta<DX, DY, DZ, K1, EXACT, QCTA, NWARPS>(a, blockIdx.x, blockIdx.y);
+}
+
+// Persistent form over the tasks of several problems (KsgTable).  A CTA takes
+// the next task, finds its problem by binary search over the task offsets and
+// runs it; it stops when the tasks run out or when one of its tasks aborted.
+template <int DX, int DY, int DZ, int K1, bool EXACT, int QCTA, int NWARPS>
+__global__ void __launch_bounds__(KsgShape<DX, DY, DZ, K1, EXACT, QCTA, NWARPS>::THREADS)
+    ksg_fused_persistent(const KsgTable t)
+{
+    __shared__ KsgLaunch s_prob;
+    __shared__ int64_t s_task;
+    __shared__ int s_p;
+    while (true) {
+        if (threadIdx.x == 0) {
+            const int64_t task = atomicAdd(t.next, 1);
+            int p = 0;
+            if (task < t.n_tasks) {
+                int lo = 0, hi = t.n_probs - 1;  // last p with start[p] <= task
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (t.start[mid] <= task)
+                        lo = mid;
+                    else
+                        hi = mid - 1;
+                }
+                p = lo;
+                s_prob = t.probs[p];
+            }
+            s_task = task;
+            s_p = p;
+        }
+        __syncthreads();
+        const int64_t task = s_task;
+        if (task >= t.n_tasks) break;
+        const KsgLaunch a = s_prob;
+        const int local = static_cast<int>(task - t.start[s_p]);
+        __syncthreads();  // s_prob, s_task, s_p are rewritten by the next iteration
+        if (!ksg_cta<DX, DY, DZ, K1, EXACT, QCTA, NWARPS>(a, local % a.n_qt, local / a.n_qt))
+            break;
+    }
 }
 
 template <int DX, int DY, int DZ, int K1, bool EXACT, int QC, int NWARPS>
@@ -716,11 +773,38 @@ cudaError_t launch_ksg(const KsgLaunch &a, int n_groups, cudaStream_t stream)
 }
 
 template <int DX, int DY, int DZ, int K1, bool EXACT, int QC, int NWARPS>
+cudaError_t launch_ksg_table(const KsgTable &t, cudaStream_t stream)
+{
+    using S = KsgShape<DX, DY, DZ, K1, EXACT, QC, NWARPS>;
+    auto kern = ksg_fused_persistent<DX, DY, DZ, K1, EXACT, QC, NWARPS>;
+    static int resident = 0;  // CTAs per SM and SMs of the device, per process
+    static int n_sms = 0;
+    if (!resident) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(S::SMEM));
+        if (e != cudaSuccess) return e;
+        int dev = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, kern, S::THREADS, S::SMEM);
+        if (e != cudaSuccess) return e;
+        if (resident < 1) resident = 1;
+    }
+    const int64_t full = static_cast<int64_t>(resident) * n_sms;
+    const unsigned grid = static_cast<unsigned>(t.n_tasks < full ? t.n_tasks : full);
+    if (grid == 0) return cudaSuccess;
+    kern<<<grid, S::THREADS, S::SMEM, stream>>>(t);
+    return cudaGetLastError();
+}
+
+template <int DX, int DY, int DZ, int K1, bool EXACT, int QC, int NWARPS>
 KsgVariant make_variant()
 {
     using S = KsgShape<DX, DY, DZ, K1, EXACT, QC, NWARPS>;
     return KsgVariant{DX, DY, DZ, K1, EXACT ? 1 : 0, S::GB, S::DSP, S::QC,
-                      &launch_ksg<DX, DY, DZ, K1, EXACT, QC, NWARPS>};
+                      &launch_ksg<DX, DY, DZ, K1, EXACT, QC, NWARPS>,
+                      &launch_ksg_table<DX, DY, DZ, K1, EXACT, QC, NWARPS>};
 }
 
 }  // namespace idtx

@@ -249,6 +249,45 @@ __global__ void k_fisher_yates(int32_t *perm, const uint64_t *streams, const uin
     }
 }
 
+// The same shuffle with the row in shared memory, one warp per slot: the
+// warp draws the next 32 SplitMix64 outputs and their indices in parallel
+// (the state before step s is seed ^ mix64(stream) + (s+1) * gamma), then
+// lane 0 performs the 32 swaps in order.  T holds an index (uint16_t for
+// n <= 65536).  Dynamic shared memory: n * sizeof(T) bytes.
+template <typename T>
+__global__ void __launch_bounds__(32)
+    k_fisher_yates_smem(int32_t *perm, const uint64_t *streams, const uint64_t *seeds, int64_t n)
+{
+    extern __shared__ __align__(16) unsigned char fy_raw[];
+    T *a = reinterpret_cast<T *>(fy_raw);
+    const int slot = blockIdx.x;
+    const int lane = threadIdx.x;
+    for (int64_t i = lane; i < n; i += 32) a[i] = (T)i;
+    __syncwarp();
+    const uint64_t base = seeds[slot] ^ mix64(streams[slot]);
+    for (int64_t s0 = 0; s0 < n - 1; s0 += 32) {
+        const int64_t s = s0 + lane;
+        int j = 0;
+        if (s < n - 1) {
+            const uint64_t r = mix64(base + (uint64_t)(s + 1) * 0x9E3779B97F4A7C15ull);
+            j = (int)__umul64hi(r, (uint64_t)(n - s));  // step s works on i = n-1-s
+        }
+        const int cnt = (int)((n - 1 - s0) < 32 ? (n - 1 - s0) : 32);
+        for (int t = 0; t < cnt; ++t) {
+            const int jt = __shfl_sync(0xffffffffu, j, t);
+            if (lane == 0) {
+                const int64_t i = n - 1 - (s0 + t);
+                const T x = a[i];
+                a[i] = a[jt];
+                a[jt] = x;
+            }
+        }
+        __syncwarp();
+    }
+    int32_t *out = perm + (int64_t)slot * n;
+    for (int64_t i = lane; i < n; i += 32) out[i] = (int32_t)a[i];
+}
+
 // xi[grp][j][g*dxb + d] = X_job[d][pi_job(order[j])] (job = grp*gb + g; jobs
 // past the end repeat job 0), 0 for d >= dx, +inf for j >= n.
 __global__ void k_gather_x(const Col *xc, int dx, int dxb, const Job *jobs, int n_jobs,
@@ -550,6 +589,7 @@ enum {
     B_SCREEN,   // screen parameters, normalisation, features, predictions, keep list
     B_MLP,      // screen network work area
     B_TRAIN,    // screen training data, order, Adam moments
+    B_TABLE,    // persistent multi-problem launches: problem table, task offsets, counters
     kNumBufs
 };
 
@@ -736,19 +776,45 @@ struct CallBuffers {
 // B_ORDER layout for n samples: order | idx | keys_in | keys_out | column ranges.
 size_t order_bytes(int64_t n) { return 4 * align_up((size_t)n * 4, 256) + 256; }
 
-void sizes_of(const Group &g, CallBuffers &b)
+// Scratch bytes one group needs (each rounded up to 256 bytes).
+CallBuffers bytes_of(const Group &g)
 {
-    b.sh = std::max(b.sh, (size_t)(g.n_pad / kTJ) * kTileRows * g.v->dsp * sizeof(float));
+    CallBuffers b;
+    b.sh = align_up((size_t)(g.n_pad / kTJ) * kTileRows * g.v->dsp * sizeof(float), 256);
     if (g.sort) {
-        b.order = std::max(b.order, order_bytes(g.n));
+        b.order = align_up(order_bytes(g.n), 256);
         size_t tmp = 0;
         sort_pairs_u32(nullptr, tmp, nullptr, nullptr, nullptr, nullptr, (int)g.n, 32, nullptr);
-        b.sort_tmp = std::max(b.sort_tmp, tmp);
+        b.sort_tmp = align_up(tmp, 256);
     }
-    b.xi = std::max(b.xi, (size_t)g.n_groups * g.n_pad * g.v->gb * g.v->dx * sizeof(float));
-    b.perm = std::max(b.perm, g.slot_stream.size() * (size_t)g.n * sizeof(int32_t));
-    b.partial = std::max(b.partial, g.jobs.size() * (size_t)g.n_qt * sizeof(double));
+    b.xi = align_up((size_t)g.n_groups * g.n_pad * g.v->gb * g.v->dx * sizeof(float), 256);
+    b.perm = align_up(g.slot_stream.size() * (size_t)g.n * sizeof(int32_t), 256);
+    b.partial = align_up(g.jobs.size() * (size_t)g.n_qt * sizeof(double), 256);
+    return b;
 }
+
+// Buffers for groups enqueued one after another (each reuses the same scratch).
+void sizes_of(const Group &g, CallBuffers &b)
+{
+    const CallBuffers o = bytes_of(g);
+    b.sh = std::max(b.sh, o.sh);
+    b.order = std::max(b.order, o.order);
+    b.sort_tmp = std::max(b.sort_tmp, o.sort_tmp);
+    b.xi = std::max(b.xi, o.xi);
+    b.perm = std::max(b.perm, o.perm);
+    b.partial = std::max(b.partial, o.partial);
+}
+
+// Where one group's scratch lives.
+struct Slices {
+    float *sh;
+    float *xi;
+    int32_t *perm;
+    double *partial;
+    unsigned char *order;
+    void *sort_tmp;
+    size_t sort_cap;
+};
 
 int take_event(idtx_ctx *c, cudaEvent_t *ev)
 {
@@ -761,9 +827,37 @@ int take_event(idtx_ctx *c, cudaEvent_t *ev)
     return IDTX_OK;
 }
 
-// Enqueue one planned group.  cmi: device [n_jobs] (the group's slice).
-int enqueue_group(idtx_ctx *c, const Group &g, cudaStream_t st, double *cmi, float *eps_out,
-                  int32_t *cnt_out, long long timeout_ns)
+// Enqueue the surrogate permutations of n_slots rows of length n.
+int enqueue_permutations(int32_t *perm, const uint64_t *streams, const uint64_t *seeds,
+                         int n_slots, int64_t n, cudaStream_t st, int &launches)
+{
+    if (n <= 65536) {
+        static bool attr_set = false;  // per process; the attribute is per function
+        const int bytes = (int)(n * sizeof(uint16_t));
+        if (!attr_set) {
+            IDTX_CUDA(cudaFuncSetAttribute(k_fisher_yates_smem<uint16_t>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(65536 * sizeof(uint16_t))));
+            attr_set = true;
+        }
+        k_fisher_yates_smem<uint16_t><<<(unsigned)n_slots, 32, bytes, st>>>(perm, streams, seeds, n);
+        IDTX_CUDA(cudaGetLastError());
+        launches += 1;
+        return IDTX_OK;
+    }
+    k_iota<<<grid_for((int64_t)n_slots * n, 256), 256, 0, st>>>(perm, n_slots, n);
+    IDTX_CUDA(cudaGetLastError());
+    k_fisher_yates<<<(n_slots + 31) / 32, 32, 0, st>>>(perm, streams, seeds, n_slots, n);
+    IDTX_CUDA(cudaGetLastError());
+    launches += 2;
+    return IDTX_OK;
+}
+
+// Enqueue the preparation of one planned group into its scratch slices
+// (sample order, shared-coordinate tiles, permutations, gathered X) and fill
+// the fused kernel's launch description.
+int prep_group(idtx_ctx *c, const Group &g, cudaStream_t st, const Slices &sl, float *eps_out,
+               int32_t *cnt_out, long long timeout_ns, KsgLaunch &a, int &launches)
 {
     const unsigned char *desc = (const unsigned char *)c->buf[B_DESC];
     const Col *xc = (const Col *)(desc + g.off_x);
@@ -772,21 +866,21 @@ int enqueue_group(idtx_ctx *c, const Group &g, cudaStream_t st, double *cmi, flo
     const Job *jobs = (const Job *)(desc + g.off_jobs);
     const uint64_t *streams = (const uint64_t *)(desc + g.off_streams);
     const uint64_t *seeds = (const uint64_t *)(desc + g.off_seeds);
-    float *sh = (float *)c->buf[B_SH];
-    float *xi = (float *)c->buf[B_XI];
-    int32_t *perm = (int32_t *)c->buf[B_PERM];
-    double *partial = (double *)c->buf[B_PARTIAL];
+    float *sh = sl.sh;
+    float *xi = sl.xi;
+    int32_t *perm = sl.perm;
+    double *partial = sl.partial;
     const KsgVariant &v = *g.v;
     const int n_jobs = (int)g.jobs.size();
     const int n_slots = (int)g.slot_stream.size();
 
     const int dzb = v.dz, dyb = v.dy;
     const int32_t *order = nullptr;
-    int launches = 0;
+    launches = 0;
     if (g.sort) {
         // Order the samples along a Morton curve of the shared coordinates, so
         // that a warp's queries and a tile's references are spatial neighbours.
-        unsigned char *ob = (unsigned char *)c->buf[B_ORDER];
+        unsigned char *ob = sl.order;
         const size_t col = align_up((size_t)g.n * 4, 256);
         int32_t *ord = (int32_t *)ob;
         int32_t *idx = (int32_t *)(ob + col);
@@ -800,8 +894,8 @@ int enqueue_group(idtx_ctx *c, const Group &g, cudaStream_t st, double *cmi, flo
         k_morton_keys<<<grid_for(g.n, 256), 256, 0, st>>>(zc, g.dz, yc, nk, bits, g.n, mm, kin,
                                                           idx);
         IDTX_CUDA(cudaGetLastError());
-        size_t tmp_bytes = c->cap[B_SORT];
-        IDTX_CUDA(sort_pairs_u32(c->buf[B_SORT], tmp_bytes, kin, kout, idx, ord, (int)g.n,
+        size_t tmp_bytes = sl.sort_cap;
+        IDTX_CUDA(sort_pairs_u32(sl.sort_tmp, tmp_bytes, kin, kout, idx, ord, (int)g.n,
                                  nk * bits, st));
         order = ord;
         launches += 3;
@@ -811,19 +905,12 @@ int enqueue_group(idtx_ctx *c, const Group &g, cudaStream_t st, double *cmi, flo
     IDTX_CUDA(cudaGetLastError());
     k_tile_boxes<<<(unsigned)(g.n_pad / kTJ), kTJ, 0, st>>>(sh, v.dsp, g.n);
     IDTX_CUDA(cudaGetLastError());
-    if (n_slots > 0) {
-        k_iota<<<grid_for((int64_t)n_slots * g.n, 256), 256, 0, st>>>(perm, n_slots, g.n);
-        IDTX_CUDA(cudaGetLastError());
-        k_fisher_yates<<<(n_slots + 31) / 32, 32, 0, st>>>(perm, streams, seeds, n_slots, g.n);
-        IDTX_CUDA(cudaGetLastError());
-        launches += 2;
-    }
+    if (n_slots > 0) IDTX_TRY(enqueue_permutations(perm, streams, seeds, n_slots, g.n, st, launches));
     k_gather_x<<<grid_for((int64_t)g.n_groups * g.n_pad * v.gb * v.dx, 256), 256, 0, st>>>(
         xc, g.dx, v.dx, jobs, n_jobs, perm, g.n, g.n_pad, v.gb, g.n_groups, order, xi, c->d_err);
     IDTX_CUDA(cudaGetLastError());
     launches += 5;  // pack, boxes, gather, fused, finalize
 
-    KsgLaunch a;
     a.sh = sh;
     a.xi = xi;
     a.psi = c->psi;
@@ -839,6 +926,46 @@ int enqueue_group(idtx_ctx *c, const Group &g, cudaStream_t st, double *cmi, flo
     a.n_qt = g.n_qt;
     a.k = g.k;
     a.timeout_ns = timeout_ns;
+    return IDTX_OK;
+}
+
+// Record a group's shape for its work counters and count its launches.
+void note_group(idtx_ctx *c, const Group &g, int launches)
+{
+    const int n_jobs = (int)g.jobs.size();
+    if (g.plain) {
+        c->stats.fused_launches += n_jobs;
+        c->stats.kernel_launches += launches - 1 + n_jobs;
+        return;
+    }
+    WorkShape ws;
+    ws.dx = g.dx;
+    ws.dy = g.dy;
+    ws.dz_eff = std::max(g.dz, 1);
+    ws.gb = g.v->gb;
+    ws.job_frac = (double)n_jobs / ((double)g.n_groups * g.v->gb);
+    ws.exhaustive_pairs = 2.0 * (double)g.n * (double)g.n * (double)g.n_groups;
+    if ((int)c->call_shapes.size() <= g.work_slot) c->call_shapes.resize(g.work_slot + 1);
+    c->call_shapes[g.work_slot] = ws;
+    c->stats.fused_launches += 1;
+    c->stats.kernel_launches += launches;
+}
+
+// Enqueue one planned group on the context's shared scratch.  cmi: device
+// [n_jobs] (the group's slice).
+int enqueue_group(idtx_ctx *c, const Group &g, cudaStream_t st, double *cmi, float *eps_out,
+                  int32_t *cnt_out, long long timeout_ns)
+{
+    const Slices sl{(float *)c->buf[B_SH],       (float *)c->buf[B_XI],
+                    (int32_t *)c->buf[B_PERM],   (double *)c->buf[B_PARTIAL],
+                    (unsigned char *)c->buf[B_ORDER], c->buf[B_SORT], c->cap[B_SORT]};
+    KsgLaunch a;
+    int launches = 0;
+    IDTX_TRY(prep_group(c, g, st, sl, eps_out, cnt_out, timeout_ns, a, launches));
+    const KsgVariant &v = *g.v;
+    const int n_jobs = (int)g.jobs.size();
+    float *xi = sl.xi;
+    double *partial = sl.partial;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (c->profiling) {
         IDTX_TRY(take_event(c, &ev0));
@@ -850,7 +977,7 @@ int enqueue_group(idtx_ctx *c, const Group &g, cudaStream_t st, double *cmi, flo
         for (int jb = 0; jb < n_jobs; ++jb) {
             const float *xg = xi + (size_t)(jb / v.gb) * g.n_pad * xw + (jb % v.gb) * v.dx;
             k_ksg_plain<<<(unsigned)g.n_qt, kPlainThreads, 0, st>>>(
-                sh, v.dsp, g.dz, v.dz, g.dy, xg, xw, g.dx, g.n, g.k, c->psi,
+                sl.sh, v.dsp, g.dz, v.dz, g.dy, xg, xw, g.dx, g.n, g.k, c->psi,
                 partial + (size_t)jb * g.n_qt);
             IDTX_CUDA(cudaGetLastError());
         }
@@ -861,25 +988,132 @@ int enqueue_group(idtx_ctx *c, const Group &g, cudaStream_t st, double *cmi, flo
         IDTX_CUDA(cudaEventRecord(ev1, st));
         c->pending.emplace_back(ev0, ev1);
     }
-    if (g.plain) {
-        c->stats.fused_launches += n_jobs;
-        c->stats.kernel_launches += launches - 1 + n_jobs;
-    } else {
-        WorkShape ws;
-        ws.dx = g.dx;
-        ws.dy = g.dy;
-        ws.dz_eff = std::max(g.dz, 1);
-        ws.gb = v.gb;
-        ws.job_frac = (double)n_jobs / ((double)g.n_groups * v.gb);
-        ws.exhaustive_pairs = 2.0 * (double)g.n * (double)g.n * (double)g.n_groups;
-        if ((int)c->call_shapes.size() <= g.work_slot) c->call_shapes.resize(g.work_slot + 1);
-        c->call_shapes[g.work_slot] = ws;
-        c->stats.fused_launches += 1;
-        c->stats.kernel_launches += launches;
-    }
+    note_group(c, g, launches);
     k_finalize<<<(n_jobs + 127) / 128, 128, 0, st>>>(partial, n_jobs, g.n_qt, c->psi, g.k, g.n,
                                                       cmi);
     IDTX_CUDA(cudaGetLastError());
+    return IDTX_OK;
+}
+
+// Enqueue several planned groups with one persistent fused launch per kernel
+// variant: every group gets its own scratch slices, all are prepared, then
+// each variant's groups run as the tasks of one launch (largest N first, so
+// long tasks start early), then every group is finalised.  cmi: device
+// [sum of jobs], group g's slice at g.off_cmi.
+int enqueue_batch(idtx_ctx *c, const std::vector<Group> &gs, cudaStream_t st, double *cmi,
+                  long long timeout_ns)
+{
+    const size_t n = gs.size();
+    std::vector<CallBuffers> off(n);
+    CallBuffers tot;
+    for (size_t i = 0; i < n; ++i) {
+        const CallBuffers b = bytes_of(gs[i]);
+        off[i] = tot;
+        tot.sh += b.sh;
+        tot.xi += b.xi;
+        tot.perm += b.perm;
+        tot.partial += b.partial;
+        tot.order += b.order;
+        tot.sort_tmp += b.sort_tmp;
+    }
+    IDTX_TRY(ensure(c, B_SH, tot.sh));
+    IDTX_TRY(ensure(c, B_XI, tot.xi));
+    IDTX_TRY(ensure(c, B_PERM, tot.perm));
+    IDTX_TRY(ensure(c, B_PARTIAL, tot.partial));
+    IDTX_TRY(ensure(c, B_ORDER, tot.order));
+    IDTX_TRY(ensure(c, B_SORT, tot.sort_tmp));
+
+    // Variant buckets, each ordered by decreasing N.
+    std::vector<const KsgVariant *> vars;
+    for (const Group &g : gs)
+        if (std::find(vars.begin(), vars.end(), g.v) == vars.end()) vars.push_back(g.v);
+    std::vector<std::vector<int>> bucket(vars.size());
+    for (size_t i = 0; i < n; ++i)
+        bucket[std::find(vars.begin(), vars.end(), gs[i].v) - vars.begin()].push_back((int)i);
+    for (auto &b : bucket)
+        std::stable_sort(b.begin(), b.end(), [&](int x, int y) { return gs[x].n > gs[y].n; });
+
+    // Table layout: per bucket its KsgLaunch entries, task offsets and counter.
+    std::vector<KsgLaunch> probs(n);
+    std::vector<int64_t> start;
+    std::vector<size_t> b_probs(vars.size()), b_start(vars.size());
+    std::vector<int64_t> b_tasks(vars.size());
+    size_t at = 0;
+    for (size_t b = 0; b < vars.size(); ++b) {
+        b_probs[b] = at;
+        at += bucket[b].size();
+    }
+    for (size_t b = 0; b < vars.size(); ++b) {
+        b_start[b] = start.size();
+        int64_t t = 0;
+        for (int i : bucket[b]) {
+            start.push_back(t);
+            t += (int64_t)gs[i].n_qt * gs[i].n_groups;
+        }
+        start.push_back(t);
+        b_tasks[b] = t;
+    }
+    const size_t probs_bytes = align_up(n * sizeof(KsgLaunch), 256);
+    const size_t start_bytes = align_up(start.size() * sizeof(int64_t), 256);
+    const size_t cnt_bytes = vars.size() * sizeof(int);
+    IDTX_TRY(ensure(c, B_TABLE, probs_bytes + start_bytes + cnt_bytes));
+    unsigned char *tb = (unsigned char *)c->buf[B_TABLE];
+    KsgLaunch *probs_d = (KsgLaunch *)tb;
+    int64_t *start_d = (int64_t *)(tb + probs_bytes);
+    int *next_d = (int *)(tb + probs_bytes + start_bytes);
+
+    // Prepare every group into its slices.
+    std::vector<int> launches(n, 0);
+    for (size_t b = 0; b < vars.size(); ++b)
+        for (size_t j = 0; j < bucket[b].size(); ++j) {
+            const int i = bucket[b][j];
+            const Slices sl{(float *)((unsigned char *)c->buf[B_SH] + off[i].sh),
+                            (float *)((unsigned char *)c->buf[B_XI] + off[i].xi),
+                            (int32_t *)((unsigned char *)c->buf[B_PERM] + off[i].perm),
+                            (double *)((unsigned char *)c->buf[B_PARTIAL] + off[i].partial),
+                            (unsigned char *)c->buf[B_ORDER] + off[i].order,
+                            (unsigned char *)c->buf[B_SORT] + off[i].sort_tmp,
+                            bytes_of(gs[i]).sort_tmp};
+            IDTX_TRY(prep_group(c, gs[i], st, sl, nullptr, nullptr, timeout_ns,
+                                probs[b_probs[b] + j], launches[i]));
+        }
+    IDTX_CUDA(cudaMemcpyAsync(probs_d, probs.data(), n * sizeof(KsgLaunch),
+                              cudaMemcpyHostToDevice, st));
+    IDTX_CUDA(cudaMemcpyAsync(start_d, start.data(), start.size() * sizeof(int64_t),
+                              cudaMemcpyHostToDevice, st));
+    IDTX_CUDA(cudaMemsetAsync(next_d, 0, cnt_bytes, st));
+
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (c->profiling) {
+        IDTX_TRY(take_event(c, &ev0));
+        IDTX_TRY(take_event(c, &ev1));
+        IDTX_CUDA(cudaEventRecord(ev0, st));
+    }
+    for (size_t b = 0; b < vars.size(); ++b) {
+        KsgTable t;
+        t.probs = probs_d + b_probs[b];
+        t.start = start_d + b_start[b];
+        t.next = next_d + b;
+        t.n_probs = (int)bucket[b].size();
+        t.n_tasks = b_tasks[b];
+        IDTX_CUDA(vars[b]->fn_table(t, st));
+    }
+    if (c->profiling) {
+        IDTX_CUDA(cudaEventRecord(ev1, st));
+        c->pending.emplace_back(ev0, ev1);
+    }
+    for (size_t i = 0; i < n; ++i) {
+        const Group &g = gs[i];
+        const int n_jobs = (int)g.jobs.size();
+        note_group(c, g, launches[i]);
+        double *partial = (double *)((unsigned char *)c->buf[B_PARTIAL] + off[i].partial);
+        k_finalize<<<(n_jobs + 127) / 128, 128, 0, st>>>(partial, n_jobs, g.n_qt, c->psi, g.k,
+                                                          g.n, cmi + g.off_cmi);
+        IDTX_CUDA(cudaGetLastError());
+    }
+    // One fused launch per variant instead of one per group.
+    c->stats.fused_launches -= (unsigned long long)(n - vars.size());
+    c->stats.kernel_launches -= (unsigned long long)(n - vars.size());
     return IDTX_OK;
 }
 
@@ -1222,23 +1456,14 @@ int idtx_cmi_batch(idtx_ctx *c, const idtx_problem *probs, int n_probs, int k, d
     }
     std::vector<unsigned char> arena;
     pack_desc(gs, arena);
-    CallBuffers b;
-    for (const Group &g : gs) sizes_of(g, b);
     IDTX_TRY(ensure(c, B_DESC, arena.size()));
-    IDTX_TRY(ensure(c, B_SH, b.sh));
-    IDTX_TRY(ensure(c, B_XI, b.xi));
-    IDTX_TRY(ensure(c, B_PERM, b.perm));
-    IDTX_TRY(ensure(c, B_PARTIAL, b.partial));
-    IDTX_TRY(ensure(c, B_ORDER, b.order));
-    IDTX_TRY(ensure(c, B_SORT, b.sort_tmp));
     IDTX_TRY(ensure(c, B_CMI, total_jobs * sizeof(double)));
     IDTX_TRY(ensure_psi(c, std::max<int64_t>(n_max, k) + 1, st));
     IDTX_CUDA(cudaMemcpyAsync(c->buf[B_DESC], arena.data(), arena.size(), cudaMemcpyHostToDevice,
                               st));
     double *cmi_d = (double *)c->buf[B_CMI];
     const long long tmo = timeout_of(nullptr);
-    for (const Group &g : gs)
-        IDTX_TRY(enqueue_group(c, g, st, cmi_d + g.off_cmi, nullptr, nullptr, tmo));
+    IDTX_TRY(enqueue_batch(c, gs, st, cmi_d, tmo));
     IDTX_CUDA(cudaMemcpyAsync(out, cmi_d, total_jobs * sizeof(double),
                               device_accessible(out) ? cudaMemcpyDeviceToDevice
                                                      : cudaMemcpyDeviceToHost,

@@ -158,6 +158,29 @@ def test_batch_uneven(idtx):
         assert np.max(np.abs(o.cpu().numpy() - ref)) < TOL
 
 
+@pytest.mark.parametrize("k", [4, 3])
+def test_batch_is_one_launch_per_variant_and_equals_separate_calls(idtx, k):
+    """A batch runs as one persistent fused launch per kernel variant; every
+    estimate equals the one a separate call gives, bit for bit (same per-CTA
+    arithmetic, same fixed-order sums).  Sizes include query tiles made only
+    of padding (N mod 128 < 64) and problems sharing a variant."""
+    shapes = [(700, 1, 1, 2), (1030, 1, 1, 2), (385, 2, 1, 3), (260, 1, 2, 1), (129, 1, 1, 2)]
+    probs = [synth.gaussian_problem(n, dx, dy, dz, seed=40 + i)
+             for i, (n, dx, dy, dz) in enumerate(shapes)]
+    ctx = idtx.Context(0)
+    ctx.reset_stats()
+    out = idtx.cmi_batch([dict(x=_dev(p.x), y=_dev(p.y), z=_dev(p.z), n_surr=9, seed=5 + i)
+                          for i, p in enumerate(probs)], k=k, ctx=ctx)
+    st = ctx.stats()
+    n_variants = 3 if k == 4 else 1   # (1,1,2) x3, (2,1,3), (1,2,1); k=3: generic
+    assert st["fused_launches"] == n_variants
+    for i, (p, o) in enumerate(zip(probs, out)):
+        sep = idtx.cmi_ksg(_dev(p.x), _dev(p.y), _dev(p.z), k=k, n_surr=9, seed=5 + i)
+        assert np.array_equal(o.cpu().numpy(), sep.cpu().numpy())
+    ref = oracle.cmi_surrogates(probs[2].x, probs[2].y, probs[2].z, k, 9, 7)
+    assert np.max(np.abs(out[2].cpu().numpy() - ref)) < TOL
+
+
 def test_greedy_step_matches_oracle(idtx):
     net = synth.var_network(n_nodes=5, order=3, T=700, density=0.4, weight=0.6, seed=21)
     S = 20
