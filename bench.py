@@ -433,6 +433,20 @@ def run_batch64(args):
     s1.record()
     torch.cuda.synchronize()
     ms_sep = s0.elapsed_time(s1)
+    # CUDA-graph replay of the same call (captured once, then replayed)
+    gctx = idtx.Context(0)
+    gctx.set_graphs(True)
+    idtx.cmi_batch(dev, k=4, ctx=gctx)
+    torch.cuda.synchronize()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record()
+    for _ in range(args.steps):
+        idtx.cmi_batch(dev, k=4, ctx=gctx)
+    g1.record()
+    torch.cuda.synchronize()
+    ms_graph = g0.elapsed_time(g1) / args.steps
+    replays = gctx.stats()["graph_launches"] - 1
+    del gctx
     # plain mode: two estimates per problem, one launch each
     t_plain = 0.0
     for p, d in zip(probs, dev):
@@ -452,6 +466,8 @@ def run_batch64(args):
             "fused_share_of_call": st["fused_ms"] / (ms * args.steps) if ms else None,
             "modes": {"batched": n_est / (ms / 1e3),
                       "separate_calls": n_est / (ms_sep / 1e3),
+                      "graph_replay": n_est / (ms_graph / 1e3),
+                      "graph_replays_timed": replays,
                       "plain_estimated": n_est / t_plain,
                       "batched_over_plain": t_plain / (ms / 1e3),
                       "plain_sample": "2 estimates of every problem, one launch each, "

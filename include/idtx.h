@@ -138,10 +138,26 @@ typedef struct {
     double scanned_a, passed_a, scanned_b, passed_b;
     double exhaustive_pairs;
     double wait_cycles, warp_cycles;
+    int64_t graph_launches;  /* calls served by replaying a captured graph */
 } idtx_stats;
 
 /* Enable (1) or disable (0) event timing of the fused kernel. */
 int idtx_ctx_set_profiling(idtx_ctx *ctx, int enable);
+
+/* Enable (1) or disable (0) CUDA-graph replay of idtx_cmi_batch (off by
+ * default; no counterpart in the paper: a launch-overhead measure for calls
+ * repeated on the same device buffers).  When enabled, profiling is off and
+ * every input is device memory, the call's device work (sample ordering,
+ * tiles, permutations, gathers, the persistent fused launches,
+ * finalisation) is captured once into a graph that owns its scratch
+ * buffers, and a later call with identical arguments (input pointers,
+ * sizes, surrogate counts, seeds, k, stream) replays it; the inputs may
+ * hold new values, and out (host or device) may differ between calls (the
+ * results are copied to it after the graph).  Calls with other arguments capture a new
+ * graph (the old one is released); disabling releases it too.  Work
+ * counters and fused-kernel timing are not collected for replayed calls.
+ * Returns IDTX_EINVAL for a NULL ctx. */
+int idtx_ctx_set_graphs(idtx_ctx *ctx, int enable);
 
 /* Read the counters accumulated since creation or the last reset. */
 int idtx_ctx_get_stats(idtx_ctx *ctx, idtx_stats *out);

@@ -59,7 +59,7 @@ class Stats(ctypes.Structure):
                 ("scanned_a", ctypes.c_double), ("passed_a", ctypes.c_double),
                 ("scanned_b", ctypes.c_double), ("passed_b", ctypes.c_double),
                 ("exhaustive_pairs", ctypes.c_double), ("wait_cycles", ctypes.c_double),
-                ("warp_cycles", ctypes.c_double)]
+                ("warp_cycles", ctypes.c_double), ("graph_launches", ctypes.c_int64)]
 
 
 class Step(ctypes.Structure):
@@ -112,10 +112,12 @@ def load():
                                           ctypes.POINTER(ctypes.c_double), vp]
         lib.idtx_screen_set.argtypes = [vp, ctypes.POINTER(ScreenC)]
         lib.idtx_ctx_set_profiling.argtypes = [vp, i32]
+        lib.idtx_ctx_set_graphs.argtypes = [vp, i32]
         lib.idtx_ctx_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
         lib.idtx_ctx_reset_stats.argtypes = [vp]
         for name in ("idtx_screen_predict", "idtx_screen_loss_grad", "idtx_screen_train",
-                     "idtx_screen_set", "idtx_ctx_set_profiling", "idtx_ctx_get_stats", "idtx_ctx_reset_stats",
+                     "idtx_screen_set", "idtx_ctx_set_profiling", "idtx_ctx_set_graphs",
+                     "idtx_ctx_get_stats", "idtx_ctx_reset_stats",
                      "idtx_ctx_create", "idtx_ctx_destroy", "idtx_cmi_ksg", "idtx_cmi_batch",
                      "idtx_mte_step", "idtx_mte_select_target", "idtx_version"):
             getattr(lib, name).restype = ctypes.c_int
@@ -143,6 +145,10 @@ class Context:
         """Time the fused estimator kernel with CUDA events (see stats())."""
         _check(load().idtx_ctx_set_profiling(self.handle, 1 if on else 0))
 
+    def set_graphs(self, on: bool = True):
+        """Replay a captured CUDA graph for repeated identical cmi_batch calls."""
+        _check(load().idtx_ctx_set_graphs(self.handle, 1 if on else 0))
+
     def stats(self) -> dict:
         st = Stats()
         _check(load().idtx_ctx_get_stats(self.handle, ctypes.byref(st)))
@@ -150,7 +156,8 @@ class Context:
                     fused_ms=st.fused_ms, fused_lane_ops=st.fused_lane_ops,
                     scanned_a=st.scanned_a, passed_a=st.passed_a, scanned_b=st.scanned_b,
                     passed_b=st.passed_b, exhaustive_pairs=st.exhaustive_pairs,
-                    wait_cycles=st.wait_cycles, warp_cycles=st.warp_cycles)
+                    wait_cycles=st.wait_cycles, warp_cycles=st.warp_cycles,
+                    graph_launches=st.graph_launches)
 
     def reset_stats(self):
         _check(load().idtx_ctx_reset_stats(self.handle))

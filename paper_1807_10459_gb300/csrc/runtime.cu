@@ -619,7 +619,31 @@ struct idtx_ctx {
     size_t h_work_cap = 0;
     bool has_screen = false;
     idtx_screen screen;  // installed by idtx_screen_set
+    // CUDA-graph replay of idtx_cmi_batch: the graph's own scratch buffers,
+    // the arguments it was captured for, the capture stream
+    bool graphs = false;
+    void *gbuf[kNumBufs] = {};
+    size_t gcap[kNumBufs] = {};
+    cudaGraphExec_t graph_exec = nullptr;
+    std::vector<uint64_t> graph_key;
+    cudaStream_t cap_stream = nullptr;
 };
+
+void drop_graph(idtx_ctx *c)
+{
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    c->graph_exec = nullptr;
+    c->graph_key.clear();
+}
+
+// Exchange the context's scratch buffers with the graph's.
+void swap_buffer_sets(idtx_ctx *c)
+{
+    for (int i = 0; i < kNumBufs; ++i) {
+        std::swap(c->buf[i], c->gbuf[i]);
+        std::swap(c->cap[i], c->gcap[i]);
+    }
+}
 
 namespace {
 
@@ -828,18 +852,26 @@ int take_event(idtx_ctx *c, cudaEvent_t *ev)
 }
 
 // Enqueue the surrogate permutations of n_slots rows of length n.
+// One-time attribute of the shared-memory shuffle (per process; the attribute
+// is per function).  Also called before a graph capture.
+int init_permutation_kernel()
+{
+    static bool attr_set = false;
+    if (!attr_set) {
+        IDTX_CUDA(cudaFuncSetAttribute(k_fisher_yates_smem<uint16_t>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(65536 * sizeof(uint16_t))));
+        attr_set = true;
+    }
+    return IDTX_OK;
+}
+
 int enqueue_permutations(int32_t *perm, const uint64_t *streams, const uint64_t *seeds,
                          int n_slots, int64_t n, cudaStream_t st, int &launches)
 {
     if (n <= 65536) {
-        static bool attr_set = false;  // per process; the attribute is per function
         const int bytes = (int)(n * sizeof(uint16_t));
-        if (!attr_set) {
-            IDTX_CUDA(cudaFuncSetAttribute(k_fisher_yates_smem<uint16_t>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)(65536 * sizeof(uint16_t))));
-            attr_set = true;
-        }
+        IDTX_TRY(init_permutation_kernel());
         k_fisher_yates_smem<uint16_t><<<(unsigned)n_slots, 32, bytes, st>>>(perm, streams, seeds, n);
         IDTX_CUDA(cudaGetLastError());
         launches += 1;
@@ -851,6 +883,27 @@ int enqueue_permutations(int32_t *perm, const uint64_t *streams, const uint64_t 
     IDTX_CUDA(cudaGetLastError());
     launches += 2;
     return IDTX_OK;
+}
+
+// The fused kernel's launch description of a group prepared into sl.
+void fill_launch(const idtx_ctx *c, const Group &g, const Slices &sl, float *eps_out,
+                 int32_t *cnt_out, long long timeout_ns, KsgLaunch &a)
+{
+    a.sh = sl.sh;
+    a.xi = sl.xi;
+    a.psi = c->psi;
+    a.partial = sl.partial;
+    a.eps_out = eps_out;
+    a.cnt_out = cnt_out;
+    a.order = g.sort ? (const int32_t *)sl.order : nullptr;
+    a.work = (unsigned long long *)c->buf[B_WORK] + (size_t)g.work_slot * kNumWork;
+    a.err = c->d_err;
+    a.n = g.n;
+    a.n_pad = g.n_pad;
+    a.n_jobs = (int)g.jobs.size();
+    a.n_qt = g.n_qt;
+    a.k = g.k;
+    a.timeout_ns = timeout_ns;
 }
 
 // Enqueue the preparation of one planned group into its scratch slices
@@ -910,22 +963,7 @@ int prep_group(idtx_ctx *c, const Group &g, cudaStream_t st, const Slices &sl, f
         xc, g.dx, v.dx, jobs, n_jobs, perm, g.n, g.n_pad, v.gb, g.n_groups, order, xi, c->d_err);
     IDTX_CUDA(cudaGetLastError());
     launches += 5;  // pack, boxes, gather, fused, finalize
-
-    a.sh = sh;
-    a.xi = xi;
-    a.psi = c->psi;
-    a.partial = partial;
-    a.eps_out = eps_out;
-    a.cnt_out = cnt_out;
-    a.order = order;
-    a.work = (unsigned long long *)c->buf[B_WORK] + (size_t)g.work_slot * kNumWork;
-    a.err = c->d_err;
-    a.n = g.n;
-    a.n_pad = g.n_pad;
-    a.n_jobs = n_jobs;
-    a.n_qt = g.n_qt;
-    a.k = g.k;
-    a.timeout_ns = timeout_ns;
+    fill_launch(c, g, sl, eps_out, cnt_out, timeout_ns, a);
     return IDTX_OK;
 }
 
@@ -995,13 +1033,24 @@ int enqueue_group(idtx_ctx *c, const Group &g, cudaStream_t st, double *cmi, flo
     return IDTX_OK;
 }
 
-// Enqueue several planned groups with one persistent fused launch per kernel
-// variant: every group gets its own scratch slices, all are prepared, then
-// each variant's groups run as the tasks of one launch (largest N first, so
-// long tasks start early), then every group is finalised.  cmi: device
-// [sum of jobs], group g's slice at g.off_cmi.
-int enqueue_batch(idtx_ctx *c, const std::vector<Group> &gs, cudaStream_t st, double *cmi,
-                  long long timeout_ns)
+// A batch of planned groups laid out for persistent fused launches: every
+// group gets its own scratch slices; the groups of each kernel variant form
+// the tasks of one launch, largest N first (long tasks start early).
+struct BatchPlan {
+    std::vector<Slices> sl;
+    std::vector<const KsgVariant *> vars;
+    std::vector<std::vector<int>> bucket;
+    std::vector<size_t> b_probs, b_start;
+    std::vector<int64_t> b_tasks;
+    KsgLaunch *probs_d = nullptr;
+    int64_t *start_d = nullptr;
+    int *next_d = nullptr;
+};
+
+// Host part of a batch: scratch, launch descriptions and task offsets, the
+// latter uploaded to the device (B_TABLE) on st.
+int batch_plan(idtx_ctx *c, const std::vector<Group> &gs, cudaStream_t st, long long timeout_ns,
+               BatchPlan &bp)
 {
     const size_t n = gs.size();
     std::vector<CallBuffers> off(n);
@@ -1022,81 +1071,87 @@ int enqueue_batch(idtx_ctx *c, const std::vector<Group> &gs, cudaStream_t st, do
     IDTX_TRY(ensure(c, B_PARTIAL, tot.partial));
     IDTX_TRY(ensure(c, B_ORDER, tot.order));
     IDTX_TRY(ensure(c, B_SORT, tot.sort_tmp));
-
-    // Variant buckets, each ordered by decreasing N.
-    std::vector<const KsgVariant *> vars;
-    for (const Group &g : gs)
-        if (std::find(vars.begin(), vars.end(), g.v) == vars.end()) vars.push_back(g.v);
-    std::vector<std::vector<int>> bucket(vars.size());
+    bp.sl.resize(n);
     for (size_t i = 0; i < n; ++i)
-        bucket[std::find(vars.begin(), vars.end(), gs[i].v) - vars.begin()].push_back((int)i);
-    for (auto &b : bucket)
+        bp.sl[i] = Slices{(float *)((unsigned char *)c->buf[B_SH] + off[i].sh),
+                          (float *)((unsigned char *)c->buf[B_XI] + off[i].xi),
+                          (int32_t *)((unsigned char *)c->buf[B_PERM] + off[i].perm),
+                          (double *)((unsigned char *)c->buf[B_PARTIAL] + off[i].partial),
+                          (unsigned char *)c->buf[B_ORDER] + off[i].order,
+                          (unsigned char *)c->buf[B_SORT] + off[i].sort_tmp,
+                          bytes_of(gs[i]).sort_tmp};
+
+    for (const Group &g : gs)
+        if (std::find(bp.vars.begin(), bp.vars.end(), g.v) == bp.vars.end()) bp.vars.push_back(g.v);
+    const size_t nv = bp.vars.size();
+    bp.bucket.assign(nv, {});
+    for (size_t i = 0; i < n; ++i)
+        bp.bucket[std::find(bp.vars.begin(), bp.vars.end(), gs[i].v) - bp.vars.begin()].push_back(
+            (int)i);
+    for (auto &b : bp.bucket)
         std::stable_sort(b.begin(), b.end(), [&](int x, int y) { return gs[x].n > gs[y].n; });
 
-    // Table layout: per bucket its KsgLaunch entries, task offsets and counter.
     std::vector<KsgLaunch> probs(n);
     std::vector<int64_t> start;
-    std::vector<size_t> b_probs(vars.size()), b_start(vars.size());
-    std::vector<int64_t> b_tasks(vars.size());
+    bp.b_probs.assign(nv, 0);
+    bp.b_start.assign(nv, 0);
+    bp.b_tasks.assign(nv, 0);
     size_t at = 0;
-    for (size_t b = 0; b < vars.size(); ++b) {
-        b_probs[b] = at;
-        at += bucket[b].size();
-    }
-    for (size_t b = 0; b < vars.size(); ++b) {
-        b_start[b] = start.size();
+    for (size_t b = 0; b < nv; ++b) {
+        bp.b_probs[b] = at;
+        bp.b_start[b] = start.size();
         int64_t t = 0;
-        for (int i : bucket[b]) {
+        for (int i : bp.bucket[b]) {
+            fill_launch(c, gs[i], bp.sl[i], nullptr, nullptr, timeout_ns, probs[at++]);
             start.push_back(t);
             t += (int64_t)gs[i].n_qt * gs[i].n_groups;
         }
         start.push_back(t);
-        b_tasks[b] = t;
+        bp.b_tasks[b] = t;
     }
     const size_t probs_bytes = align_up(n * sizeof(KsgLaunch), 256);
     const size_t start_bytes = align_up(start.size() * sizeof(int64_t), 256);
-    const size_t cnt_bytes = vars.size() * sizeof(int);
-    IDTX_TRY(ensure(c, B_TABLE, probs_bytes + start_bytes + cnt_bytes));
+    IDTX_TRY(ensure(c, B_TABLE, probs_bytes + start_bytes + nv * sizeof(int)));
     unsigned char *tb = (unsigned char *)c->buf[B_TABLE];
-    KsgLaunch *probs_d = (KsgLaunch *)tb;
-    int64_t *start_d = (int64_t *)(tb + probs_bytes);
-    int *next_d = (int *)(tb + probs_bytes + start_bytes);
+    bp.probs_d = (KsgLaunch *)tb;
+    bp.start_d = (int64_t *)(tb + probs_bytes);
+    bp.next_d = (int *)(tb + probs_bytes + start_bytes);
+    IDTX_CUDA(cudaMemcpyAsync(bp.probs_d, probs.data(), n * sizeof(KsgLaunch),
+                              cudaMemcpyHostToDevice, st));
+    IDTX_CUDA(cudaMemcpyAsync(bp.start_d, start.data(), start.size() * sizeof(int64_t),
+                              cudaMemcpyHostToDevice, st));
+    return IDTX_OK;
+}
 
-    // Prepare every group into its slices.
+// Device part of a batch (stream operations only, so it can be captured):
+// prepare every group, reset the task counters, one persistent fused launch
+// per variant, finalise every group.  cmi: device [sum of jobs], group g's
+// slice at g.off_cmi.
+int batch_enqueue(idtx_ctx *c, const std::vector<Group> &gs, const BatchPlan &bp,
+                  cudaStream_t st, double *cmi, long long timeout_ns)
+{
+    const size_t n = gs.size(), nv = bp.vars.size();
     std::vector<int> launches(n, 0);
-    for (size_t b = 0; b < vars.size(); ++b)
-        for (size_t j = 0; j < bucket[b].size(); ++j) {
-            const int i = bucket[b][j];
-            const Slices sl{(float *)((unsigned char *)c->buf[B_SH] + off[i].sh),
-                            (float *)((unsigned char *)c->buf[B_XI] + off[i].xi),
-                            (int32_t *)((unsigned char *)c->buf[B_PERM] + off[i].perm),
-                            (double *)((unsigned char *)c->buf[B_PARTIAL] + off[i].partial),
-                            (unsigned char *)c->buf[B_ORDER] + off[i].order,
-                            (unsigned char *)c->buf[B_SORT] + off[i].sort_tmp,
-                            bytes_of(gs[i]).sort_tmp};
-            IDTX_TRY(prep_group(c, gs[i], st, sl, nullptr, nullptr, timeout_ns,
-                                probs[b_probs[b] + j], launches[i]));
-        }
-    IDTX_CUDA(cudaMemcpyAsync(probs_d, probs.data(), n * sizeof(KsgLaunch),
-                              cudaMemcpyHostToDevice, st));
-    IDTX_CUDA(cudaMemcpyAsync(start_d, start.data(), start.size() * sizeof(int64_t),
-                              cudaMemcpyHostToDevice, st));
-    IDTX_CUDA(cudaMemsetAsync(next_d, 0, cnt_bytes, st));
-
+    for (size_t i = 0; i < n; ++i) {
+        KsgLaunch unused;
+        IDTX_TRY(prep_group(c, gs[i], st, bp.sl[i], nullptr, nullptr, timeout_ns, unused,
+                            launches[i]));
+    }
+    IDTX_CUDA(cudaMemsetAsync(bp.next_d, 0, nv * sizeof(int), st));
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (c->profiling) {
         IDTX_TRY(take_event(c, &ev0));
         IDTX_TRY(take_event(c, &ev1));
         IDTX_CUDA(cudaEventRecord(ev0, st));
     }
-    for (size_t b = 0; b < vars.size(); ++b) {
+    for (size_t b = 0; b < nv; ++b) {
         KsgTable t;
-        t.probs = probs_d + b_probs[b];
-        t.start = start_d + b_start[b];
-        t.next = next_d + b;
-        t.n_probs = (int)bucket[b].size();
-        t.n_tasks = b_tasks[b];
-        IDTX_CUDA(vars[b]->fn_table(t, st));
+        t.probs = bp.probs_d + bp.b_probs[b];
+        t.start = bp.start_d + bp.b_start[b];
+        t.next = bp.next_d + b;
+        t.n_probs = (int)bp.bucket[b].size();
+        t.n_tasks = bp.b_tasks[b];
+        IDTX_CUDA(bp.vars[b]->fn_table(t, st));
     }
     if (c->profiling) {
         IDTX_CUDA(cudaEventRecord(ev1, st));
@@ -1106,14 +1161,13 @@ int enqueue_batch(idtx_ctx *c, const std::vector<Group> &gs, cudaStream_t st, do
         const Group &g = gs[i];
         const int n_jobs = (int)g.jobs.size();
         note_group(c, g, launches[i]);
-        double *partial = (double *)((unsigned char *)c->buf[B_PARTIAL] + off[i].partial);
-        k_finalize<<<(n_jobs + 127) / 128, 128, 0, st>>>(partial, n_jobs, g.n_qt, c->psi, g.k,
-                                                          g.n, cmi + g.off_cmi);
+        k_finalize<<<(n_jobs + 127) / 128, 128, 0, st>>>(bp.sl[i].partial, n_jobs, g.n_qt,
+                                                          c->psi, g.k, g.n, cmi + g.off_cmi);
         IDTX_CUDA(cudaGetLastError());
     }
     // One fused launch per variant instead of one per group.
-    c->stats.fused_launches -= (unsigned long long)(n - vars.size());
-    c->stats.kernel_launches -= (unsigned long long)(n - vars.size());
+    c->stats.fused_launches -= (int64_t)(n - nv);
+    c->stats.kernel_launches -= (int64_t)(n - nv);
     return IDTX_OK;
 }
 
@@ -1245,6 +1299,15 @@ int idtx_ctx_set_profiling(idtx_ctx *c, int enable)
     return IDTX_OK;
 }
 
+int idtx_ctx_set_graphs(idtx_ctx *c, int enable)
+{
+    if (!c) return fail(IDTX_EINVAL, "ctx is NULL");
+    DeviceGuard guard(c->device);
+    c->graphs = enable != 0;
+    if (!c->graphs) drop_graph(c);
+    return IDTX_OK;
+}
+
 int idtx_ctx_get_stats(idtx_ctx *c, idtx_stats *out)
 {
     if (!c || !out) return fail(IDTX_EINVAL, "NULL argument");
@@ -1266,8 +1329,12 @@ int idtx_ctx_destroy(idtx_ctx *c)
     cudaDeviceSynchronize();
     for (auto &pe : c->pending) c->event_pool.push_back(pe.first), c->event_pool.push_back(pe.second);
     for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
-    for (int i = 0; i < kNumBufs; ++i)
+    drop_graph(c);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    for (int i = 0; i < kNumBufs; ++i) {
         if (c->buf[i]) cudaFree(c->buf[i]);
+        if (c->gbuf[i]) cudaFree(c->gbuf[i]);
+    }
     if (c->psi) cudaFree(c->psi);
     if (c->d_err) cudaFree(c->d_err);
     if (c->h_err) cudaFreeHost(c->h_err);
@@ -1413,6 +1480,32 @@ int idtx_cmi_batch(idtx_ctx *c, const idtx_problem *probs, int n_probs, int k, d
         n_max = std::max(n_max, q.n);
         total_jobs += 1 + (size_t)q.n_surr;
     }
+    // CUDA-graph replay: same arguments as the captured call, all on the device.
+    const bool use_graph = c->graphs && !c->profiling && in_floats == 0;
+    const cudaMemcpyKind out_kind =
+        device_accessible(out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    std::vector<uint64_t> key;
+    if (use_graph) {
+        key = {(uint64_t)n_probs, (uint64_t)k, (uint64_t)(uintptr_t)stream,
+               (uint64_t)(uintptr_t)c->psi};
+        for (int p = 0; p < n_probs; ++p) {
+            const idtx_problem &q = probs[p];
+            const uint64_t w[] = {(uint64_t)(uintptr_t)q.x, (uint64_t)(uintptr_t)q.y,
+                                  (uint64_t)(uintptr_t)q.z, (uint64_t)q.dx, (uint64_t)q.dy,
+                                  (uint64_t)q.dz, (uint64_t)q.n, (uint64_t)q.ld,
+                                  (uint64_t)q.n_surr, q.seed};
+            key.insert(key.end(), w, w + 10);
+        }
+        if (c->graph_exec && key == c->graph_key) {
+            IDTX_TRY(begin_call(c, n_probs, st));
+            IDTX_CUDA(cudaGraphLaunch(c->graph_exec, st));
+            c->stats.graph_launches += 1;
+            IDTX_CUDA(cudaMemcpyAsync(out, c->gbuf[B_CMI], total_jobs * sizeof(double), out_kind,
+                                      st));
+            return finish_call(c, st);
+        }
+        drop_graph(c);
+    }
     IDTX_TRY(ensure(c, B_IN, in_floats * sizeof(float)));
     IDTX_TRY(begin_call(c, n_probs, st));
     std::vector<Group> gs(n_probs);
@@ -1456,18 +1549,74 @@ int idtx_cmi_batch(idtx_ctx *c, const idtx_problem *probs, int n_probs, int k, d
     }
     std::vector<unsigned char> arena;
     pack_desc(gs, arena);
+    const long long tmo = timeout_of(nullptr);
+    IDTX_TRY(ensure_psi(c, std::max<int64_t>(n_max, k) + 1, st));
+    if (use_graph) {
+        // Capture into a graph that owns its scratch: plan and upload on st
+        // with the graph's buffers in place, record the device work on the
+        // capture stream, launch the graph on st.
+        key[3] = (uint64_t)(uintptr_t)c->psi;
+        if (!c->cap_stream)
+            IDTX_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        swap_buffer_sets(c);
+        int rc = IDTX_OK;
+        cudaGraph_t graph = nullptr;
+        BatchPlan bp;
+        rc = ensure(c, B_DESC, arena.size());
+        if (rc == IDTX_OK) rc = ensure(c, B_CMI, total_jobs * sizeof(double));
+        if (rc == IDTX_OK) rc = ensure(c, B_WORK, (size_t)n_probs * kNumWork * 8);
+        if (rc == IDTX_OK) rc = batch_plan(c, gs, st, tmo, bp);
+        if (rc == IDTX_OK && cudaMemcpyAsync(c->buf[B_DESC], arena.data(), arena.size(),
+                                             cudaMemcpyHostToDevice, st) != cudaSuccess)
+            rc = fail(IDTX_ECUDA, "descriptor upload failed");
+        // one-time kernel attributes and occupancy queries, outside the capture
+        if (rc == IDTX_OK) rc = init_permutation_kernel();
+        for (const KsgVariant *v : bp.vars)
+            if (rc == IDTX_OK && v->fn_table(KsgTable{nullptr, nullptr, nullptr, 0, 0}, st) !=
+                                     cudaSuccess)
+                rc = fail(IDTX_ECUDA, "kernel attribute setup failed");
+        if (rc == IDTX_OK) {
+            if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) !=
+                cudaSuccess) {
+                rc = fail(IDTX_ECUDA, "stream capture could not start");
+            } else {
+                rc = batch_enqueue(c, gs, bp, c->cap_stream, (double *)c->buf[B_CMI], tmo);
+                const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+                if (rc == IDTX_OK && e != cudaSuccess)
+                    rc = fail(IDTX_ECUDA, "stream capture failed: %s", cudaGetErrorString(e));
+            }
+        }
+        if (rc == IDTX_OK) {
+            const cudaError_t e = cudaGraphInstantiate(&c->graph_exec, graph, 0);
+            if (e != cudaSuccess) {
+                c->graph_exec = nullptr;
+                rc = fail(IDTX_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+            }
+        }
+        if (graph) cudaGraphDestroy(graph);
+        swap_buffer_sets(c);
+        c->call_shapes.clear();  // the graph's work counters are not read back
+        if (rc != IDTX_OK) {
+            drop_graph(c);
+            cudaGetLastError();
+            return rc;
+        }
+        c->graph_key = key;
+        IDTX_CUDA(cudaGraphLaunch(c->graph_exec, st));
+        c->stats.graph_launches += 1;
+        IDTX_CUDA(
+            cudaMemcpyAsync(out, c->gbuf[B_CMI], total_jobs * sizeof(double), out_kind, st));
+        return finish_call(c, st);
+    }
     IDTX_TRY(ensure(c, B_DESC, arena.size()));
     IDTX_TRY(ensure(c, B_CMI, total_jobs * sizeof(double)));
-    IDTX_TRY(ensure_psi(c, std::max<int64_t>(n_max, k) + 1, st));
     IDTX_CUDA(cudaMemcpyAsync(c->buf[B_DESC], arena.data(), arena.size(), cudaMemcpyHostToDevice,
                               st));
     double *cmi_d = (double *)c->buf[B_CMI];
-    const long long tmo = timeout_of(nullptr);
-    IDTX_TRY(enqueue_batch(c, gs, st, cmi_d, tmo));
-    IDTX_CUDA(cudaMemcpyAsync(out, cmi_d, total_jobs * sizeof(double),
-                              device_accessible(out) ? cudaMemcpyDeviceToDevice
-                                                     : cudaMemcpyDeviceToHost,
-                              st));
+    BatchPlan bp;
+    IDTX_TRY(batch_plan(c, gs, st, tmo, bp));
+    IDTX_TRY(batch_enqueue(c, gs, bp, st, cmi_d, tmo));
+    IDTX_CUDA(cudaMemcpyAsync(out, cmi_d, total_jobs * sizeof(double), out_kind, st));
     return finish_call(c, st);
 }
 
