@@ -29,11 +29,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "KSG CMI estimates/s incl. surrogates (N=1e4,k=4); batched/screened vs plain"
 N_SMS = 152
-# DRAM bytes (read + write) of one fused-kernel launch of the 200-surrogate step,
-# from the ncu capture summarised in profiles/ksg_fused_kernel_greedy_step_small.md
-# (15-surrogate case, 31.68 MB, scaled by job groups 296/24).  Set to None when the
-# kernel changes until it is captured again.
-FUSED_TRAFFIC_BYTES = 390.7e6
+# DRAM bytes (read + write) per launch of the 200-surrogate step, from ncu
+# captures (profiles/), per kernel; None until the current kernel is captured.
+# Tile kernel: profiles/ksg_fused_kernel_greedy_step_small.md (15-surrogate case,
+# 31.68 MB, scaled by job groups 296/24).
+TRAFFIC_BYTES = {"tile": 390.7e6, "list": None}
 LANES_PER_SM = 128  # 4 sub-partitions x 32 lanes: one warp instruction per clock each
 
 WORKLOAD = dict(n_proc=10, order=5, T=10000, n_past=3, min_lag=1, max_lag=5, k=4, n_surr=200,
@@ -229,6 +229,27 @@ def run_ours(args):
         t_max = float(t.item())
     value = est_per_step * args.steps * world / (t_max / 1e3)
 
+    # the same step with each kernel forced (both give identical estimates)
+    kernels = {}
+    if rank == 0:
+        for name, kern in (("tile", idtx.KERNEL_TILE), ("list", idtx.KERNEL_LIST)):
+            kctx = idtx.Context(local)
+            kctx.set_kernel(kern)
+            step_k = lambda: idtx.mte_step(series_d, target, w["n_past"], w["min_lag"],
+                                           w["max_lag"], (), 0, k=w["k"], n_surr=w["n_surr"],
+                                           alpha=w["alpha"], seed=w["seed"], ctx=kctx)
+            step_k()
+            torch.cuda.synchronize()
+            k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            k0.record(stream)
+            for _ in range(2):
+                flush.fill_(1.0)
+                step_k()
+            k1.record(stream)
+            torch.cuda.synchronize()
+            kernels[name] = est_per_step * 2 / (k0.elapsed_time(k1) / 1e3)
+            del kctx
+
     # plain schedule (one launch per estimate, no sharing) on a subset of the
     # step: the same 47 candidates with 4 surrogates each (its cost per estimate
     # does not depend on the number of surrogates)
@@ -296,11 +317,14 @@ def run_ours(args):
         "sm_mhz_median", 1477.0)
     peak = N_SMS * LANES_PER_SM * sm_mhz * 1e6 / 1e12
     achieved = st["fused_lane_ops"] / (st["fused_ms"] / 1e3) / 1e12 if st["fused_ms"] else None
+    used = "list" if st["list_launches"] > 0 else "tile"
+    traffic = TRAFFIC_BYTES[used] if w["n_surr"] == 200 else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                 "frac": (achieved / peak) if achieved else None,
-                "traffic": FUSED_TRAFFIC_BYTES if w["n_surr"] == 200 and FUSED_TRAFFIC_BYTES else None,
-                "traffic_unit": "bytes per launch (ncu, scaled from the 15-surrogate case)",
-                "kernel": "ksg_fused_kernel<DX=1,DY=1,DZ=3,K1=5,exact,QC=64,NW=8>",
+                "traffic": traffic,
+                "traffic_unit": "bytes per launch (ncu)",
+                "kernel": ("ksg_list_kernel" if used == "list" else "ksg_fused_kernel") +
+                          "<DX=1,DY=1,DZ=3,K1=5,exact,QC=64,NW=8>",
                 "peak_basis": f"{N_SMS} SMs x {LANES_PER_SM} lanes x median SM clock "
                               f"{sm_mhz:.0f} MHz under load (issue-slot peak)",
                 "fused_share_of_step": st["fused_ms"] / ms if ms else None,
@@ -308,10 +332,16 @@ def run_ours(args):
                     ((st["scanned_a"] + st["scanned_b"]) / st["exhaustive_pairs"])
                     if st["exhaustive_pairs"] else None,
                 "work_per_step": {k: st[k] / args.steps for k in
-                                  ("scanned_a", "passed_a", "scanned_b", "passed_b")},
-                "ops_basis": "lane-ops the kernel's algorithm needs for the tiles it scans: "
-                             "shared scan per (query, reference, job group) plus per-job work "
-                             "for pairs passing the shared bound (counted in-kernel)"}
+                                  (("list_walk_a", "list_walk_b", "brute_samples", "fallbacks")
+                                   if used == "list" else
+                                   ("scanned_a", "passed_a", "scanned_b", "passed_b"))},
+                "ops_basis": ("lane-ops per job of the list entries each (query, group of 32 "
+                              "jobs) walks (2dx+2 in the neighbour pass, 2dx+4 in the count "
+                              "pass) and of full-scan fallback samples (counted in-kernel)")
+                             if used == "list" else
+                             ("lane-ops the kernel's algorithm needs for the tiles it scans: "
+                              "shared scan per (query, reference, job group) plus per-job work "
+                              "for pairs passing the shared bound (counted in-kernel)")}
     cpu = cpu_oracle_sample(net.series, target, budget_s=12.0) if world == 1 else None
     line = {"metric": METRIC, "value": value, "unit": "estimates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -320,6 +350,8 @@ def run_ours(args):
             "per step over all candidates and surrogates)",
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(st["kernel_launches"]), "clocks": clocks,
+            "kernels": {"chosen": used, "tile": kernels.get("tile"), "list": kernels.get("list"),
+                        "unit": "estimates/s, the same step with the kernel forced"},
             "modes": {"batched": value, "plain": plain["value"] if plain else None,
                       "batched_over_plain": value / plain["value"] if plain else None,
                       "plain_sample": plain["sample"] if plain else None,

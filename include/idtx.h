@@ -139,6 +139,16 @@ typedef struct {
     double exhaustive_pairs;
     double wait_cycles, warp_cycles;
     int64_t graph_launches;  /* calls served by replaying a captured graph */
+    /* List kernel (see idtx_ctx_set_kernel): launches, list entries walked in
+     * the neighbour pass (list A) and the count pass (list B) per (query,
+     * group of 32 jobs), samples scanned by full-scan fallbacks, fallbacks
+     * taken (a (query, group) whose lists did not cover some job), and
+     * timed trials run by the kernel choice.  fused_lane_ops of a list
+     * launch counts, per job, 2dx+2 per list A entry, 2dx+4 per list B entry
+     * and 2(dx+dy+dz')+2 / +6 per full-scan sample of the two passes. */
+    int64_t list_launches;
+    double list_walk_a, list_walk_b, brute_samples, fallbacks;
+    int64_t tune_trials;
 } idtx_stats;
 
 /* Enable (1) or disable (0) event timing of the fused kernel. */
@@ -158,6 +168,31 @@ int idtx_ctx_set_profiling(idtx_ctx *ctx, int enable);
  * counters and fused-kernel timing are not collected for replayed calls.
  * Returns IDTX_EINVAL for a NULL ctx. */
 int idtx_ctx_set_graphs(idtx_ctx *ctx, int enable);
+
+/* Which kernel computes the estimates of a call (no counterpart in the paper,
+ * whose GPU estimator is not described; both give bit-identical results):
+ *   IDTX_KERNEL_TILE: the tile kernel scans reference tiles staged into
+ *     shared memory, skipping tiles that are provably out of reach.
+ *   IDTX_KERNEL_LIST: the list kernel first sorts, once per query and for
+ *     all estimates of the call together (they share Y and Z), the samples
+ *     by their (Y,Z) and their Z distance, keeping the nearest up to a
+ *     capacity; each estimate then walks only the prefix it needs, with a
+ *     full scan for a (query, estimate) whose neighbourhood the lists do not
+ *     cover.  Needs dz >= 1 (dz = 0 calls use the tile kernel).
+ *   IDTX_KERNEL_AUTO (default): on the first call of a shape (kernel
+ *     variant, floor(log2 N)) both kernels run, timed, and the faster serves
+ *     that shape from then on in this context.
+ * Returns IDTX_EINVAL for a NULL ctx or an unknown value. */
+#define IDTX_KERNEL_AUTO 0
+#define IDTX_KERNEL_TILE 1
+#define IDTX_KERNEL_LIST 2
+int idtx_ctx_set_kernel(idtx_ctx *ctx, int kernel);
+
+/* Capacities of the list kernel's per-query lists (entries; 0 restores the
+ * defaults 2048 and 4096).  Smaller lists make full-scan fallbacks more
+ * frequent; results do not change.  cap_a, cap_b: 0 or multiples of 32 in
+ * [32, default].  Returns IDTX_EINVAL otherwise. */
+int idtx_ctx_set_list_caps(idtx_ctx *ctx, int cap_a, int cap_b);
 
 /* Read the counters accumulated since creation or the last reset. */
 int idtx_ctx_get_stats(idtx_ctx *ctx, idtx_stats *out);

@@ -29,6 +29,7 @@ _default_ctx = {}
 
 IDTX_OK, IDTX_EINVAL, IDTX_ENOMEM, IDTX_ECUDA, IDTX_ETIMEOUT, IDTX_EINTERNAL = range(6)
 MODE_BATCHED, MODE_PLAIN, MODE_SCREENED = 0, 1, 2
+KERNEL_AUTO, KERNEL_TILE, KERNEL_LIST = 0, 1, 2
 SCREEN_F, SCREEN_H = 10, 64
 SCREEN_NPARAMS = SCREEN_H * SCREEN_F + SCREEN_H + SCREEN_H * SCREEN_H + SCREEN_H + SCREEN_H + 1
 _ERR_NAMES = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EINTERNAL"}
@@ -59,7 +60,10 @@ class Stats(ctypes.Structure):
                 ("scanned_a", ctypes.c_double), ("passed_a", ctypes.c_double),
                 ("scanned_b", ctypes.c_double), ("passed_b", ctypes.c_double),
                 ("exhaustive_pairs", ctypes.c_double), ("wait_cycles", ctypes.c_double),
-                ("warp_cycles", ctypes.c_double), ("graph_launches", ctypes.c_int64)]
+                ("warp_cycles", ctypes.c_double), ("graph_launches", ctypes.c_int64),
+                ("list_launches", ctypes.c_int64), ("list_walk_a", ctypes.c_double),
+                ("list_walk_b", ctypes.c_double), ("brute_samples", ctypes.c_double),
+                ("fallbacks", ctypes.c_double), ("tune_trials", ctypes.c_int64)]
 
 
 class Step(ctypes.Structure):
@@ -115,7 +119,9 @@ def load():
         lib.idtx_ctx_set_graphs.argtypes = [vp, i32]
         lib.idtx_ctx_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
         lib.idtx_ctx_reset_stats.argtypes = [vp]
-        for name in ("idtx_screen_predict", "idtx_screen_loss_grad", "idtx_screen_train",
+        lib.idtx_ctx_set_kernel.argtypes = [vp, i32]
+        lib.idtx_ctx_set_list_caps.argtypes = [vp, i32, i32]
+        for name in ("idtx_ctx_set_kernel", "idtx_ctx_set_list_caps","idtx_screen_predict", "idtx_screen_loss_grad", "idtx_screen_train",
                      "idtx_screen_set", "idtx_ctx_set_profiling", "idtx_ctx_set_graphs",
                      "idtx_ctx_get_stats", "idtx_ctx_reset_stats",
                      "idtx_ctx_create", "idtx_ctx_destroy", "idtx_cmi_ksg", "idtx_cmi_batch",
@@ -149,15 +155,18 @@ class Context:
         """Replay a captured CUDA graph for repeated identical cmi_batch calls."""
         _check(load().idtx_ctx_set_graphs(self.handle, 1 if on else 0))
 
+    def set_kernel(self, kernel: int = KERNEL_AUTO):
+        """KERNEL_AUTO (timed choice per shape), KERNEL_TILE or KERNEL_LIST."""
+        _check(load().idtx_ctx_set_kernel(self.handle, int(kernel)))
+
+    def set_list_caps(self, cap_a: int = 0, cap_b: int = 0):
+        """Capacities of the list kernel's per-query lists (0: defaults)."""
+        _check(load().idtx_ctx_set_list_caps(self.handle, int(cap_a), int(cap_b)))
+
     def stats(self) -> dict:
         st = Stats()
         _check(load().idtx_ctx_get_stats(self.handle, ctypes.byref(st)))
-        return dict(kernel_launches=st.kernel_launches, fused_launches=st.fused_launches,
-                    fused_ms=st.fused_ms, fused_lane_ops=st.fused_lane_ops,
-                    scanned_a=st.scanned_a, passed_a=st.passed_a, scanned_b=st.scanned_b,
-                    passed_b=st.passed_b, exhaustive_pairs=st.exhaustive_pairs,
-                    wait_cycles=st.wait_cycles, warp_cycles=st.warp_cycles,
-                    graph_launches=st.graph_launches)
+        return {name: getattr(st, name) for name, _ in Stats._fields_}
 
     def reset_stats(self):
         _check(load().idtx_ctx_reset_stats(self.handle))

@@ -47,7 +47,15 @@ constexpr int kTileRows = kTJ + 2;  // samples + bounding box rows
 //   [2] pairs scanned by the count pass, [3] pairs that passed its bound,
 //   [4] SM clock cycles warps spent waiting for staged tiles, [5] cycles warps
 //   spent in the kernel (both summed over warps).
+// The list kernel (ksg_list.cuh) writes, per (query, group of jobs):
+//   [0] list A entries walked, [1] list B entries walked, [2] / [3] samples
+//   scanned by pass-A / pass-B full-scan fallbacks, [4] fallbacks taken,
+//   [5] cycles as above.
 constexpr int kNumWork = 6;
+
+// Capacities of the per-query neighbour lists (entries; multiples of 32).
+constexpr int kMaxListA = 2048;  // by d_YZ
+constexpr int kMaxListB = 4096;  // by d_Z
 
 struct KsgLaunch {
     const float *sh;
@@ -62,6 +70,13 @@ struct KsgLaunch {
     int64_t n, n_pad;
     int n_jobs, n_qt, k;
     long long timeout_ns;
+    // list kernel only (ksg_list.cuh): per query i, list_a[i * cap_a ..] and
+    // list_b[i * cap_b ..] entries (sorted sample j, distance bits) and
+    // lmeta[i] = (len_a, len_b, bits of r_a, bits of r_b)
+    const int2 *list_a;
+    const int2 *list_b;
+    const int4 *lmeta;
+    int cap_a, cap_b;
 };
 
 typedef cudaError_t (*KsgLaunchFn)(const KsgLaunch &, int n_groups, cudaStream_t);
@@ -90,7 +105,14 @@ struct KsgVariant {
     int qc;           // queries per CTA
     KsgLaunchFn fn;
     KsgTableFn fn_table;  // persistent multi-problem form
+    KsgLaunchFn fn_list;  // the same estimates over sorted neighbour lists
 };
+
+// Per-query sorted neighbour lists of a group prepared into sh (lists.cu):
+// z columns [0, dzb), y columns [dzb, dsb) of rows of dsp floats.
+size_t list_smem_bytes(int cap_a, int cap_b);
+cudaError_t build_lists(const float *sh, int dsp, int dzb, int dsb, int64_t n, int cap_a,
+                        int cap_b, int2 *list_a, int2 *list_b, int4 *meta, cudaStream_t st);
 
 // Radix sort of (key, index) pairs on the low end_bit key bits (sort.cu).
 // With tmp == nullptr only sets tmp_bytes.

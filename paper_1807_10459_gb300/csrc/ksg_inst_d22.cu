@@ -1,6 +1,6 @@
 // ksg_inst_d22.cu -- compiled specialisations of the fused KSG kernel for
 // dx = 2, dy = 2, k = 4, 32 jobs per CTA, z buckets 1..6, 8, 10, 12, 16.
-#include "ksg_kernel.cuh"
+#include "ksg_list.cuh"
 
 namespace idtx {
 

@@ -1,6 +1,6 @@
 // ksg_inst_generic.cu -- the catch-all specialisation of the fused KSG kernel:
 // any k <= 15 (runtime), dx <= 4, dy <= 4, dz <= 16 (zero-padded), 32 jobs x 16 queries per CTA, 8 warps.
-#include "ksg_kernel.cuh"
+#include "ksg_list.cuh"
 
 namespace idtx {
 

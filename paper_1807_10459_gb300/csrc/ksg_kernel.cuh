@@ -798,13 +798,4 @@ cudaError_t launch_ksg_table(const KsgTable &t, cudaStream_t stream)
     return cudaGetLastError();
 }
 
-template <int DX, int DY, int DZ, int K1, bool EXACT, int QC, int NWARPS>
-KsgVariant make_variant()
-{
-    using S = KsgShape<DX, DY, DZ, K1, EXACT, QC, NWARPS>;
-    return KsgVariant{DX, DY, DZ, K1, EXACT ? 1 : 0, S::GB, S::DSP, S::QC,
-                      &launch_ksg<DX, DY, DZ, K1, EXACT, QC, NWARPS>,
-                      &launch_ksg_table<DX, DY, DZ, K1, EXACT, QC, NWARPS>};
-}
-
 }  // namespace idtx

@@ -18,6 +18,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -590,11 +591,13 @@ enum {
     B_MLP,      // screen network work area
     B_TRAIN,    // screen training data, order, Adam moments
     B_TABLE,    // persistent multi-problem launches: problem table, task offsets, counters
+    B_LIST,     // per-query sorted neighbour lists of the list kernel
     kNumBufs
 };
 
 // Shape of one fused launch, to turn its work counters into operations.
 struct WorkShape {
+    bool list;  // the list kernel ran (else the tile kernel)
     int dx, dy, dz_eff, gb;
     double job_frac;  // real jobs / (groups * gb)
     double exhaustive_pairs;
@@ -627,6 +630,11 @@ struct idtx_ctx {
     cudaGraphExec_t graph_exec = nullptr;
     std::vector<uint64_t> graph_key;
     cudaStream_t cap_stream = nullptr;
+    // kernel choice: IDTX_KERNEL_AUTO picks per (variant, log2 N) by timing
+    // both kernels on the first call of that shape; list capacities (0: default)
+    int kernel_pref = IDTX_KERNEL_AUTO;
+    std::map<std::pair<const KsgVariant *, int>, int> tuned;  // 1: list kernel
+    int cap_a = 0, cap_b = 0;
 };
 
 void drop_graph(idtx_ctx *c)
@@ -745,7 +753,35 @@ struct Group {
     bool sort = false;   // order the samples along a Morton curve first
     bool plain = false;  // one launch per estimate (IDTX_MODE_PLAIN)
     int work_slot = 0;   // index of the group's work counters in the call
+    bool use_list = false;  // run the list kernel (ksg_list.cuh)
+    bool tune = false;      // time both kernels first (shape not tuned yet)
+    int cap_a = 0, cap_b = 0;  // list capacities
 };
+
+// Memory the lists of one group may take; larger N gets shorter lists.
+constexpr size_t kListBudget = size_t(8) << 30;
+
+size_t list_bytes(int64_t n, int cap_a, int cap_b);
+
+// List capacities for n samples (0, 0: no lists).
+void list_caps(const idtx_ctx *c, int64_t n, int &cap_a, int &cap_b)
+{
+    const int all = (int)std::min<int64_t>((n - 1 + 31) / 32 * 32, 1 << 30);
+    cap_a = std::min(c->cap_a > 0 ? c->cap_a : kMaxListA, all);
+    cap_b = std::min(c->cap_b > 0 ? c->cap_b : kMaxListB, all);
+    while (cap_a >= 64 && list_bytes(n, cap_a, cap_b) > kListBudget) {
+        cap_a = cap_a / 64 * 32;
+        cap_b = std::max(32, cap_b / 64 * 32);
+    }
+    if (list_bytes(n, cap_a, cap_b) > kListBudget) cap_a = cap_b = 0;
+}
+
+std::pair<const KsgVariant *, int> tune_key(const Group &g)
+{
+    int lg = 0;
+    while ((int64_t(1) << (lg + 1)) <= g.n) ++lg;
+    return {g.v, lg};
+}
 
 int plan(idtx_ctx *c, Group &g)
 {
@@ -758,6 +794,24 @@ int plan(idtx_ctx *c, Group &g)
     if (g.n_groups > 65535) return fail(IDTX_EINVAL, "too many estimates in one group");
     g.sort = !g.plain && g.n > 2 * kTJ;
     if (g.plain) g.n_qt = (int)(g.n_pad / kPlainThreads);
+    // The list kernel needs a Z subspace (with dz = 0 list B would hold every
+    // sample) and lists that fit the memory budget.
+    g.use_list = g.tune = false;
+    g.cap_a = g.cap_b = 0;
+    if (!g.plain && g.dz >= 1 && c->kernel_pref != IDTX_KERNEL_TILE) {
+        list_caps(c, g.n, g.cap_a, g.cap_b);
+        if (g.cap_a > 0) {
+            if (c->kernel_pref == IDTX_KERNEL_LIST) {
+                g.use_list = true;
+            } else {
+                auto it = c->tuned.find(tune_key(g));
+                if (it == c->tuned.end())
+                    g.tune = true;
+                else
+                    g.use_list = it->second == 1;
+            }
+        }
+    }
     return IDTX_OK;
 }
 
@@ -794,8 +848,15 @@ void pack_desc(std::vector<Group> &gs, std::vector<unsigned char> &arena)
 }
 
 struct CallBuffers {
-    size_t sh = 0, xi = 0, perm = 0, partial = 0, order = 0, sort_tmp = 0;
+    size_t sh = 0, xi = 0, perm = 0, partial = 0, order = 0, sort_tmp = 0, lists = 0;
 };
+
+// B_LIST layout for n queries: list_a [n][cap_a] | list_b [n][cap_b] | meta [n].
+size_t list_bytes(int64_t n, int cap_a, int cap_b)
+{
+    return align_up((size_t)n * cap_a * sizeof(int2), 256) +
+           align_up((size_t)n * cap_b * sizeof(int2), 256) + align_up((size_t)n * sizeof(int4), 256);
+}
 
 // B_ORDER layout for n samples: order | idx | keys_in | keys_out | column ranges.
 size_t order_bytes(int64_t n) { return 4 * align_up((size_t)n * 4, 256) + 256; }
@@ -814,6 +875,7 @@ CallBuffers bytes_of(const Group &g)
     b.xi = align_up((size_t)g.n_groups * g.n_pad * g.v->gb * g.v->dx * sizeof(float), 256);
     b.perm = align_up(g.slot_stream.size() * (size_t)g.n * sizeof(int32_t), 256);
     b.partial = align_up(g.jobs.size() * (size_t)g.n_qt * sizeof(double), 256);
+    if (g.use_list || g.tune) b.lists = list_bytes(g.n, g.cap_a, g.cap_b);
     return b;
 }
 
@@ -827,6 +889,7 @@ void sizes_of(const Group &g, CallBuffers &b)
     b.xi = std::max(b.xi, o.xi);
     b.perm = std::max(b.perm, o.perm);
     b.partial = std::max(b.partial, o.partial);
+    b.lists = std::max(b.lists, o.lists);
 }
 
 // Where one group's scratch lives.
@@ -838,6 +901,7 @@ struct Slices {
     unsigned char *order;
     void *sort_tmp;
     size_t sort_cap;
+    unsigned char *lists;  // B_LIST region (list groups only)
 };
 
 int take_event(idtx_ctx *c, cudaEvent_t *ev)
@@ -904,6 +968,18 @@ void fill_launch(const idtx_ctx *c, const Group &g, const Slices &sl, float *eps
     a.n_qt = g.n_qt;
     a.k = g.k;
     a.timeout_ns = timeout_ns;
+    a.list_a = nullptr;
+    a.list_b = nullptr;
+    a.lmeta = nullptr;
+    a.cap_a = g.cap_a;
+    a.cap_b = g.cap_b;
+    if ((g.use_list || g.tune) && sl.lists) {
+        const size_t oa = align_up((size_t)g.n * g.cap_a * sizeof(int2), 256);
+        const size_t ob = align_up((size_t)g.n * g.cap_b * sizeof(int2), 256);
+        a.list_a = (const int2 *)sl.lists;
+        a.list_b = (const int2 *)(sl.lists + oa);
+        a.lmeta = (const int4 *)(sl.lists + oa + ob);
+    }
 }
 
 // Enqueue the preparation of one planned group into its scratch slices
@@ -958,17 +1034,25 @@ int prep_group(idtx_ctx *c, const Group &g, cudaStream_t st, const Slices &sl, f
     IDTX_CUDA(cudaGetLastError());
     k_tile_boxes<<<(unsigned)(g.n_pad / kTJ), kTJ, 0, st>>>(sh, v.dsp, g.n);
     IDTX_CUDA(cudaGetLastError());
+    fill_launch(c, g, sl, eps_out, cnt_out, timeout_ns, a);
+    if ((g.use_list || g.tune) && !a.list_a)
+        return fail(IDTX_EINTERNAL, "list kernel chosen without a list buffer");
+    if (a.list_a) {
+        IDTX_CUDA(build_lists(sh, v.dsp, v.dz, v.dz + v.dy, g.n, g.cap_a, g.cap_b,
+                              const_cast<int2 *>(a.list_a), const_cast<int2 *>(a.list_b),
+                              const_cast<int4 *>(a.lmeta), st));
+        launches += 1;
+    }
     if (n_slots > 0) IDTX_TRY(enqueue_permutations(perm, streams, seeds, n_slots, g.n, st, launches));
     k_gather_x<<<grid_for((int64_t)g.n_groups * g.n_pad * v.gb * v.dx, 256), 256, 0, st>>>(
         xc, g.dx, v.dx, jobs, n_jobs, perm, g.n, g.n_pad, v.gb, g.n_groups, order, xi, c->d_err);
     IDTX_CUDA(cudaGetLastError());
     launches += 5;  // pack, boxes, gather, fused, finalize
-    fill_launch(c, g, sl, eps_out, cnt_out, timeout_ns, a);
     return IDTX_OK;
 }
 
 // Record a group's shape for its work counters and count its launches.
-void note_group(idtx_ctx *c, const Group &g, int launches)
+void note_group(idtx_ctx *c, const Group &g, int launches, bool list)
 {
     const int n_jobs = (int)g.jobs.size();
     if (g.plain) {
@@ -977,6 +1061,7 @@ void note_group(idtx_ctx *c, const Group &g, int launches)
         return;
     }
     WorkShape ws;
+    ws.list = list;
     ws.dx = g.dx;
     ws.dy = g.dy;
     ws.dz_eff = std::max(g.dz, 1);
@@ -987,6 +1072,31 @@ void note_group(idtx_ctx *c, const Group &g, int launches)
     c->call_shapes[g.work_slot] = ws;
     c->stats.fused_launches += 1;
     c->stats.kernel_launches += launches;
+    if (list) c->stats.list_launches += 1;
+}
+
+// Time both kernels on a prepared group (every launch writes the same
+// partial sums) and remember the faster for this (variant, log2 N).
+int tune_group(idtx_ctx *c, const Group &g, KsgLaunch a, cudaStream_t st, bool &use_list)
+{
+    a.work = nullptr;
+    cudaEvent_t ev[3];
+    for (int i = 0; i < 3; ++i) IDTX_TRY(take_event(c, &ev[i]));
+    IDTX_CUDA(cudaEventRecord(ev[0], st));
+    IDTX_CUDA(g.v->fn(a, g.n_groups, st));
+    IDTX_CUDA(cudaEventRecord(ev[1], st));
+    IDTX_CUDA(g.v->fn_list(a, g.n_groups, st));
+    IDTX_CUDA(cudaEventRecord(ev[2], st));
+    IDTX_CUDA(cudaEventSynchronize(ev[2]));
+    float t_tile = 0.0f, t_list = 0.0f;
+    IDTX_CUDA(cudaEventElapsedTime(&t_tile, ev[0], ev[1]));
+    IDTX_CUDA(cudaEventElapsedTime(&t_list, ev[1], ev[2]));
+    for (int i = 0; i < 3; ++i) c->event_pool.push_back(ev[i]);
+    use_list = t_list < t_tile;
+    c->tuned[tune_key(g)] = use_list ? 1 : 0;
+    c->stats.tune_trials += 1;
+    c->stats.kernel_launches += 2;
+    return IDTX_OK;
 }
 
 // Enqueue one planned group on the context's shared scratch.  cmi: device
@@ -996,11 +1106,14 @@ int enqueue_group(idtx_ctx *c, const Group &g, cudaStream_t st, double *cmi, flo
 {
     const Slices sl{(float *)c->buf[B_SH],       (float *)c->buf[B_XI],
                     (int32_t *)c->buf[B_PERM],   (double *)c->buf[B_PARTIAL],
-                    (unsigned char *)c->buf[B_ORDER], c->buf[B_SORT], c->cap[B_SORT]};
+                    (unsigned char *)c->buf[B_ORDER], c->buf[B_SORT], c->cap[B_SORT],
+                    (unsigned char *)c->buf[B_LIST]};
     KsgLaunch a;
     int launches = 0;
     IDTX_TRY(prep_group(c, g, st, sl, eps_out, cnt_out, timeout_ns, a, launches));
     const KsgVariant &v = *g.v;
+    bool use_list = g.use_list;
+    if (g.tune) IDTX_TRY(tune_group(c, g, a, st, use_list));
     const int n_jobs = (int)g.jobs.size();
     float *xi = sl.xi;
     double *partial = sl.partial;
@@ -1019,6 +1132,8 @@ int enqueue_group(idtx_ctx *c, const Group &g, cudaStream_t st, double *cmi, flo
                 partial + (size_t)jb * g.n_qt);
             IDTX_CUDA(cudaGetLastError());
         }
+    } else if (use_list) {
+        IDTX_CUDA(v.fn_list(a, g.n_groups, st));
     } else {
         IDTX_CUDA(v.fn(a, g.n_groups, st));
     }
@@ -1026,7 +1141,7 @@ int enqueue_group(idtx_ctx *c, const Group &g, cudaStream_t st, double *cmi, flo
         IDTX_CUDA(cudaEventRecord(ev1, st));
         c->pending.emplace_back(ev0, ev1);
     }
-    note_group(c, g, launches);
+    note_group(c, g, launches, use_list && !g.plain);
     k_finalize<<<(n_jobs + 127) / 128, 128, 0, st>>>(partial, n_jobs, g.n_qt, c->psi, g.k, g.n,
                                                       cmi);
     IDTX_CUDA(cudaGetLastError());
@@ -1042,6 +1157,7 @@ struct BatchPlan {
     std::vector<std::vector<int>> bucket;
     std::vector<size_t> b_probs, b_start;
     std::vector<int64_t> b_tasks;
+    std::vector<int> list_groups;  // run one after another on the shared B_LIST
     KsgLaunch *probs_d = nullptr;
     int64_t *start_d = nullptr;
     int *next_d = nullptr;
@@ -1071,6 +1187,9 @@ int batch_plan(idtx_ctx *c, const std::vector<Group> &gs, cudaStream_t st, long 
     IDTX_TRY(ensure(c, B_PARTIAL, tot.partial));
     IDTX_TRY(ensure(c, B_ORDER, tot.order));
     IDTX_TRY(ensure(c, B_SORT, tot.sort_tmp));
+    size_t list_max = 0;
+    for (size_t i = 0; i < n; ++i) list_max = std::max(list_max, bytes_of(gs[i]).lists);
+    IDTX_TRY(ensure(c, B_LIST, list_max));
     bp.sl.resize(n);
     for (size_t i = 0; i < n; ++i)
         bp.sl[i] = Slices{(float *)((unsigned char *)c->buf[B_SH] + off[i].sh),
@@ -1079,15 +1198,24 @@ int batch_plan(idtx_ctx *c, const std::vector<Group> &gs, cudaStream_t st, long 
                           (double *)((unsigned char *)c->buf[B_PARTIAL] + off[i].partial),
                           (unsigned char *)c->buf[B_ORDER] + off[i].order,
                           (unsigned char *)c->buf[B_SORT] + off[i].sort_tmp,
-                          bytes_of(gs[i]).sort_tmp};
+                          bytes_of(gs[i]).sort_tmp, (unsigned char *)c->buf[B_LIST]};
 
-    for (const Group &g : gs)
+    // List-kernel groups run one by one; the others form the persistent
+    // launches of their variants.
+    for (size_t i = 0; i < n; ++i) {
+        const Group &g = gs[i];
+        if (g.use_list) {
+            bp.list_groups.push_back((int)i);
+            continue;
+        }
         if (std::find(bp.vars.begin(), bp.vars.end(), g.v) == bp.vars.end()) bp.vars.push_back(g.v);
+    }
     const size_t nv = bp.vars.size();
     bp.bucket.assign(nv, {});
     for (size_t i = 0; i < n; ++i)
-        bp.bucket[std::find(bp.vars.begin(), bp.vars.end(), gs[i].v) - bp.vars.begin()].push_back(
-            (int)i);
+        if (!gs[i].use_list)
+            bp.bucket[std::find(bp.vars.begin(), bp.vars.end(), gs[i].v) - bp.vars.begin()]
+                .push_back((int)i);
     for (auto &b : bp.bucket)
         std::stable_sort(b.begin(), b.end(), [&](int x, int y) { return gs[x].n > gs[y].n; });
 
@@ -1133,6 +1261,7 @@ int batch_enqueue(idtx_ctx *c, const std::vector<Group> &gs, const BatchPlan &bp
     const size_t n = gs.size(), nv = bp.vars.size();
     std::vector<int> launches(n, 0);
     for (size_t i = 0; i < n; ++i) {
+        if (gs[i].use_list) continue;
         KsgLaunch unused;
         IDTX_TRY(prep_group(c, gs[i], st, bp.sl[i], nullptr, nullptr, timeout_ns, unused,
                             launches[i]));
@@ -1157,17 +1286,69 @@ int batch_enqueue(idtx_ctx *c, const std::vector<Group> &gs, const BatchPlan &bp
         IDTX_CUDA(cudaEventRecord(ev1, st));
         c->pending.emplace_back(ev0, ev1);
     }
+    for (int i : bp.list_groups) {
+        const Group &g = gs[i];
+        KsgLaunch a;
+        IDTX_TRY(prep_group(c, g, st, bp.sl[i], nullptr, nullptr, timeout_ns, a, launches[i]));
+        a.work = (unsigned long long *)c->buf[B_WORK] + (size_t)g.work_slot * kNumWork;
+        cudaEvent_t l0 = nullptr, l1 = nullptr;
+        if (c->profiling) {
+            IDTX_TRY(take_event(c, &l0));
+            IDTX_TRY(take_event(c, &l1));
+            IDTX_CUDA(cudaEventRecord(l0, st));
+        }
+        IDTX_CUDA(g.v->fn_list(a, g.n_groups, st));
+        if (c->profiling) {
+            IDTX_CUDA(cudaEventRecord(l1, st));
+            c->pending.emplace_back(l0, l1);
+        }
+    }
     for (size_t i = 0; i < n; ++i) {
         const Group &g = gs[i];
         const int n_jobs = (int)g.jobs.size();
-        note_group(c, g, launches[i]);
+        note_group(c, g, launches[i], g.use_list);
         k_finalize<<<(n_jobs + 127) / 128, 128, 0, st>>>(bp.sl[i].partial, n_jobs, g.n_qt,
                                                           c->psi, g.k, g.n, cmi + g.off_cmi);
         IDTX_CUDA(cudaGetLastError());
     }
-    // One fused launch per variant instead of one per group.
-    c->stats.fused_launches -= (int64_t)(n - nv);
-    c->stats.kernel_launches -= (int64_t)(n - nv);
+    // One fused launch per variant instead of one per tile-kernel group.
+    const int64_t n_tile = (int64_t)(n - bp.list_groups.size());
+    c->stats.fused_launches -= n_tile - (int64_t)nv;
+    c->stats.kernel_launches -= n_tile - (int64_t)nv;
+    return IDTX_OK;
+}
+
+// Settle the kernel choice of every group whose shape is not tuned yet, by a
+// timed trial on that group (prepared into the single-group scratch; the
+// descriptors must already be in B_DESC).  Runs outside any stream capture.
+int resolve_tuning(idtx_ctx *c, std::vector<Group> &gs, cudaStream_t st, long long timeout_ns)
+{
+    for (Group &g : gs) {
+        if (!g.tune) continue;
+        if (c->tuned.find(tune_key(g)) == c->tuned.end()) {
+            CallBuffers b;
+            sizes_of(g, b);
+            IDTX_TRY(ensure(c, B_SH, b.sh));
+            IDTX_TRY(ensure(c, B_XI, b.xi));
+            IDTX_TRY(ensure(c, B_PERM, b.perm));
+            IDTX_TRY(ensure(c, B_PARTIAL, b.partial));
+            IDTX_TRY(ensure(c, B_ORDER, b.order));
+            IDTX_TRY(ensure(c, B_SORT, b.sort_tmp));
+            IDTX_TRY(ensure(c, B_LIST, b.lists));
+            const Slices sl{(float *)c->buf[B_SH],       (float *)c->buf[B_XI],
+                            (int32_t *)c->buf[B_PERM],   (double *)c->buf[B_PARTIAL],
+                            (unsigned char *)c->buf[B_ORDER], c->buf[B_SORT], c->cap[B_SORT],
+                            (unsigned char *)c->buf[B_LIST]};
+            KsgLaunch a;
+            int launches = 0;
+            IDTX_TRY(prep_group(c, g, st, sl, nullptr, nullptr, timeout_ns, a, launches));
+            bool unused = false;
+            IDTX_TRY(tune_group(c, g, a, st, unused));
+            c->stats.kernel_launches += launches - 2;
+        }
+        g.use_list = c->tuned[tune_key(g)] == 1;
+        g.tune = false;
+    }
     return IDTX_OK;
 }
 
@@ -1216,6 +1397,25 @@ int finish_call(idtx_ctx *c, cudaStream_t st)
         const WorkShape &ws = c->call_shapes[w];
         const unsigned long long *k = c->h_work + w * kNumWork;
         const double jobs = ws.gb * ws.job_frac;
+        c->stats.exhaustive_pairs += ws.exhaustive_pairs;
+        if (ws.list) {
+            // List kernel, per job: a list A entry costs 2dx+2 (X distance,
+            // max with d_YZ, compare), a list B entry 2dx+4 (X distance, two
+            // compares, two adds); a full-scan sample 2(dx+dy+dz')+2 (pass A)
+            // or +6 (pass B).  Counters: walked A, walked B, full-scan
+            // samples of pass A, of pass B, fallbacks, cycles.
+            const double dall = 2.0 * (ws.dx + ws.dy + ws.dz_eff);
+            c->stats.fused_lane_ops += jobs * ((double)k[0] * (2.0 * ws.dx + 2.0) +
+                                               (double)k[1] * (2.0 * ws.dx + 4.0) +
+                                               (double)k[2] * (dall + 2.0) +
+                                               (double)k[3] * (dall + 6.0));
+            c->stats.list_walk_a += (double)k[0];
+            c->stats.list_walk_b += (double)k[1];
+            c->stats.brute_samples += (double)(k[2] + k[3]);
+            c->stats.fallbacks += (double)k[4];
+            c->stats.warp_cycles += (double)k[5];
+            continue;
+        }
         c->stats.fused_lane_ops += (double)k[0] * (2.0 * (ws.dy + ws.dz_eff) + 1.0) +
                                    (double)k[1] * jobs * (2.0 * ws.dx + 1.0) +
                                    (double)k[2] * (2.0 * ws.dz_eff + 1.0) +
@@ -1226,7 +1426,6 @@ int finish_call(idtx_ctx *c, cudaStream_t st)
         c->stats.passed_b += (double)k[3];
         c->stats.wait_cycles += (double)k[4];
         c->stats.warp_cycles += (double)k[5];
-        c->stats.exhaustive_pairs += ws.exhaustive_pairs;
     }
     c->call_shapes.clear();
     for (auto &pe : c->pending) {
@@ -1305,6 +1504,32 @@ int idtx_ctx_set_graphs(idtx_ctx *c, int enable)
     DeviceGuard guard(c->device);
     c->graphs = enable != 0;
     if (!c->graphs) drop_graph(c);
+    return IDTX_OK;
+}
+
+int idtx_ctx_set_kernel(idtx_ctx *c, int kernel)
+{
+    if (!c) return fail(IDTX_EINVAL, "ctx is NULL");
+    if (kernel != IDTX_KERNEL_AUTO && kernel != IDTX_KERNEL_TILE && kernel != IDTX_KERNEL_LIST)
+        return fail(IDTX_EINVAL, "unknown kernel choice %d", kernel);
+    DeviceGuard guard(c->device);
+    c->kernel_pref = kernel;
+    drop_graph(c);
+    return IDTX_OK;
+}
+
+int idtx_ctx_set_list_caps(idtx_ctx *c, int cap_a, int cap_b)
+{
+    if (!c) return fail(IDTX_EINVAL, "ctx is NULL");
+    auto bad = [](int v, int mx) { return v != 0 && (v < 32 || v > mx || v % 32 != 0); };
+    if (bad(cap_a, kMaxListA) || bad(cap_b, kMaxListB))
+        return fail(IDTX_EINVAL, "list capacities %d, %d: 0 or multiples of 32 up to %d, %d",
+                    cap_a, cap_b, kMaxListA, kMaxListB);
+    DeviceGuard guard(c->device);
+    c->cap_a = cap_a;
+    c->cap_b = cap_b;
+    c->tuned.clear();
+    drop_graph(c);
     return IDTX_OK;
 }
 
@@ -1426,6 +1651,7 @@ int idtx_cmi_ksg(idtx_ctx *c, const float *x, int dx, const float *y, int dy, co
     IDTX_TRY(ensure(c, B_PARTIAL, b.partial));
     IDTX_TRY(ensure(c, B_ORDER, b.order));
     IDTX_TRY(ensure(c, B_SORT, b.sort_tmp));
+    IDTX_TRY(ensure(c, B_LIST, b.lists));
     IDTX_TRY(ensure(c, B_CMI, (size_t)n_jobs * sizeof(double)));
     if (eps_out && !eps_dev) IDTX_TRY(ensure(c, B_EPS, (size_t)n_jobs * n * sizeof(float)));
     if (counts_out && !cnt_dev)
@@ -1551,6 +1777,14 @@ int idtx_cmi_batch(idtx_ctx *c, const idtx_problem *probs, int n_probs, int k, d
     pack_desc(gs, arena);
     const long long tmo = timeout_of(nullptr);
     IDTX_TRY(ensure_psi(c, std::max<int64_t>(n_max, k) + 1, st));
+    // Shapes met for the first time: time both kernels on them now (on the
+    // context's own buffers, before any capture).
+    if (std::any_of(gs.begin(), gs.end(), [](const Group &g) { return g.tune; })) {
+        IDTX_TRY(ensure(c, B_DESC, arena.size()));
+        IDTX_CUDA(cudaMemcpyAsync(c->buf[B_DESC], arena.data(), arena.size(),
+                                  cudaMemcpyHostToDevice, st));
+        IDTX_TRY(resolve_tuning(c, gs, st, tmo));
+    }
     if (use_graph) {
         // Capture into a graph that owns its scratch: plan and upload on st
         // with the graph's buffers in place, record the device work on the
@@ -1571,6 +1805,9 @@ int idtx_cmi_batch(idtx_ctx *c, const idtx_problem *probs, int n_probs, int k, d
             rc = fail(IDTX_ECUDA, "descriptor upload failed");
         // one-time kernel attributes and occupancy queries, outside the capture
         if (rc == IDTX_OK) rc = init_permutation_kernel();
+        if (rc == IDTX_OK && build_lists(nullptr, 4, 1, 1, 0, 0, 0, nullptr, nullptr, nullptr, st) !=
+                                 cudaSuccess)
+            rc = fail(IDTX_ECUDA, "list kernel attribute setup failed");
         for (const KsgVariant *v : bp.vars)
             if (rc == IDTX_OK && v->fn_table(KsgTable{nullptr, nullptr, nullptr, 0, 0}, st) !=
                                      cudaSuccess)
@@ -1721,6 +1958,7 @@ int idtx_mte_step(idtx_ctx *c, const float *series, int n_proc, int64_t T, int t
         IDTX_TRY(ensure(c, B_PARTIAL, b.partial));
         IDTX_TRY(ensure(c, B_ORDER, b.order));
         IDTX_TRY(ensure(c, B_SORT, b.sort_tmp));
+        IDTX_TRY(ensure(c, B_LIST, b.lists));
         IDTX_TRY(ensure(c, B_CMI, cmi_bytes));
         IDTX_CUDA(cudaMemcpyAsync(c->buf[B_DESC], arena.data(), arena.size(),
                                   cudaMemcpyHostToDevice, st));

@@ -168,6 +168,7 @@ def test_batch_is_one_launch_per_variant_and_equals_separate_calls(idtx, k):
     probs = [synth.gaussian_problem(n, dx, dy, dz, seed=40 + i)
              for i, (n, dx, dy, dz) in enumerate(shapes)]
     ctx = idtx.Context(0)
+    ctx.set_kernel(idtx.KERNEL_TILE)   # the persistent launches are the tile kernel's
     ctx.reset_stats()
     out = idtx.cmi_batch([dict(x=_dev(p.x), y=_dev(p.y), z=_dev(p.z), n_surr=9, seed=5 + i)
                           for i, p in enumerate(probs)], k=k, ctx=ctx)
