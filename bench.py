@@ -328,6 +328,7 @@ def run_ours(args):
                 "peak_basis": f"{N_SMS} SMs x {LANES_PER_SM} lanes x median SM clock "
                               f"{sm_mhz:.0f} MHz under load (issue-slot peak)",
                 "fused_share_of_step": st["fused_ms"] / ms if ms else None,
+                "list_caps": [st["list_cap_a"], st["list_cap_b"]] if used == "list" else None,
                 "scanned_fraction_of_exhaustive":
                     ((st["scanned_a"] + st["scanned_b"]) / st["exhaustive_pairs"])
                     if st["exhaustive_pairs"] else None,

@@ -149,6 +149,7 @@ typedef struct {
     int64_t list_launches;
     double list_walk_a, list_walk_b, brute_samples, fallbacks;
     int64_t tune_trials;
+    int32_t list_cap_a, list_cap_b;  /* list capacities of the last list launch */
 } idtx_stats;
 
 /* Enable (1) or disable (0) event timing of the fused kernel. */

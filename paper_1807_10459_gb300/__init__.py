@@ -63,7 +63,8 @@ class Stats(ctypes.Structure):
                 ("warp_cycles", ctypes.c_double), ("graph_launches", ctypes.c_int64),
                 ("list_launches", ctypes.c_int64), ("list_walk_a", ctypes.c_double),
                 ("list_walk_b", ctypes.c_double), ("brute_samples", ctypes.c_double),
-                ("fallbacks", ctypes.c_double), ("tune_trials", ctypes.c_int64)]
+                ("fallbacks", ctypes.c_double), ("tune_trials", ctypes.c_int64),
+                ("list_cap_a", ctypes.c_int32), ("list_cap_b", ctypes.c_int32)]
 
 
 class Step(ctypes.Structure):

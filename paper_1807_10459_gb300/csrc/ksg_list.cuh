@@ -267,8 +267,10 @@ __device__ __forceinline__ void ksg_list_cta(const KsgLaunch &a, const int qt, c
         // went on until each job's k-th value was at most the next entry).
         if (job_ok && !fb) nyz = list_lower(la, walked_a, eps);
         // List B up to the largest eps of the jobs it serves (ascending, so
-        // the walk stops at the first entry at or beyond it).
+        // the walk stops at the first entry at or beyond it); n_z is then the
+        // number of walked entries below the job's eps (binary search).
         const float emax = warp_max((job_ok && !fb) ? eps : -1.0f);
+        int walked_b = 0;
         {
             int2 nxt = len_b > 0 ? __ldg(lb + lane) : sentinel;
             for (int f = 0; f < len_b; f += 32) {
@@ -293,16 +295,15 @@ __device__ __forceinline__ void ksg_list_cta(const KsgLaunch &a, const int qt, c
 #pragma unroll
                     for (int t = 0; t < SB; ++t) dx[t] = x_dist(xq, jj[t]);
 #pragma unroll
-                    for (int t = 0; t < SB; ++t) {
-                        const bool pz = dz[t] < eps;
-                        nz += pz ? 1 : 0;
-                        nxz += (pz && dx[t] < eps) ? 1 : 0;
-                    }
+                    for (int t = 0; t < SB; ++t) nxz += (dz[t] < eps && dx[t] < eps) ? 1 : 0;
                 }
-                walk_b += u;
+                walked_b = f + u;
                 if (u < 32) break;
             }
         }
+        if (walked_b > len_b) walked_b = len_b;
+        walk_b += walked_b;
+        if (job_ok && !fb) nz = list_lower(lb, walked_b, eps);
         // Jobs whose eps reaches past a list: counts by a full scan, the 32
         // lanes splitting the samples of one such job at a time.
         uint32_t bmask = __ballot_sync(kFull, fb);

@@ -633,7 +633,11 @@ struct idtx_ctx {
     // kernel choice: IDTX_KERNEL_AUTO picks per (variant, log2 N) by timing
     // both kernels on the first call of that shape; list capacities (0: default)
     int kernel_pref = IDTX_KERNEL_AUTO;
-    std::map<std::pair<const KsgVariant *, int>, int> tuned;  // 1: list kernel
+    struct Choice {
+        bool list;         // list kernel (else tile kernel)
+        int cap_a, cap_b;  // its list capacities
+    };
+    std::map<std::pair<const KsgVariant *, int>, Choice> tuned;
     int cap_a = 0, cap_b = 0;
 };
 
@@ -805,10 +809,15 @@ int plan(idtx_ctx *c, Group &g)
                 g.use_list = true;
             } else {
                 auto it = c->tuned.find(tune_key(g));
-                if (it == c->tuned.end())
+                if (it == c->tuned.end()) {
                     g.tune = true;
-                else
-                    g.use_list = it->second == 1;
+                } else {
+                    g.use_list = it->second.list;
+                    if (g.use_list) {
+                        g.cap_a = it->second.cap_a;
+                        g.cap_b = it->second.cap_b;
+                    }
+                }
             }
         }
     }
@@ -1075,27 +1084,70 @@ void note_group(idtx_ctx *c, const Group &g, int launches, bool list)
     if (list) c->stats.list_launches += 1;
 }
 
-// Time both kernels on a prepared group (every launch writes the same
-// partial sums) and remember the faster for this (variant, log2 N).
-int tune_group(idtx_ctx *c, const Group &g, KsgLaunch a, cudaStream_t st, bool &use_list)
+// Time the candidate ways of running a prepared group -- the tile kernel, and
+// the list kernel (list building included) with the group's list capacities
+// and with two smaller ones -- and remember the fastest for this (variant,
+// log2 N).  Every candidate writes the same partial sums.  On return the
+// lists in the buffer, and a's capacities, are those of the choice.
+int tune_group(idtx_ctx *c, const Group &g, KsgLaunch &a, cudaStream_t st, bool &use_list)
 {
-    a.work = nullptr;
-    cudaEvent_t ev[3];
-    for (int i = 0; i < 3; ++i) IDTX_TRY(take_event(c, &ev[i]));
+    struct Cand {
+        bool list;
+        int ca, cb;
+        float ms;
+    };
+    std::vector<Cand> cands{{false, 0, 0, 0.0f}, {true, g.cap_a, g.cap_b, 0.0f}};
+    if (c->cap_a == 0 && c->cap_b == 0)  // capacities not fixed by the caller
+        for (int sh = 1; sh <= 2; ++sh) {
+            const int ca = (g.cap_a >> sh) / 32 * 32, cb = (g.cap_b >> sh) / 32 * 32;
+            if (ca >= 256 && cb >= 256) cands.push_back({true, ca, cb, 0.0f});
+        }
+    const KsgVariant &v = *g.v;
+    KsgLaunch t = a;
+    t.work = nullptr;
+    std::vector<cudaEvent_t> ev(cands.size() + 1);
+    for (auto &e : ev) IDTX_TRY(take_event(c, &e));
     IDTX_CUDA(cudaEventRecord(ev[0], st));
-    IDTX_CUDA(g.v->fn(a, g.n_groups, st));
-    IDTX_CUDA(cudaEventRecord(ev[1], st));
-    IDTX_CUDA(g.v->fn_list(a, g.n_groups, st));
-    IDTX_CUDA(cudaEventRecord(ev[2], st));
-    IDTX_CUDA(cudaEventSynchronize(ev[2]));
-    float t_tile = 0.0f, t_list = 0.0f;
-    IDTX_CUDA(cudaEventElapsedTime(&t_tile, ev[0], ev[1]));
-    IDTX_CUDA(cudaEventElapsedTime(&t_list, ev[1], ev[2]));
-    for (int i = 0; i < 3; ++i) c->event_pool.push_back(ev[i]);
-    use_list = t_list < t_tile;
-    c->tuned[tune_key(g)] = use_list ? 1 : 0;
+    int built_a = g.cap_a, built_b = g.cap_b;  // the lists prep_group built
+    for (size_t i = 0; i < cands.size(); ++i) {
+        const Cand &cd = cands[i];
+        if (!cd.list) {
+            IDTX_CUDA(v.fn(t, g.n_groups, st));
+        } else {
+            // the first list candidate re-times the build prep_group did
+            IDTX_CUDA(build_lists(t.sh, v.dsp, v.dz, v.dz + v.dy, g.n, cd.ca, cd.cb,
+                                  const_cast<int2 *>(t.list_a), const_cast<int2 *>(t.list_b),
+                                  const_cast<int4 *>(t.lmeta), st));
+            built_a = cd.ca;
+            built_b = cd.cb;
+            t.cap_a = cd.ca;
+            t.cap_b = cd.cb;
+            IDTX_CUDA(v.fn_list(t, g.n_groups, st));
+        }
+        IDTX_CUDA(cudaEventRecord(ev[i + 1], st));
+    }
+    IDTX_CUDA(cudaEventSynchronize(ev.back()));
+    size_t best = 0;
+    for (size_t i = 0; i < cands.size(); ++i) {
+        IDTX_CUDA(cudaEventElapsedTime(&cands[i].ms, ev[i], ev[i + 1]));
+        if (cands[i].ms < cands[best].ms) best = i;
+    }
+    for (auto &e : ev) c->event_pool.push_back(e);
+    const Cand &b = cands[best];
+    use_list = b.list;
+    c->tuned[tune_key(g)] = idtx_ctx::Choice{b.list, b.ca, b.cb};
+    if (b.list && (built_a != b.ca || built_b != b.cb)) {
+        IDTX_CUDA(build_lists(a.sh, v.dsp, v.dz, v.dz + v.dy, g.n, b.ca, b.cb,
+                              const_cast<int2 *>(a.list_a), const_cast<int2 *>(a.list_b),
+                              const_cast<int4 *>(a.lmeta), st));
+        c->stats.kernel_launches += 1;
+    }
+    if (b.list) {
+        a.cap_a = b.ca;
+        a.cap_b = b.cb;
+    }
     c->stats.tune_trials += 1;
-    c->stats.kernel_launches += 2;
+    c->stats.kernel_launches += (int64_t)(2 * cands.size() - 1);
     return IDTX_OK;
 }
 
@@ -1134,6 +1186,8 @@ int enqueue_group(idtx_ctx *c, const Group &g, cudaStream_t st, double *cmi, flo
         }
     } else if (use_list) {
         IDTX_CUDA(v.fn_list(a, g.n_groups, st));
+        c->stats.list_cap_a = a.cap_a;
+        c->stats.list_cap_b = a.cap_b;
     } else {
         IDTX_CUDA(v.fn(a, g.n_groups, st));
     }
@@ -1298,6 +1352,8 @@ int batch_enqueue(idtx_ctx *c, const std::vector<Group> &gs, const BatchPlan &bp
             IDTX_CUDA(cudaEventRecord(l0, st));
         }
         IDTX_CUDA(g.v->fn_list(a, g.n_groups, st));
+        c->stats.list_cap_a = a.cap_a;
+        c->stats.list_cap_b = a.cap_b;
         if (c->profiling) {
             IDTX_CUDA(cudaEventRecord(l1, st));
             c->pending.emplace_back(l0, l1);
@@ -1346,7 +1402,12 @@ int resolve_tuning(idtx_ctx *c, std::vector<Group> &gs, cudaStream_t st, long lo
             IDTX_TRY(tune_group(c, g, a, st, unused));
             c->stats.kernel_launches += launches - 2;
         }
-        g.use_list = c->tuned[tune_key(g)] == 1;
+        const idtx_ctx::Choice ch = c->tuned[tune_key(g)];
+        g.use_list = ch.list;
+        if (ch.list) {
+            g.cap_a = ch.cap_a;
+            g.cap_b = ch.cap_b;
+        }
         g.tune = false;
     }
     return IDTX_OK;
