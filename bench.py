@@ -32,8 +32,9 @@ N_SMS = 152
 # DRAM bytes (read + write) per launch of the 200-surrogate step, from ncu
 # captures (profiles/), per kernel; None until the current kernel is captured.
 # Tile kernel: profiles/ksg_fused_kernel_greedy_step_small.md (15-surrogate case,
-# 31.68 MB, scaled by job groups 296/24).
-TRAFFIC_BYTES = {"tile": 390.7e6, "list": None}
+# 31.68 MB, scaled by job groups 296/24).  List kernel:
+# profiles/ksg_list_kernel_greedy_step_small.md (full-size launch, captured directly).
+TRAFFIC_BYTES = {"tile": 390.7e6, "list": 2.566e9}
 LANES_PER_SM = 128  # 4 sub-partitions x 32 lanes: one warp instruction per clock each
 
 WORKLOAD = dict(n_proc=10, order=5, T=10000, n_past=3, min_lag=1, max_lag=5, k=4, n_surr=200,
@@ -189,6 +190,9 @@ def run_ours(args):
     target = rank % w["n_proc"]
     series_d = torch.from_numpy(net.series).to(dev)
     ctx = idtx.Context(local)
+    ctx.set_kernel({"auto": idtx.KERNEL_AUTO, "tile": idtx.KERNEL_TILE,
+                    "list": idtx.KERNEL_LIST}[args.kernel])
+    ctx.set_list_caps(*args.list_caps)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     est_per_step = 47 * (1 + w["n_surr"])
 
@@ -322,9 +326,10 @@ def run_ours(args):
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                 "frac": (achieved / peak) if achieved else None,
                 "traffic": traffic,
-                "traffic_unit": "bytes per launch (ncu)",
+                "traffic_unit": "DRAM bytes read + written per launch (ncu)",
                 "kernel": ("ksg_list_kernel" if used == "list" else "ksg_fused_kernel") +
-                          "<DX=1,DY=1,DZ=3,K1=5,exact,QC=64,NW=8>",
+                          ("<DX=1,DY=1,DZ=3,K1=5,exact,QC=64,NW=8,LNW=4>" if used == "list" else
+                           "<DX=1,DY=1,DZ=3,K1=5,exact,QC=64,NW=8>"),
                 "peak_basis": f"{N_SMS} SMs x {LANES_PER_SM} lanes x median SM clock "
                               f"{sm_mhz:.0f} MHz under load (issue-slot peak)",
                 "fused_share_of_step": st["fused_ms"] / ms if ms else None,
@@ -520,6 +525,10 @@ def main():
                     help="var10-step: the benchmarked greedy step (default); var50-greedy: "
                          "full inference on a 50-node VAR(3), exact vs screened; batch64: "
                          "the 64-problem uneven batch")
+    ap.add_argument("--kernel", default="auto", choices=["auto", "tile", "list"],
+                    help="estimator kernel of the timed step (auto: the library's timed choice)")
+    ap.add_argument("--list-caps", type=int, nargs=2, default=(0, 0), metavar=("A", "B"),
+                    help="list capacities of the list kernel (0 0: the library's choice)")
     ap.add_argument("--n-surr", type=int, default=WORKLOAD["n_surr"],
                     help="surrogates per candidate (200 is the benchmarked workload; smaller "
                          "values give a small case for profiling)")

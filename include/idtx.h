@@ -336,8 +336,9 @@ int idtx_screen_set(idtx_ctx *ctx, const idtx_screen *screen);
  * the device, paths where a cudaMalloc would synchronise the device, or
  * services that must not grow their footprint after start-up).
  *
- * Same estimate and surrogates as idtx_cmi_ksg (same kernels, same results),
- * without a context: it runs on the current CUDA device and takes all its
+ * Same estimate and surrogates as idtx_cmi_ksg (its preparation kernels and
+ * its tile kernel; idtx_cmi_ksg's kernels agree bit for bit, so the results
+ * are the same), without a context: it runs on the current CUDA device and takes all its
  * scratch from one fixed array of IDTX_NOALLOC_SCRATCH_BYTES bytes in device
  * memory that the library declares at file scope.  Every GPU that loads the
  * library holds that array until the process exits.

@@ -110,7 +110,6 @@ struct KsgVariant {
 
 // Per-query sorted neighbour lists of a group prepared into sh (lists.cu):
 // z columns [0, dzb), y columns [dzb, dsb) of rows of dsp floats.
-size_t list_smem_bytes(int cap_a, int cap_b);
 cudaError_t build_lists(const float *sh, int dsp, int dzb, int dsb, int64_t n, int cap_a,
                         int cap_b, int2 *list_a, int2 *list_b, int4 *meta, cudaStream_t st);
 

@@ -64,7 +64,7 @@
 #define IDTX_LIST_MINB 0
 #endif
 #ifndef IDTX_LIST_GBLK
-#define IDTX_LIST_GBLK 8
+#define IDTX_LIST_GBLK 32
 #endif
 
 namespace idtx {

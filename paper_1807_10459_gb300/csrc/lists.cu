@@ -10,7 +10,10 @@
 // capacities (+inf when every sample fits).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
+
+#include <cub/block/block_radix_sort.cuh>
 
 #include "ksg_common.cuh"
 
@@ -67,36 +70,50 @@ __device__ int cut_bin(const int *hist, int cap, int *s_part, int *s_cut)
     return r;
 }
 
-// Ascending bitonic sort of keys[0..p), p a power of two.
-__device__ void bitonic_sort(unsigned long long *keys, int p)
+// Sort the n collected (distance bits, sample) pairs of one list ascending by
+// distance and write them, then +inf sentinels up to a multiple of 32 (at
+// most cap), to out.  Ties may land in any order: nothing downstream depends
+// on the order of equal distances.  The pairs are first taken into
+// registers, so the sort's scratch may overlay the collection buffers
+// (tmp); all threads of the block call it.
+template <int ITEMS>
+__device__ void sort_and_store(const uint32_t *keys, const int32_t *vals, int n, int cap,
+                               void *tmp, int2 *out)
 {
-    for (int size = 2; size <= p; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int t = threadIdx.x; t < (p >> 1); t += blockDim.x) {
-                const int lo = 2 * t - (t & (stride - 1));
-                const int hi = lo + stride;
-                const bool asc = (lo & size) == 0;
-                const unsigned long long x = keys[lo], y = keys[hi];
-                if ((x > y) == asc) {
-                    keys[lo] = y;
-                    keys[hi] = x;
-                }
-            }
-            __syncthreads();
-        }
+    using Sort = cub::BlockRadixSort<uint32_t, kLThreads, ITEMS, int32_t>;
+    uint32_t k[ITEMS];
+    int32_t v[ITEMS];
+    const int t0 = threadIdx.x * ITEMS;
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        const int at = t0 + i;
+        k[i] = at < n ? keys[at] : 0xFFFFFFFFu;
+        v[i] = at < n ? vals[at] : 0;
     }
+    __syncthreads();  // the collection buffers may now be overwritten
+    Sort(*reinterpret_cast<typename Sort::TempStorage *>(tmp)).Sort(k, v, 0, 32);
+    const int end = min(cap, (n + 31) & ~31);
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        const int at = t0 + i;
+        if (at < end)
+            out[at] = at < n ? make_int2(v[i], (int)k[i]) : make_int2(0, __float_as_int(INFINITY));
+    }
+    __syncthreads();
 }
 
-__device__ __forceinline__ int pow2_at_least(int v)
+template <int ITEMS>
+constexpr size_t sort_tmp_bytes()
 {
-    int p = 1;
-    while (p < v) p <<= 1;
-    return p;
+    return sizeof(typename cub::BlockRadixSort<uint32_t, kLThreads, ITEMS, int32_t>::TempStorage);
 }
 
-// One block per query.  Dynamic shared memory: max(2 * kBins ints,
-// (pow2(cap_a) + pow2(cap_b)) keys); the key arrays reuse the histograms.
-__global__ void __launch_bounds__(kLThreads)
+// One block per query.  Dynamic shared memory (build_smem): the two
+// histograms, later overlaid by the collected keys and samples of both
+// lists, later by the sort's scratch.  IA, IB: sort items per thread
+// (kLThreads * IA >= cap_a, kLThreads * IB >= cap_b).
+template <int IA, int IB>
+__global__ void __launch_bounds__(kLThreads, 3)
     k_build_lists(const float *sh, int dsp, int dzb, int dsb, int64_t n, int cap_a, int cap_b,
                   int2 *list_a, int2 *list_b, int4 *meta)
 {
@@ -127,10 +144,11 @@ __global__ void __launch_bounds__(kLThreads)
     const float r_a = cut_a >= kBins ? INFINITY : __uint_as_float((unsigned)cut_a << kBinShift);
     const float r_b = cut_b >= kBins ? INFINITY : __uint_as_float((unsigned)cut_b << kBinShift);
 
-    // Collect the samples below the cuts (order of arrival), then sort.
-    const int pa = pow2_at_least(cap_a);
-    unsigned long long *keys_a = reinterpret_cast<unsigned long long *>(l_smem);
-    unsigned long long *keys_b = keys_a + pa;
+    // Collect the samples below the cuts (in order of arrival).
+    uint32_t *key_a = reinterpret_cast<uint32_t *>(l_smem);
+    int32_t *val_a = reinterpret_cast<int32_t *>(key_a + kLThreads * IA);
+    uint32_t *key_b = reinterpret_cast<uint32_t *>(val_a + kLThreads * IA);
+    int32_t *val_b = reinterpret_cast<int32_t *>(key_b + kLThreads * IB);
     if (tid < 2) s_cnt[tid] = 0;
     __syncthreads();  // histograms are dead from here on
     for (int64_t j = tid; j < n; j += kLThreads) {
@@ -139,66 +157,95 @@ __global__ void __launch_bounds__(kLThreads)
         dists(s_q, row_of(j), dzb, dsb, dz, dyz);
         if (dyz < r_a) {
             const int at = atomicAdd(&s_cnt[0], 1);
-            if (at < cap_a) keys_a[at] = ((unsigned long long)__float_as_uint(dyz) << 32) | (uint32_t)j;
+            if (at < cap_a) {
+                key_a[at] = __float_as_uint(dyz);
+                val_a[at] = (int32_t)j;
+            }
         }
         if (dz < r_b) {
             const int at = atomicAdd(&s_cnt[1], 1);
-            if (at < cap_b) keys_b[at] = ((unsigned long long)__float_as_uint(dz) << 32) | (uint32_t)j;
+            if (at < cap_b) {
+                key_b[at] = __float_as_uint(dz);
+                val_b[at] = (int32_t)j;
+            }
         }
     }
     __syncthreads();
     const int na = min(s_cnt[0], cap_a), nb = min(s_cnt[1], cap_b);
-    const int p_a = pow2_at_least(max(na, 1)), p_b = pow2_at_least(max(nb, 1));
-    for (int t = na + tid; t < p_a; t += kLThreads) keys_a[t] = ~0ull;
-    for (int t = nb + tid; t < p_b; t += kLThreads) keys_b[t] = ~0ull;
-    __syncthreads();
-    bitonic_sort(keys_a, p_a);
-    bitonic_sort(keys_b, p_b);
-
-    // Entries, then +inf sentinels up to a multiple of 32 (the walks read 32
-    // entries at a time; capacities are multiples of 32).
-    const int2 sentinel = make_int2(0, __float_as_int(INFINITY));
-    int2 *la = list_a + i * cap_a;
-    int2 *lb = list_b + i * cap_b;
-    const int end_a = min(cap_a, (na + 31) & ~31), end_b = min(cap_b, (nb + 31) & ~31);
-    for (int t = tid; t < end_a; t += kLThreads)
-        la[t] = t < na ? make_int2((int)(uint32_t)keys_a[t], (int)(keys_a[t] >> 32)) : sentinel;
-    for (int t = tid; t < end_b; t += kLThreads)
-        lb[t] = t < nb ? make_int2((int)(uint32_t)keys_b[t], (int)(keys_b[t] >> 32)) : sentinel;
-    if (tid == 0)
-        meta[i] = make_int4(na, nb, __float_as_int(r_a), __float_as_int(r_b));
+    // List B first: its pairs go to registers, then its scratch overlays
+    // list B's buffers (list A's stay intact below them).
+    sort_and_store<IB>(key_b, val_b, nb, cap_b, key_b, list_b + i * cap_b);
+    sort_and_store<IA>(key_a, val_a, na, cap_a, key_a, list_a + i * cap_a);
+    if (tid == 0) meta[i] = make_int4(na, nb, __float_as_int(r_a), __float_as_int(r_b));
 }
 
-}  // namespace
-
-size_t list_smem_bytes(int cap_a, int cap_b)
+// Items per thread covering a capacity (a power of two, at least 1).
+int items_for(int cap)
 {
-    auto p2 = [](int v) {
-        int p = 1;
-        while (p < v) p <<= 1;
-        return p;
-    };
-    const size_t keys = (size_t)(p2(cap_a) + p2(cap_b)) * sizeof(unsigned long long);
-    const size_t hist = 2 * (size_t)kBins * sizeof(int);
-    return keys > hist ? keys : hist;
+    int it = 1;
+    while (it * kLThreads < cap) it <<= 1;
+    return it;
 }
 
-cudaError_t build_lists(const float *sh, int dsp, int dzb, int dsb, int64_t n, int cap_a,
-                        int cap_b, int2 *list_a, int2 *list_b, int4 *meta, cudaStream_t st)
+// Shared memory of k_build_lists<ia, ib>: the histograms, or the collected
+// pairs of both lists, or list A's pairs plus list B's sort scratch,
+// whichever is largest.
+size_t build_smem(int ia, int ib, size_t tmp_b, size_t tmp_a)
+{
+    const size_t hist = 2 * (size_t)kBins * sizeof(int);
+    const size_t pairs_a = (size_t)kLThreads * ia * 8, pairs_b = (size_t)kLThreads * ib * 8;
+    size_t m = hist;
+    m = std::max(m, pairs_a + pairs_b);
+    m = std::max(m, pairs_a + tmp_b);
+    m = std::max(m, tmp_a);
+    return (m + 15) & ~size_t(15);
+}
+
+template <int IA, int IB>
+cudaError_t launch_build(const float *sh, int dsp, int dzb, int dsb, int64_t n, int cap_a,
+                         int cap_b, int2 *list_a, int2 *list_b, int4 *meta, cudaStream_t st)
 {
     static bool attr_set = false;  // per process; the attribute is per function
-    const size_t smem = list_smem_bytes(kMaxListA, kMaxListB);
+    const size_t smem = build_smem(IA, IB, sort_tmp_bytes<IB>(), sort_tmp_bytes<IA>());
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_build_lists,
+        cudaError_t e = cudaFuncSetAttribute(k_build_lists<IA, IB>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     if (n <= 0) return cudaSuccess;
-    k_build_lists<<<(unsigned)n, kLThreads, list_smem_bytes(cap_a, cap_b), st>>>(
-        sh, dsp, dzb, dsb, n, cap_a, cap_b, list_a, list_b, meta);
+    k_build_lists<IA, IB><<<(unsigned)n, kLThreads, smem, st>>>(sh, dsp, dzb, dsb, n, cap_a,
+                                                                 cap_b, list_a, list_b, meta);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t build_lists(const float *sh, int dsp, int dzb, int dsb, int64_t n, int cap_a,
+                        int cap_b, int2 *list_a, int2 *list_b, int4 *meta, cudaStream_t st)
+{
+    // One instantiation per size class s: list A up to 128 s entries, list B
+    // up to 256 s (s = 2, 4, 8, 16).
+    int s = std::max(items_for(cap_b), 2 * items_for(cap_a));
+    s = std::max(s, 2);
+    if (n <= 0) {  // set-up only: every instantiation's attribute (outside captures)
+        cudaError_t e = launch_build<1, 2>(sh, dsp, dzb, dsb, 0, 0, 0, nullptr, nullptr, nullptr, st);
+        if (e == cudaSuccess) e = launch_build<2, 4>(sh, dsp, dzb, dsb, 0, 0, 0, nullptr, nullptr, nullptr, st);
+        if (e == cudaSuccess) e = launch_build<4, 8>(sh, dsp, dzb, dsb, 0, 0, 0, nullptr, nullptr, nullptr, st);
+        if (e == cudaSuccess) e = launch_build<8, 16>(sh, dsp, dzb, dsb, 0, 0, 0, nullptr, nullptr, nullptr, st);
+        return e;
+    }
+    switch (s) {
+    case 2:
+        return launch_build<1, 2>(sh, dsp, dzb, dsb, n, cap_a, cap_b, list_a, list_b, meta, st);
+    case 4:
+        return launch_build<2, 4>(sh, dsp, dzb, dsb, n, cap_a, cap_b, list_a, list_b, meta, st);
+    case 8:
+        return launch_build<4, 8>(sh, dsp, dzb, dsb, n, cap_a, cap_b, list_a, list_b, meta, st);
+    default:
+        return launch_build<8, 16>(sh, dsp, dzb, dsb, n, cap_a, cap_b, list_a, list_b, meta, st);
+    }
 }
 
 }  // namespace idtx

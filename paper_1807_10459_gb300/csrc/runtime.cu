@@ -630,6 +630,7 @@ struct idtx_ctx {
     cudaGraphExec_t graph_exec = nullptr;
     std::vector<uint64_t> graph_key;
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t side_stream = nullptr;  // second stream of a call (prep_group)
     // kernel choice: IDTX_KERNEL_AUTO picks per (variant, log2 N) by timing
     // both kernels on the first call of that shape; list capacities (0: default)
     int kernel_pref = IDTX_KERNEL_AUTO;
@@ -1046,16 +1047,33 @@ int prep_group(idtx_ctx *c, const Group &g, cudaStream_t st, const Slices &sl, f
     fill_launch(c, g, sl, eps_out, cnt_out, timeout_ns, a);
     if ((g.use_list || g.tune) && !a.list_a)
         return fail(IDTX_EINTERNAL, "list kernel chosen without a list buffer");
+    // The permutations and the X gather do not depend on the lists: with
+    // lists to build they run on the context's second stream, forked from st
+    // after the sample order is known and joined back before the estimator.
+    cudaStream_t xs = st;
+    cudaEvent_t fork = nullptr, join = nullptr;
     if (a.list_a) {
+        IDTX_TRY(take_event(c, &fork));
+        IDTX_TRY(take_event(c, &join));
+        IDTX_CUDA(cudaEventRecord(fork, st));
+        IDTX_CUDA(cudaStreamWaitEvent(c->side_stream, fork, 0));
+        xs = c->side_stream;
+    }
+    if (n_slots > 0) IDTX_TRY(enqueue_permutations(perm, streams, seeds, n_slots, g.n, xs, launches));
+    k_gather_x<<<grid_for((int64_t)g.n_groups * g.n_pad * v.gb * v.dx, 256), 256, 0, xs>>>(
+        xc, g.dx, v.dx, jobs, n_jobs, perm, g.n, g.n_pad, v.gb, g.n_groups, order, xi, c->d_err);
+    IDTX_CUDA(cudaGetLastError());
+    if (a.list_a) {
+        IDTX_CUDA(cudaEventRecord(join, xs));
         IDTX_CUDA(build_lists(sh, v.dsp, v.dz, v.dz + v.dy, g.n, g.cap_a, g.cap_b,
                               const_cast<int2 *>(a.list_a), const_cast<int2 *>(a.list_b),
                               const_cast<int4 *>(a.lmeta), st));
+        IDTX_CUDA(cudaStreamWaitEvent(st, join, 0));
+        // a later record of these events does not disturb the waits above
+        c->event_pool.push_back(fork);
+        c->event_pool.push_back(join);
         launches += 1;
     }
-    if (n_slots > 0) IDTX_TRY(enqueue_permutations(perm, streams, seeds, n_slots, g.n, st, launches));
-    k_gather_x<<<grid_for((int64_t)g.n_groups * g.n_pad * v.gb * v.dx, 256), 256, 0, st>>>(
-        xc, g.dx, v.dx, jobs, n_jobs, perm, g.n, g.n_pad, v.gb, g.n_groups, order, xi, c->d_err);
-    IDTX_CUDA(cudaGetLastError());
     launches += 5;  // pack, boxes, gather, fused, finalize
     return IDTX_OK;
 }
@@ -1544,6 +1562,7 @@ int idtx_ctx_create(idtx_ctx **out, int device)
     c->variants.assign(tmp, tmp + n);
     cudaError_t e = cudaMalloc(&c->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         idtx_ctx_destroy(c);
         return fail(IDTX_ENOMEM, "context allocation failed: %s", cudaGetErrorString(e));
@@ -1617,6 +1636,7 @@ int idtx_ctx_destroy(idtx_ctx *c)
     for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
     drop_graph(c);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->side_stream) cudaStreamDestroy(c->side_stream);
     for (int i = 0; i < kNumBufs; ++i) {
         if (c->buf[i]) cudaFree(c->buf[i]);
         if (c->gbuf[i]) cudaFree(c->gbuf[i]);
@@ -1866,6 +1886,14 @@ int idtx_cmi_batch(idtx_ctx *c, const idtx_problem *probs, int n_probs, int k, d
             rc = fail(IDTX_ECUDA, "descriptor upload failed");
         // one-time kernel attributes and occupancy queries, outside the capture
         if (rc == IDTX_OK) rc = init_permutation_kernel();
+        // events for the fork and join of every group, created before the capture
+        for (size_t i = c->event_pool.size(); rc == IDTX_OK && i < 2 * gs.size() + 4; ++i) {
+            cudaEvent_t ev = nullptr;
+            if (cudaEventCreate(&ev) != cudaSuccess)
+                rc = fail(IDTX_ECUDA, "event creation failed");
+            else
+                c->event_pool.push_back(ev);
+        }
         if (rc == IDTX_OK && build_lists(nullptr, 4, 1, 1, 0, 0, 0, nullptr, nullptr, nullptr, st) !=
                                  cudaSuccess)
             rc = fail(IDTX_ECUDA, "list kernel attribute setup failed");
@@ -2414,7 +2442,8 @@ int idtx_mte_select_target(idtx_ctx *c, const float *series, int n_proc, int64_t
 // caller's memory pool owns the device and forbids other allocations, code
 // on a path where a cudaMalloc would synchronise the device (and so stall
 // other work), or long-running services that must not grow their footprint
-// after start-up.  It runs the same kernels as idtx_cmi_ksg, with every
+// after start-up.  It runs idtx_cmi_ksg's preparation kernels and its tile
+// kernel (the list kernel's lists would not fit a fixed array), with every
 // scratch buffer carved out of one file-scope device array instead.
 namespace {
 
