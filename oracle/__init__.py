@@ -84,6 +84,13 @@ def _load():
         lib.orc_mlp_loss_grad.argtypes = [_F32P, ctypes.c_int, ctypes.c_int, _F32P, _F32P, _F32P,
                                           _F32P, ctypes.c_int64, ctypes.c_int, ctypes.c_double,
                                           _F64P, _F64P]
+        post = [_F32P, ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                ctypes.c_int, _I32P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                ctypes.c_uint64]
+        lib.orc_prune.argtypes = post + [_I32P, ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(OrcStep), ctypes.POINTER(ctypes.c_int)]
+        lib.orc_omnibus.argtypes = post + [_F64P, _F64P, ctypes.POINTER(ctypes.c_int)]
+        lib.orc_seqmax.argtypes = post + [_F64P, _F64P, _I32P]
         lib.orc_num_threads.restype = ctypes.c_int
         lib.orc_set_num_threads.argtypes = [ctypes.c_int]
         _lib = lib
@@ -223,6 +230,65 @@ def select_target(series, target: int, n_past: int, min_lag: int, max_lag: int, 
                 steps=[(steps[i].cand, bool(steps[i].significant), steps[i].stat, steps[i].pval)
                        for i in range(n_steps.value)],
                 first_step=est)
+
+
+def _post_args(series, parents):
+    s = np.ascontiguousarray(np.asarray(series, np.float32))
+    par = np.ascontiguousarray(np.asarray(parents, np.int32))
+    return s, par
+
+
+def prune(series, target: int, n_past: int, min_lag: int, max_lag: int, parents, k: int,
+          n_surr: int, alpha: float, seed: int):
+    """Minimum-statistic pruning of a selected parent list.
+
+    Returns dict(kept=[cand ids], rounds=[(cand at the minimum, significant, T_min, p)])."""
+    s, par = _post_args(series, parents)
+    m = len(par)
+    kept = np.zeros(max(1, m), np.int32)
+    n_kept = ctypes.c_int()
+    rounds = (OrcStep * max(1, m))()
+    n_rounds = ctypes.c_int()
+    rc = _load().orc_prune(_fp(s), s.shape[0], s.shape[1], target, n_past, min_lag, max_lag,
+                           par.ctypes.data_as(_I32P), m, k, n_surr, alpha, ctypes.c_uint64(seed),
+                           kept.ctypes.data_as(_I32P), ctypes.byref(n_kept), rounds,
+                           ctypes.byref(n_rounds))
+    if rc != 0:
+        raise ValueError("orc_prune: invalid arguments")
+    return dict(kept=[int(c) for c in kept[:n_kept.value]],
+                rounds=[(rounds[i].cand, bool(rounds[i].significant), rounds[i].stat,
+                         rounds[i].pval) for i in range(n_rounds.value)])
+
+
+def omnibus(series, target: int, n_past: int, min_lag: int, max_lag: int, parents, k: int,
+            n_surr: int, alpha: float, seed: int):
+    """Omnibus test of a parent set: (stat, p, significant)."""
+    s, par = _post_args(series, parents)
+    stat, pval, sig = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+    rc = _load().orc_omnibus(_fp(s), s.shape[0], s.shape[1], target, n_past, min_lag, max_lag,
+                             par.ctypes.data_as(_I32P), len(par), k, n_surr, alpha,
+                             ctypes.c_uint64(seed), ctypes.byref(stat), ctypes.byref(pval),
+                             ctypes.byref(sig))
+    if rc != 0:
+        raise ValueError("orc_omnibus: invalid arguments")
+    return stat.value, pval.value, bool(sig.value)
+
+
+def seqmax(series, target: int, n_past: int, min_lag: int, max_lag: int, parents, k: int,
+           n_surr: int, alpha: float, seed: int):
+    """Sequential maximum statistic: (stats [m], pvals [m], significant [m]) by parent."""
+    s, par = _post_args(series, parents)
+    m = len(par)
+    stats = np.zeros(m, np.float64)
+    pvals = np.zeros(m, np.float64)
+    sig = np.zeros(m, np.int32)
+    rc = _load().orc_seqmax(_fp(s), s.shape[0], s.shape[1], target, n_past, min_lag, max_lag,
+                            par.ctypes.data_as(_I32P), m, k, n_surr, alpha, ctypes.c_uint64(seed),
+                            stats.ctypes.data_as(_F64P), pvals.ctypes.data_as(_F64P),
+                            sig.ctypes.data_as(_I32P))
+    if rc != 0:
+        raise ValueError("orc_seqmax: invalid arguments")
+    return stats, pvals, sig.astype(bool)
 
 
 def num_threads() -> int:

@@ -404,6 +404,238 @@ int orc_select_target(const float *series, int n_proc, int64_t T, int target, in
     return rc;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Tests after the greedy selection (Summary, paragraph 3: the errors of     */
+/* testing many sources must be controlled; the paper describes no test).    */
+/* Readings, for a target, its past Z0 (lags 1..n_past) and a selected       */
+/* parent list P = (c_0, ..., c_{m-1}) of candidate ids:                     */
+/*   - leave-one-out statistic of parent i:                                  */
+/*       T_i = I(X_{c_i}; Y | Z0, X_{c_j} for j != i, in list order),        */
+/*     its surrogate s permutes X_{c_i} with stream tag | c_i<<24 | s;       */
+/*   - pruning (minimum statistic): T_min = min_i T_i (ties: lowest i),      */
+/*     p = #{s : min_i T_i,s >= T_min} / S; if p >= alpha the parent at the  */
+/*     minimum is removed and the test repeats on the rest (round r uses     */
+/*     tag 0x9000+r in the top 16 bits); it stops at the first significant   */
+/*     round or when no parent is left;                                      */
+/*   - omnibus: T = I(X_P; Y | Z0) with X_P all selected parents jointly;    */
+/*     surrogate s permutes the rows of X_P (one permutation for all its     */
+/*     columns), stream 0xA000<<48 | 0xFFFFFF<<24 | s; p = #{s : T_s >= T}/S;*/
+/*   - sequential maximum statistic: parents in decreasing order of T_i      */
+/*     (ties: lowest i first), tag 0xB000; the r-th is tested against the    */
+/*     surrogate maxima over itself and the parents after it,                */
+/*     p_r = #{s : max_{j at or after r} T_j,s >= T_(r)} / S; parents are    */
+/*     significant down to the first p_r >= alpha, none after it.            */
+/* Pinned by: an independent noise source added to true parents is pruned   */
+/* and the true parents kept; the omnibus test of true parents is            */
+/* significant and of independent noise is not; with one parent the three   */
+/* statistics equal the greedy step's estimate of that candidate.            */
+/* ------------------------------------------------------------------------ */
+#define ORC_TAG_PRUNE 0x9000u
+#define ORC_TAG_OMNIBUS 0xA000u
+#define ORC_TAG_SEQMAX 0xB000u
+
+static int orc_post_args_ok(const float *series, int n_proc, int64_t T, int target, int n_past,
+                            int min_lag, int max_lag, const int32_t *parents, int m, int k,
+                            int n_surr)
+{
+    if (!series || n_proc < 1 || target < 0 || target >= n_proc || n_past < 0 || min_lag < 1 ||
+        max_lag < min_lag || k < 1 || n_surr < 1 || m < 1 || !parents)
+        return 0;
+    int n_lags = max_lag - min_lag + 1;
+    for (int i = 0; i < m; ++i)
+        if (parents[i] < 0 || parents[i] >= n_proc * n_lags) return 0;
+    int64_t L = max_lag > n_past ? max_lag : n_past;
+    return T - L >= (int64_t)k + 1;
+}
+
+/* est[i*(1+S) + 0] = T_i, est[i*(1+S) + 1 + s] = its surrogate s. */
+static int orc_loo_estimates(const float *series, int n_proc, int64_t T, int target, int n_past,
+                             int min_lag, int max_lag, const int32_t *parents, int m, int k,
+                             int n_surr, uint64_t seed, uint64_t tag, double *est)
+{
+    (void)n_proc;
+    int n_lags = max_lag - min_lag + 1;
+    int64_t L = max_lag > n_past ? max_lag : n_past;
+    int64_t n = T - L;
+    int dz = n_past + m - 1;
+    float *y = (float *)malloc(sizeof(float) * (size_t)n);
+    float *z = (float *)malloc(sizeof(float) * (size_t)n * (size_t)(dz > 0 ? dz : 1));
+    float *xc = (float *)malloc(sizeof(float) * (size_t)n);
+    float *xs = (float *)malloc(sizeof(float) * (size_t)n);
+    int64_t *pi = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    orc_gather_lag(series, T, target, 0, L, y);
+    int rc = 0;
+    for (int i = 0; i < m && rc == 0; ++i) {
+        int d = 0;
+        for (int lag = 1; lag <= n_past; ++lag) orc_gather_lag(series, T, target, lag, L, z + (int64_t)d++ * n);
+        for (int j = 0; j < m; ++j)
+            if (j != i)
+                orc_gather_lag(series, T, parents[j] / n_lags, min_lag + parents[j] % n_lags, L,
+                               z + (int64_t)d++ * n);
+        int c = parents[i];
+        orc_gather_lag(series, T, c / n_lags, min_lag + c % n_lags, L, xc);
+        double *row = est + (int64_t)i * (1 + n_surr);
+        rc |= orc_cmi_ksg(xc, 1, y, 1, z, dz, n, n, k, &row[0], NULL, NULL);
+        for (int s = 0; s < n_surr && rc == 0; ++s) {
+            uint64_t stream = (tag << 48) | ((uint64_t)c << 24) | (uint64_t)s;
+            orc_perm(seed, stream, n, pi);
+            orc_permute_rows(xc, 1, n, n, pi, xs);
+            rc |= orc_cmi_ksg(xs, 1, y, 1, z, dz, n, n, k, &row[1 + s], NULL, NULL);
+        }
+    }
+    free(y);
+    free(z);
+    free(xc);
+    free(xs);
+    free(pi);
+    return rc;
+}
+
+/* Pruning.  kept[0..n_kept) = surviving parents in their original order;
+ * rounds[r] = (cand removed or kept at the minimum, significant, T_min, p). */
+int orc_prune(const float *series, int n_proc, int64_t T, int target, int n_past, int min_lag,
+              int max_lag, const int32_t *parents, int n_parents, int k, int n_surr, double alpha,
+              uint64_t seed, int32_t *kept, int *n_kept, orc_step *rounds, int *n_rounds)
+{
+    if (!orc_post_args_ok(series, n_proc, T, target, n_past, min_lag, max_lag, parents, n_parents,
+                          k, n_surr) ||
+        !kept || !n_kept || !rounds || !n_rounds)
+        return -1;
+    int m = n_parents;
+    memcpy(kept, parents, sizeof(int32_t) * (size_t)m);
+    double *est = (double *)malloc(sizeof(double) * (size_t)m * (size_t)(1 + n_surr));
+    int r = 0, rc = 0;
+    while (m > 0) {
+        rc = orc_loo_estimates(series, n_proc, T, target, n_past, min_lag, max_lag, kept, m, k,
+                               n_surr, seed, ORC_TAG_PRUNE + (uint64_t)r, est);
+        if (rc) break;
+        int at = 0;
+        for (int i = 1; i < m; ++i)
+            if (est[(int64_t)i * (1 + n_surr)] < est[(int64_t)at * (1 + n_surr)]) at = i;
+        double t_min = est[(int64_t)at * (1 + n_surr)];
+        int count = 0;
+        for (int s = 0; s < n_surr; ++s) {
+            double mn = INFINITY;
+            for (int i = 0; i < m; ++i) {
+                double v = est[(int64_t)i * (1 + n_surr) + 1 + s];
+                if (v < mn) mn = v;
+            }
+            if (mn >= t_min) ++count;
+        }
+        double pval = (double)count / (double)n_surr;
+        int sig = pval < alpha;
+        rounds[r].cand = kept[at];
+        rounds[r].significant = sig;
+        rounds[r].stat = t_min;
+        rounds[r].pval = pval;
+        ++r;
+        if (sig) break;
+        for (int i = at; i + 1 < m; ++i) kept[i] = kept[i + 1];
+        --m;
+    }
+    free(est);
+    *n_kept = m;
+    *n_rounds = r;
+    return rc;
+}
+
+/* Omnibus test of the whole parent set. */
+int orc_omnibus(const float *series, int n_proc, int64_t T, int target, int n_past, int min_lag,
+                int max_lag, const int32_t *parents, int n_parents, int k, int n_surr,
+                double alpha, uint64_t seed, double *stat, double *pval, int *significant)
+{
+    if (!orc_post_args_ok(series, n_proc, T, target, n_past, min_lag, max_lag, parents, n_parents,
+                          k, n_surr) ||
+        !stat || !pval || !significant)
+        return -1;
+    int n_lags = max_lag - min_lag + 1;
+    int64_t L = max_lag > n_past ? max_lag : n_past;
+    int64_t n = T - L;
+    int m = n_parents;
+    float *y = (float *)malloc(sizeof(float) * (size_t)n);
+    float *z = (float *)malloc(sizeof(float) * (size_t)n * (size_t)(n_past > 0 ? n_past : 1));
+    float *x = (float *)malloc(sizeof(float) * (size_t)n * (size_t)m);
+    float *xs = (float *)malloc(sizeof(float) * (size_t)n * (size_t)m);
+    int64_t *pi = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    double *est = (double *)malloc(sizeof(double) * (size_t)(1 + n_surr));
+    orc_gather_lag(series, T, target, 0, L, y);
+    for (int lag = 1; lag <= n_past; ++lag) orc_gather_lag(series, T, target, lag, L, z + (int64_t)(lag - 1) * n);
+    for (int i = 0; i < m; ++i)
+        orc_gather_lag(series, T, parents[i] / n_lags, min_lag + parents[i] % n_lags, L,
+                       x + (int64_t)i * n);
+    int rc = orc_cmi_ksg(x, m, y, 1, z, n_past, n, n, k, &est[0], NULL, NULL);
+    for (int s = 0; s < n_surr && rc == 0; ++s) {
+        uint64_t stream = ((uint64_t)ORC_TAG_OMNIBUS << 48) | ((uint64_t)0xFFFFFFu << 24) | (uint64_t)s;
+        orc_perm(seed, stream, n, pi);
+        orc_permute_rows(x, m, n, n, pi, xs);
+        rc = orc_cmi_ksg(xs, m, y, 1, z, n_past, n, n, k, &est[1 + s], NULL, NULL);
+    }
+    if (rc == 0) {
+        int count = 0;
+        for (int s = 0; s < n_surr; ++s)
+            if (est[1 + s] >= est[0]) ++count;
+        *stat = est[0];
+        *pval = (double)count / (double)n_surr;
+        *significant = *pval < alpha;
+    }
+    free(y);
+    free(z);
+    free(x);
+    free(xs);
+    free(pi);
+    free(est);
+    return rc;
+}
+
+/* Sequential maximum statistic: stats[i] = T_i, pvals[i], significant[i],
+ * all indexed like parents. */
+int orc_seqmax(const float *series, int n_proc, int64_t T, int target, int n_past, int min_lag,
+               int max_lag, const int32_t *parents, int n_parents, int k, int n_surr, double alpha,
+               uint64_t seed, double *stats, double *pvals, int32_t *significant)
+{
+    if (!orc_post_args_ok(series, n_proc, T, target, n_past, min_lag, max_lag, parents, n_parents,
+                          k, n_surr) ||
+        !stats || !pvals || !significant)
+        return -1;
+    int m = n_parents;
+    double *est = (double *)malloc(sizeof(double) * (size_t)m * (size_t)(1 + n_surr));
+    int *order = (int *)malloc(sizeof(int) * (size_t)m);
+    int rc = orc_loo_estimates(series, n_proc, T, target, n_past, min_lag, max_lag, parents, m, k,
+                               n_surr, seed, ORC_TAG_SEQMAX, est);
+    if (rc == 0) {
+        /* decreasing T_i, ties to the lower index: insertion sort of indices */
+        for (int i = 0; i < m; ++i) {
+            int j = i;
+            while (j > 0 && est[(int64_t)i * (1 + n_surr)] > est[(int64_t)order[j - 1] * (1 + n_surr)]) {
+                order[j] = order[j - 1];
+                --j;
+            }
+            order[j] = i;
+        }
+        int still = 1;
+        for (int r = 0; r < m; ++r) {
+            int c = order[r];
+            double t = est[(int64_t)c * (1 + n_surr)];
+            int count = 0;
+            for (int s = 0; s < n_surr; ++s) {
+                double mx = -INFINITY;
+                for (int q = r; q < m; ++q) {
+                    double v = est[(int64_t)order[q] * (1 + n_surr) + 1 + s];
+                    if (v > mx) mx = v;
+                }
+                if (mx >= t) ++count;
+            }
+            stats[c] = t;
+            pvals[c] = (double)count / (double)n_surr;
+            still = still && pvals[c] < alpha;
+            significant[c] = still;
+        }
+    }
+    free(est);
+    free(order);
+    return rc;
+}
+
 /* Number of threads the OpenMP runtime will use (1 without OpenMP). */
 int orc_num_threads(void)
 {

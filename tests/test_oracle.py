@@ -380,3 +380,78 @@ def test_pinball_loss_of_a_constant_is_minimised_at_the_quantile():
     _, g = oracle.mlp_loss_grad(p, f, h, np.zeros(f, np.float32), np.ones(f, np.float32), x, t,
                                 quantile=q)
     assert abs(g[-1] - (np.count_nonzero(t < best) / 2001 - q)) < 1e-12
+
+
+# ---------------------------------------------------------------- tests after selection
+def _driven_system(T=1500, seed=3):
+    """Node 0 is driven at lag 1 by nodes 1 and 2 (AR(1) each); nodes 3, 4, 5
+    are independent noise.  Candidates use lag 1 only: candidate id = node."""
+    rng = np.random.default_rng(seed)
+    x = np.zeros((6, T + 100))
+    e = rng.standard_normal((6, T + 100))
+    for t in range(1, T + 100):
+        x[1, t] = 0.5 * x[1, t - 1] + e[1, t]
+        x[2, t] = 0.5 * x[2, t - 1] + e[2, t]
+        x[3:, t] = e[3:, t]
+        x[0, t] = 0.3 * x[0, t - 1] + 0.6 * x[1, t - 1] + 0.6 * x[2, t - 1] + 0.5 * e[0, t]
+    x = x[:, 100:]
+    x = (x - x.mean(axis=1, keepdims=True)) / x.std(axis=1, keepdims=True)
+    return x.astype(np.float32)
+
+
+POST = dict(target=0, n_past=1, min_lag=1, max_lag=1, k=4, n_surr=40, alpha=0.05, seed=11)
+
+
+def test_pruning_keeps_drivers_and_empties_a_noise_list():
+    """The minimum statistic compares the weakest parent with the minima of
+    all parents' surrogates; true drivers pass in the first round, a list of
+    independent sources is pruned away one round at a time."""
+    s = _driven_system()
+    r = oracle.prune(s, parents=[2, 1], **POST)
+    assert r["kept"] == [2, 1] and len(r["rounds"]) == 1 and r["rounds"][0][1]
+    r = oracle.prune(s, parents=[3, 4, 5], **POST)
+    assert r["kept"] == [] and len(r["rounds"]) == 3
+    assert all(not sig for (_, sig, _, _) in r["rounds"])
+    # each round removes the parent at the minimum of the remaining ones
+    removed = [c for (c, _, _, _) in r["rounds"]]
+    assert sorted(removed) == [3, 4, 5]
+
+
+def test_omnibus_separates_drivers_from_noise():
+    s = _driven_system()
+    stat, p, sig = oracle.omnibus(s, parents=[1, 2], **POST)
+    assert sig and p == 0.0 and stat > 0.2
+    stat_n, p_n, sig_n = oracle.omnibus(s, parents=[3, 4], **POST)
+    assert not sig_n and abs(stat_n) < 0.05
+
+
+def test_sequential_max_statistic_orders_and_stops():
+    s = _driven_system()
+    stats, pvals, sig = oracle.seqmax(s, parents=[1, 3, 2], **POST)
+    assert list(sig) == [True, False, True]
+    assert stats[1] < min(stats[0], stats[2])
+    assert pvals[0] == 0.0 and pvals[2] == 0.0 and pvals[1] >= POST["alpha"]
+    # leave-one-out statistics are those of the first pruning round (same conditioning)
+    r = oracle.prune(s, parents=[1, 3, 2], **POST)
+    assert r["rounds"][0][0] == 3 and r["rounds"][0][2] == stats[1]
+
+
+def test_single_parent_statistics_equal_the_greedy_estimate():
+    """With one parent, the leave-one-out statistic, the omnibus statistic and
+    the greedy step's estimate of that candidate are the same CMI."""
+    s = _driven_system(T=700, seed=5)
+    sel = oracle.select_target(s, 0, 1, 1, 1, 4, 5, 0.05, 11, 1, want_first_step=True)
+    for c in (1, 2, 3):
+        greedy = sel["first_step"][c, 0]
+        stat, _, _ = oracle.omnibus(s, parents=[c], **POST)
+        stats, _, _ = oracle.seqmax(s, parents=[c], **POST)
+        r = oracle.prune(s, parents=[c], **POST)
+        assert stat == greedy and stats[0] == greedy and r["rounds"][0][2] == greedy
+
+
+def test_post_selection_rejects_bad_arguments():
+    s = _driven_system(T=300)
+    for bad in (dict(parents=[]), dict(parents=[9]), dict(parents=[1], n_surr=0)):
+        args = dict(POST, **bad)
+        with pytest.raises(ValueError):
+            oracle.prune(s, **args)
