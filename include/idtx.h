@@ -277,6 +277,48 @@ int idtx_mte_select_target(idtx_ctx *ctx, const float *series, int n_proc, int64
                            int max_parents, int32_t *parents_out, int *n_parents,
                            idtx_step *steps_out, int *n_steps, void *stream);
 
+/* Tests after the greedy selection (the paper's Summary asks that the errors
+ * of testing many sources be controlled, and describes no test; these are
+ * readings).  Common arguments as for idtx_mte_step; parents[0..n_parents)
+ * are distinct candidate ids, none of them a target-past variable;
+ * settings->mode must be IDTX_MODE_BATCHED.  The leave-one-out statistic of
+ * parent i is T_i = I(X_{c_i}; Y | target lags 1..n_past, the other parents
+ * in list order), its surrogate s permutes X_{c_i} with stream
+ * tag << 48 | c_i << 24 | s.  Outputs may be host or device memory.
+ *
+ * Pruning by the minimum statistic.  Round r (tag 0x9000 + r): T_min =
+ * min_i T_i (ties: lowest i), p = #{s : min_i T_i,s >= T_min} / n_surr; if
+ * p >= alpha the parent at the minimum is removed and the next round tests
+ * the rest; the loop stops at the first significant round or when no parent
+ * is left.  kept_out [n_parents]: surviving parents in input order, *n_kept;
+ * rounds_out (nullable) [n_parents]: per round, cand = the parent at the
+ * minimum, significant, stat = T_min, pval; *n_rounds (nullable).
+ * n_past + n_parents - 1 <= IDTX_MAX_DZ. */
+int idtx_mte_prune(idtx_ctx *ctx, const float *series, int n_proc, int64_t T, int target,
+                   int n_past, int min_lag, int max_lag, const int32_t *parents, int n_parents,
+                   const idtx_settings *settings, int32_t *kept_out, int *n_kept,
+                   idtx_step *rounds_out, int *n_rounds, void *stream);
+
+/* Omnibus test of a parent set: T = I(X_P; Y | target lags 1..n_past) with
+ * X_P the n_parents parents jointly (n_parents <= IDTX_MAX_DX); surrogate s
+ * permutes the rows of X_P together, stream 0xA000 << 48 | 0xFFFFFF << 24 | s;
+ * p = #{s : T_s >= T} / n_surr.  result: cand = -1, significant, stat, pval. */
+int idtx_mte_omnibus(idtx_ctx *ctx, const float *series, int n_proc, int64_t T, int target,
+                     int n_past, int min_lag, int max_lag, const int32_t *parents,
+                     int n_parents, const idtx_settings *settings, idtx_step *result,
+                     void *stream);
+
+/* Sequential maximum statistic (tag 0xB000): parents in decreasing order of
+ * T_i (ties: lower i first); the r-th is compared with the surrogate maxima
+ * over itself and the parents after it, p_r = #{s : max_{j >= r} T_j,s >=
+ * T_(r)} / n_surr; parents are significant down to the first p_r >= alpha.
+ * stat_out, pval_out (fp64), significant_out (int32): [n_parents], indexed
+ * like parents.  n_past + n_parents - 1 <= IDTX_MAX_DZ. */
+int idtx_mte_seqmax(idtx_ctx *ctx, const float *series, int n_proc, int64_t T, int target,
+                    int n_past, int min_lag, int max_lag, const int32_t *parents, int n_parents,
+                    const idtx_settings *settings, double *stat_out, double *pval_out,
+                    int32_t *significant_out, void *stream);
+
 /* ------------------------------------------------------------------------ */
 /* Learned screen (no counterpart in the paper).                            */
 /* A perceptron F -> H -> H -> 1 with ReLU.  Parameters, flat fp32 master    */

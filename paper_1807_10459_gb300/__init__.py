@@ -18,7 +18,7 @@ import threading
 import numpy as np
 
 __all__ = ["IdtxError", "Settings", "Context", "load", "cmi_ksg", "cmi_batch", "mte_step",
-           "mte_select_target", "library_path", "Screen", "screen_predict", "screen_loss_grad",
+           "mte_select_target", "mte_prune", "mte_omnibus", "mte_seqmax", "library_path", "Screen", "screen_predict", "screen_loss_grad",
            "screen_train", "screen_set", "StepResult"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -120,9 +120,15 @@ def load():
         lib.idtx_ctx_set_graphs.argtypes = [vp, i32]
         lib.idtx_ctx_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
         lib.idtx_ctx_reset_stats.argtypes = [vp]
+        post = [vp, vp, i32, i64, i32, i32, i32, i32, vp, i32, ctypes.POINTER(Settings)]
+        lib.idtx_mte_prune.argtypes = post + [vp, ctypes.POINTER(i32), ctypes.POINTER(Step),
+                                              ctypes.POINTER(i32), vp]
+        lib.idtx_mte_omnibus.argtypes = post + [ctypes.POINTER(Step), vp]
+        lib.idtx_mte_seqmax.argtypes = post + [vp, vp, vp, vp]
         lib.idtx_ctx_set_kernel.argtypes = [vp, i32]
         lib.idtx_ctx_set_list_caps.argtypes = [vp, i32, i32]
-        for name in ("idtx_ctx_set_kernel", "idtx_ctx_set_list_caps","idtx_screen_predict", "idtx_screen_loss_grad", "idtx_screen_train",
+        for name in ("idtx_mte_prune", "idtx_mte_omnibus", "idtx_mte_seqmax",
+                     "idtx_ctx_set_kernel", "idtx_ctx_set_list_caps","idtx_screen_predict", "idtx_screen_loss_grad", "idtx_screen_train",
                      "idtx_screen_set", "idtx_ctx_set_profiling", "idtx_ctx_set_graphs",
                      "idtx_ctx_get_stats", "idtx_ctx_reset_stats",
                      "idtx_ctx_create", "idtx_ctx_destroy", "idtx_cmi_ksg", "idtx_cmi_batch",
@@ -476,3 +482,57 @@ def mte_select_target(series, target: int, n_past: int, min_lag: int, max_lag: i
                                   int(steps[i].n_cand), int(steps[i].n_full),
                                   int(steps[i].surr_done))
                        for i in range(n_steps.value)])
+
+
+def _post_call(name, series, target, n_past, min_lag, max_lag, parents, k, n_surr, alpha, seed,
+               timeout_ms, ctx, *outs):
+    a = _Arr(series, name="series")
+    dev = series.device.index if (_is_torch(series) and series.is_cuda) else 0
+    ctx = ctx or default_context(dev or 0)
+    s = _settings(k, n_surr, seed, alpha, timeout_ms, MODE_BATCHED)
+    par = np.ascontiguousarray(np.asarray(parents, np.int32))
+    _check(getattr(load(), name)(ctx.handle, a.ptr, a.d, a.n, int(target), int(n_past),
+                                 int(min_lag), int(max_lag), par.ctypes.data, len(par),
+                                 ctypes.byref(s), *outs, _stream_for(series)))
+    return len(par)
+
+
+def mte_prune(series, target: int, n_past: int, min_lag: int, max_lag: int, parents, k: int = 4,
+              n_surr: int = 200, alpha: float = 0.05, seed: int = 0, timeout_ms: int = 0,
+              ctx: Context | None = None):
+    """Minimum-statistic pruning of a parent list:
+    dict(kept=[ids], rounds=[(cand at the minimum, significant, T_min, p)])."""
+    m = len(parents)
+    kept = np.zeros(max(1, m), np.int32)
+    rounds = (Step * max(1, m))()
+    n_kept, n_rounds = ctypes.c_int(), ctypes.c_int()
+    _post_call("idtx_mte_prune", series, target, n_past, min_lag, max_lag, parents, k, n_surr,
+               alpha, seed, timeout_ms, ctx, kept.ctypes.data, ctypes.byref(n_kept), rounds,
+               ctypes.byref(n_rounds))
+    return dict(kept=[int(c) for c in kept[:n_kept.value]],
+                rounds=[(int(rounds[i].cand), bool(rounds[i].significant), float(rounds[i].stat),
+                         float(rounds[i].pval)) for i in range(n_rounds.value)])
+
+
+def mte_omnibus(series, target: int, n_past: int, min_lag: int, max_lag: int, parents,
+                k: int = 4, n_surr: int = 200, alpha: float = 0.05, seed: int = 0,
+                timeout_ms: int = 0, ctx: Context | None = None):
+    """Omnibus test of a parent set: (stat, p, significant)."""
+    r = Step()
+    _post_call("idtx_mte_omnibus", series, target, n_past, min_lag, max_lag, parents, k, n_surr,
+               alpha, seed, timeout_ms, ctx, ctypes.byref(r))
+    return float(r.stat), float(r.pval), bool(r.significant)
+
+
+def mte_seqmax(series, target: int, n_past: int, min_lag: int, max_lag: int, parents,
+               k: int = 4, n_surr: int = 200, alpha: float = 0.05, seed: int = 0,
+               timeout_ms: int = 0, ctx: Context | None = None):
+    """Sequential maximum statistic: (stats [m], pvals [m], significant [m]) by parent."""
+    m = len(parents)
+    stats = np.zeros(max(1, m), np.float64)
+    pvals = np.zeros(max(1, m), np.float64)
+    sig = np.zeros(max(1, m), np.int32)
+    _post_call("idtx_mte_seqmax", series, target, n_past, min_lag, max_lag, parents, k, n_surr,
+               alpha, seed, timeout_ms, ctx, stats.ctypes.data, pvals.ctypes.data,
+               sig.ctypes.data)
+    return stats[:m], pvals[:m], sig[:m].astype(bool)

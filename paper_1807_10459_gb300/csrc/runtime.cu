@@ -459,6 +459,121 @@ __global__ void k_gate(const double *est_a, int n_cand, int sa, const double *es
 
 // Screened steps: T_obs, its candidate, and the count over the first sa
 // surrogate indices (every candidate has them) into out / *count.
+// Tests after the greedy selection.  est: [m][1+S], row i = parent ids[i]'s
+// leave-one-out estimate and its surrogates.
+//
+// Minimum statistic (pruning round): T_min = min_i T_i (ties: lowest i),
+// p = #{s : min_i T_i,s >= T_min} / S.  One block.
+__global__ void k_min_stat(const double *est, int m, int n_surr, const int32_t *ids, double alpha,
+                           idtx_step *out)
+{
+    __shared__ double s_tmin;
+    __shared__ int s_at;
+    __shared__ int s_cnt[32];
+    const int tid = threadIdx.x, row = 1 + n_surr;
+    if (tid == 0) {
+        int at = 0;
+        for (int i = 1; i < m; ++i)
+            if (est[(int64_t)i * row] < est[(int64_t)at * row]) at = i;
+        s_at = at;
+        s_tmin = est[(int64_t)at * row];
+    }
+    __syncthreads();
+    int cnt = 0;
+    for (int sidx = tid; sidx < n_surr; sidx += blockDim.x) {
+        double mn = INFINITY;
+        for (int i = 0; i < m; ++i) mn = fmin(mn, est[(int64_t)i * row + 1 + sidx]);
+        cnt += mn >= s_tmin ? 1 : 0;
+    }
+    for (int off = 16; off >= 1; off >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
+    if ((tid & 31) == 0) s_cnt[tid >> 5] = cnt;
+    __syncthreads();
+    if (tid == 0) {
+        int total = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) total += s_cnt[w];
+        const double p = (double)total / (double)n_surr;
+        out->cand = ids[s_at];
+        out->significant = p < alpha ? 1 : 0;
+        out->stat = s_tmin;
+        out->pval = p;
+        out->n_cand = m;
+        out->n_full = m;
+        out->surr_done = n_surr;
+        out->reserved = 0;
+    }
+}
+
+// Single statistic against its own surrogates (omnibus test): p = #{s : T_s >= T} / S.
+__global__ void k_single_stat(const double *est, int n_surr, double alpha, idtx_step *out)
+{
+    __shared__ int s_cnt[32];
+    const int tid = threadIdx.x;
+    int cnt = 0;
+    for (int sidx = tid; sidx < n_surr; sidx += blockDim.x) cnt += est[1 + sidx] >= est[0] ? 1 : 0;
+    for (int off = 16; off >= 1; off >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
+    if ((tid & 31) == 0) s_cnt[tid >> 5] = cnt;
+    __syncthreads();
+    if (tid == 0) {
+        int total = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) total += s_cnt[w];
+        const double p = (double)total / (double)n_surr;
+        out->cand = -1;
+        out->significant = p < alpha ? 1 : 0;
+        out->stat = est[0];
+        out->pval = p;
+        out->n_cand = 1;
+        out->n_full = 1;
+        out->surr_done = n_surr;
+        out->reserved = 0;
+    }
+}
+
+// Sequential maximum statistic: parents in decreasing T_i (ties: lower i
+// first); the r-th is compared with the surrogate maxima over itself and the
+// parents after it; significant down to the first p >= alpha.  One block;
+// rank[] (m ints) is scratch.  stats, pvals, sig indexed like the parents.
+__global__ void k_seqmax_stat(const double *est, int m, int n_surr, double alpha, int32_t *rank,
+                              double *stats, double *pvals, int32_t *sig)
+{
+    __shared__ int s_cnt[32];
+    const int tid = threadIdx.x, row = 1 + n_surr;
+    if (tid == 0) {
+        for (int i = 0; i < m; ++i) {
+            int j = i;
+            while (j > 0 && est[(int64_t)i * row] > est[(int64_t)rank[j - 1] * row]) {
+                rank[j] = rank[j - 1];
+                --j;
+            }
+            rank[j] = i;
+        }
+    }
+    __syncthreads();
+    int still = 1;
+    for (int r = 0; r < m; ++r) {
+        const int c = rank[r];
+        const double t = est[(int64_t)c * row];
+        int cnt = 0;
+        for (int sidx = tid; sidx < n_surr; sidx += blockDim.x) {
+            double mx = -INFINITY;
+            for (int q = r; q < m; ++q) mx = fmax(mx, est[(int64_t)rank[q] * row + 1 + sidx]);
+            cnt += mx >= t ? 1 : 0;
+        }
+        for (int off = 16; off >= 1; off >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
+        if ((tid & 31) == 0) s_cnt[tid >> 5] = cnt;
+        __syncthreads();
+        if (tid == 0) {
+            int total = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) total += s_cnt[w];
+            const double p = (double)total / (double)n_surr;
+            still = still && p < alpha;
+            stats[c] = t;
+            pvals[c] = p;
+            sig[c] = still;
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void k_gate_begin(const double *est_a, int n_cand, int sa, const int32_t *ids,
                              idtx_step *out, int *count)
 {
@@ -2432,6 +2547,238 @@ int idtx_mte_select_target(idtx_ctx *c, const float *series, int n_proc, int64_t
         cudaFree(dev_series);
     }
     return rc;
+}
+
+
+// ------------------------------------------------------------------ tests after selection
+namespace {
+
+constexpr uint64_t kTagPrune = 0x9000, kTagOmnibus = 0xA000, kTagSeqmax = 0xB000;
+
+// Common checks of a post-selection call; puts the series on the device
+// (host series are copied into B_IN) and sets the sample range.
+int post_begin(idtx_ctx *c, const float *series, int n_proc, int64_t T, int target, int n_past,
+               int min_lag, int max_lag, const int32_t *parents, int m, const idtx_settings *s,
+               int dx_max_needed, int dz_needed, cudaStream_t st, const float **ser, int64_t *L)
+{
+    if (!c) return fail(IDTX_EINVAL, "ctx is NULL");
+    if (!series || !s || !parents) return fail(IDTX_EINVAL, "NULL series/settings/parents");
+    if (n_proc < 1 || target < 0 || target >= n_proc || n_past < 0 || min_lag < 1 ||
+        max_lag < min_lag || m < 1)
+        return fail(IDTX_EINVAL, "bad arguments");
+    const int n_lags = max_lag - min_lag + 1;
+    for (int i = 0; i < m; ++i) {
+        const int cid = parents[i];
+        if (cid < 0 || cid >= n_proc * n_lags)
+            return fail(IDTX_EINVAL, "parent id %d out of range", cid);
+        if (cid / n_lags == target && min_lag + cid % n_lags <= n_past)
+            return fail(IDTX_EINVAL, "parent id %d is a target-past variable", cid);
+        for (int j = 0; j < i; ++j)
+            if (parents[j] == cid) return fail(IDTX_EINVAL, "parent id %d repeated", cid);
+    }
+    *L = std::max(max_lag, n_past);
+    if (T <= *L || T - *L > IDTX_MAX_N) return fail(IDTX_EINVAL, "bad T for the lags");
+    if (s->k < 1 || s->k > IDTX_MAX_K || s->k > T - *L - 1) return fail(IDTX_EINVAL, "bad k");
+    if (s->n_surr < 1) return fail(IDTX_EINVAL, "n_surr must be >= 1");
+    if (!(s->alpha > 0.0 && s->alpha < 1.0)) return fail(IDTX_EINVAL, "alpha out of (0,1)");
+    if (s->mode != IDTX_MODE_BATCHED) return fail(IDTX_EINVAL, "only IDTX_MODE_BATCHED");
+    if (dx_max_needed > IDTX_MAX_DX || dz_needed > IDTX_MAX_DZ)
+        return fail(IDTX_EINVAL, "parent set too large (dx=%d dz=%d)", dx_max_needed, dz_needed);
+    *ser = series;
+    if (!device_accessible(series)) {
+        IDTX_TRY(ensure(c, B_IN, (size_t)n_proc * T * sizeof(float)));
+        IDTX_CUDA(cudaMemcpyAsync(c->buf[B_IN], series, (size_t)n_proc * T * sizeof(float),
+                                  cudaMemcpyHostToDevice, st));
+        *ser = (const float *)c->buf[B_IN];
+    }
+    return ensure_psi(c, std::max<int64_t>(T - *L, s->k) + 1, st);
+}
+
+// Run fully described groups as one batch; estimates land in B_CMI at each
+// group's off_cmi.
+int run_groups(idtx_ctx *c, std::vector<Group> &gs, cudaStream_t st, long long tmo, size_t n_est)
+{
+    std::vector<unsigned char> arena;
+    pack_desc(gs, arena);
+    IDTX_TRY(ensure(c, B_DESC, arena.size()));
+    IDTX_CUDA(cudaMemcpyAsync(c->buf[B_DESC], arena.data(), arena.size(), cudaMemcpyHostToDevice,
+                              st));
+    if (std::any_of(gs.begin(), gs.end(), [](const Group &g) { return g.tune; }))
+        IDTX_TRY(resolve_tuning(c, gs, st, tmo));
+    IDTX_TRY(ensure(c, B_CMI, n_est * sizeof(double)));
+    BatchPlan bp;
+    IDTX_TRY(batch_plan(c, gs, st, tmo, bp));
+    return batch_enqueue(c, gs, bp, st, (double *)c->buf[B_CMI], tmo);
+}
+
+// Leave-one-out estimates of a parent list: group i estimates
+// I(X_{c_i}; Y | target past, X_{c_j} for j != i) and its surrogates
+// (streams tag<<48 | c_i<<24 | s) into B_CMI row i.
+int enqueue_loo(idtx_ctx *c, const float *ser, int64_t T, int64_t L, int target, int n_past,
+                int min_lag, int max_lag, const std::vector<int32_t> &par,
+                const idtx_settings *s, uint64_t tag, cudaStream_t st)
+{
+    const int n_lags = max_lag - min_lag + 1, m = (int)par.size();
+    auto col = [&](int cid) {
+        return Col{ser + (int64_t)(cid / n_lags) * T, L - (min_lag + cid % n_lags)};
+    };
+    std::vector<Group> gs(m);
+    size_t off = 0;
+    for (int i = 0; i < m; ++i) {
+        Group &g = gs[i];
+        g.n = T - L;
+        g.dx = 1;
+        g.dy = 1;
+        g.dz = n_past + m - 1;
+        g.k = s->k;
+        g.ycols.push_back(Col{ser + (int64_t)target * T, L});
+        for (int lag = 1; lag <= n_past; ++lag) g.zcols.push_back(Col{ser + (int64_t)target * T, L - lag});
+        for (int j = 0; j < m; ++j)
+            if (j != i) g.zcols.push_back(col(par[j]));
+        g.xcols.push_back(col(par[i]));
+        g.jobs.push_back(Job{0, -1});
+        for (int sidx = 0; sidx < s->n_surr; ++sidx) {
+            g.jobs.push_back(Job{0, sidx});
+            g.slot_stream.push_back((tag << 48) | ((uint64_t)par[i] << 24) | (uint64_t)sidx);
+            g.slot_seed.push_back(s->seed);
+        }
+        IDTX_TRY(plan(c, g));
+        g.work_slot = i;
+        g.off_cmi = off;
+        off += 1 + (size_t)s->n_surr;
+    }
+    return run_groups(c, gs, st, timeout_of(s), off);
+}
+
+}  // namespace
+
+int idtx_mte_prune(idtx_ctx *c, const float *series, int n_proc, int64_t T, int target, int n_past,
+                   int min_lag, int max_lag, const int32_t *parents, int n_parents,
+                   const idtx_settings *s, int32_t *kept_out, int *n_kept, idtx_step *rounds_out,
+                   int *n_rounds, void *stream)
+{
+    if (!kept_out || !n_kept) return fail(IDTX_EINVAL, "kept_out / n_kept is NULL");
+    *n_kept = 0;
+    if (n_rounds) *n_rounds = 0;
+    if (c == nullptr) return fail(IDTX_EINVAL, "ctx is NULL");
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const float *ser = nullptr;
+    int64_t L = 0;
+    IDTX_TRY(post_begin(c, series, n_proc, T, target, n_past, min_lag, max_lag, parents, n_parents,
+                        s, 1, n_past + n_parents - 1, st, &ser, &L));
+    std::vector<int32_t> cur(parents, parents + n_parents);
+    for (int round = 0; !cur.empty(); ++round) {
+        const int m = (int)cur.size();
+        IDTX_TRY(begin_call(c, m, st));
+        IDTX_TRY(enqueue_loo(c, ser, T, L, target, n_past, min_lag, max_lag, cur, s,
+                             kTagPrune + (uint64_t)round, st));
+        IDTX_TRY(ensure(c, B_STEP, align_up(sizeof(idtx_step), 16) + (size_t)m * 4 + 64));
+        idtx_step *step_d = (idtx_step *)c->buf[B_STEP];
+        int32_t *ids_d = (int32_t *)((unsigned char *)c->buf[B_STEP] + align_up(sizeof(idtx_step), 16));
+        IDTX_CUDA(cudaMemcpyAsync(ids_d, cur.data(), (size_t)m * 4, cudaMemcpyHostToDevice, st));
+        k_min_stat<<<1, 256, 0, st>>>((const double *)c->buf[B_CMI], m, s->n_surr, ids_d, s->alpha,
+                                      step_d);
+        IDTX_CUDA(cudaGetLastError());
+        c->stats.kernel_launches += 1;
+        idtx_step r;
+        IDTX_CUDA(cudaMemcpyAsync(&r, step_d, sizeof(idtx_step), cudaMemcpyDeviceToHost, st));
+        IDTX_TRY(finish_call(c, st));
+        if (rounds_out) rounds_out[round] = r;
+        if (n_rounds) *n_rounds = round + 1;
+        if (r.significant) break;
+        cur.erase(std::find(cur.begin(), cur.end(), r.cand));
+    }
+    for (size_t i = 0; i < cur.size(); ++i) kept_out[i] = cur[i];
+    *n_kept = (int)cur.size();
+    return IDTX_OK;
+}
+
+int idtx_mte_omnibus(idtx_ctx *c, const float *series, int n_proc, int64_t T, int target,
+                     int n_past, int min_lag, int max_lag, const int32_t *parents, int n_parents,
+                     const idtx_settings *s, idtx_step *result, void *stream)
+{
+    if (!result) return fail(IDTX_EINVAL, "result is NULL");
+    if (c == nullptr) return fail(IDTX_EINVAL, "ctx is NULL");
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const float *ser = nullptr;
+    int64_t L = 0;
+    IDTX_TRY(post_begin(c, series, n_proc, T, target, n_past, min_lag, max_lag, parents, n_parents,
+                        s, n_parents, n_past, st, &ser, &L));
+    const int n_lags = max_lag - min_lag + 1;
+    IDTX_TRY(begin_call(c, 1, st));
+    std::vector<Group> gs(1);
+    Group &g = gs[0];
+    g.n = T - L;
+    g.dx = n_parents;
+    g.dy = 1;
+    g.dz = n_past;
+    g.k = s->k;
+    g.ycols.push_back(Col{ser + (int64_t)target * T, L});
+    for (int lag = 1; lag <= n_past; ++lag) g.zcols.push_back(Col{ser + (int64_t)target * T, L - lag});
+    for (int i = 0; i < n_parents; ++i)
+        g.xcols.push_back(Col{ser + (int64_t)(parents[i] / n_lags) * T,
+                              L - (min_lag + parents[i] % n_lags)});
+    g.jobs.push_back(Job{0, -1});
+    for (int sidx = 0; sidx < s->n_surr; ++sidx) {
+        g.jobs.push_back(Job{0, sidx});
+        g.slot_stream.push_back((kTagOmnibus << 48) | ((uint64_t)0xFFFFFF << 24) | (uint64_t)sidx);
+        g.slot_seed.push_back(s->seed);
+    }
+    IDTX_TRY(plan(c, g));
+    IDTX_TRY(run_groups(c, gs, st, timeout_of(s), 1 + (size_t)s->n_surr));
+    IDTX_TRY(ensure(c, B_STEP, sizeof(idtx_step) + 64));
+    idtx_step *step_d = (idtx_step *)c->buf[B_STEP];
+    k_single_stat<<<1, 256, 0, st>>>((const double *)c->buf[B_CMI], s->n_surr, s->alpha, step_d);
+    IDTX_CUDA(cudaGetLastError());
+    c->stats.kernel_launches += 1;
+    IDTX_CUDA(cudaMemcpyAsync(result, step_d, sizeof(idtx_step),
+                              device_accessible(result) ? cudaMemcpyDeviceToDevice
+                                                        : cudaMemcpyDeviceToHost,
+                              st));
+    return finish_call(c, st);
+}
+
+int idtx_mte_seqmax(idtx_ctx *c, const float *series, int n_proc, int64_t T, int target,
+                    int n_past, int min_lag, int max_lag, const int32_t *parents, int n_parents,
+                    const idtx_settings *s, double *stat_out, double *pval_out,
+                    int32_t *significant_out, void *stream)
+{
+    if (!stat_out || !pval_out || !significant_out) return fail(IDTX_EINVAL, "NULL output");
+    if (c == nullptr) return fail(IDTX_EINVAL, "ctx is NULL");
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const float *ser = nullptr;
+    int64_t L = 0;
+    IDTX_TRY(post_begin(c, series, n_proc, T, target, n_past, min_lag, max_lag, parents, n_parents,
+                        s, 1, n_past + n_parents - 1, st, &ser, &L));
+    const int m = n_parents;
+    std::vector<int32_t> par(parents, parents + m);
+    IDTX_TRY(begin_call(c, m, st));
+    IDTX_TRY(enqueue_loo(c, ser, T, L, target, n_past, min_lag, max_lag, par, s, kTagSeqmax, st));
+    const size_t o_stats = 256, o_pvals = o_stats + align_up((size_t)m * 8, 16),
+                 o_sig = o_pvals + align_up((size_t)m * 8, 16);
+    IDTX_TRY(ensure(c, B_STEP, o_sig + align_up((size_t)m * 4, 16)));
+    unsigned char *b = (unsigned char *)c->buf[B_STEP];
+    int32_t *rank_d = (int32_t *)b;  // m <= IDTX_MAX_DZ + 1 ints fit in the first 256 bytes
+    double *stats_d = (double *)(b + o_stats), *pvals_d = (double *)(b + o_pvals);
+    int32_t *sig_d = (int32_t *)(b + o_sig);
+    k_seqmax_stat<<<1, 256, 0, st>>>((const double *)c->buf[B_CMI], m, s->n_surr, s->alpha, rank_d,
+                                     stats_d, pvals_d, sig_d);
+    IDTX_CUDA(cudaGetLastError());
+    c->stats.kernel_launches += 1;
+    auto out = [&](void *dst, const void *src, size_t bytes) -> int {
+        IDTX_CUDA(cudaMemcpyAsync(dst, src, bytes,
+                                  device_accessible(dst) ? cudaMemcpyDeviceToDevice
+                                                         : cudaMemcpyDeviceToHost,
+                                  st));
+        return IDTX_OK;
+    };
+    IDTX_TRY(out(stat_out, stats_d, (size_t)m * 8));
+    IDTX_TRY(out(pval_out, pvals_d, (size_t)m * 8));
+    IDTX_TRY(out(significant_out, sig_d, (size_t)m * 4));
+    return finish_call(c, st);
 }
 
 }  // extern "C"
