@@ -115,3 +115,24 @@ def test_bad_parent_lists_are_rejected(idtx):
             idtx.mte_prune(d, **dict(POST, **b))
     with pytest.raises(idtx.IdtxError):      # more parents than the omnibus kernel's X columns
         idtx.mte_omnibus(d, **dict(POST, parents=[1, 2, 3, 4, 5]))
+
+
+@pytest.mark.slow
+def test_full_size_post_selection_sampled(idtx):
+    """The benchmarked network (10-node VAR(5), T=10000, target 0, history 3,
+    lags 1..5, k=4, 200 surrogates): after the greedy selection, the
+    leave-one-out statistic of every selected parent against the oracle's
+    estimate (N = 9995)."""
+    net = synth.var_network()
+    s = torch.from_numpy(net.series).cuda()
+    kw = dict(k=4, n_surr=200, alpha=0.05, seed=20181029)
+    par = idtx.mte_select_target(s, 0, 3, 1, 5, max_parents=10, **kw)["parents"]
+    assert len(par) >= 1
+    stats, pvals, sig = idtx.mte_seqmax(s, 0, 3, 1, 5, par, **kw)
+    L, T = 5, net.series.shape[1]
+    col = lambda c: net.series[c // 5, L - (1 + c % 5):T - (1 + c % 5)]
+    y = net.series[0, L:]
+    past = [net.series[0, L - lag:T - lag] for lag in (1, 2, 3)]
+    for i, c in enumerate(par):
+        z = np.stack(past + [col(d) for j, d in enumerate(par) if j != i])
+        assert abs(stats[i] - oracle.cmi_ksg(col(c)[None, :], y, z, 4)) < TOL
