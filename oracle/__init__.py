@@ -91,6 +91,9 @@ def _load():
                                          ctypes.POINTER(OrcStep), ctypes.POINTER(ctypes.c_int)]
         lib.orc_omnibus.argtypes = post + [_F64P, _F64P, ctypes.POINTER(ctypes.c_int)]
         lib.orc_seqmax.argtypes = post + [_F64P, _F64P, _I32P]
+        lib.orc_bivariate_te.argtypes = [_F32P, ctypes.c_int, ctypes.c_int64, ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_uint64, _F64P, _F64P]
         lib.orc_num_threads.restype = ctypes.c_int
         lib.orc_set_num_threads.argtypes = [ctypes.c_int]
         _lib = lib
@@ -289,6 +292,23 @@ def seqmax(series, target: int, n_past: int, min_lag: int, max_lag: int, parents
     if rc != 0:
         raise ValueError("orc_seqmax: invalid arguments")
     return stats, pvals, sig.astype(bool)
+
+
+def bivariate_te(series, target: int, n_past: int, min_lag: int, max_lag: int, k: int,
+                 n_surr: int, seed: int):
+    """Bivariate TE of every source variable: (est [n_cand][1+S], pvals [n_cand]);
+    rows of the target's own variables are NaN."""
+    s = np.ascontiguousarray(np.asarray(series, np.float32))
+    n_proc, T = s.shape
+    n_cand = n_proc * (max_lag - min_lag + 1)
+    est = np.full((n_cand, 1 + n_surr), np.nan, np.float64)
+    pvals = np.full(n_cand, np.nan, np.float64)
+    rc = _load().orc_bivariate_te(_fp(s), n_proc, T, target, n_past, min_lag, max_lag, k, n_surr,
+                                  ctypes.c_uint64(seed), est.ctypes.data_as(_F64P),
+                                  pvals.ctypes.data_as(_F64P))
+    if rc != 0:
+        raise ValueError("orc_bivariate_te: invalid arguments")
+    return est, pvals
 
 
 def num_threads() -> int:

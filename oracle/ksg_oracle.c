@@ -636,6 +636,62 @@ int orc_seqmax(const float *series, int n_proc, int64_t T, int target, int n_pas
     return rc;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Bivariate transfer entropy (Summary, paragraph 5 lists bivariate TE among */
+/* the network inference algorithms; the test is a reading): every source    */
+/* variable c = (p, lag), p != target, lag in [min_lag, max_lag], on its own:*/
+/*   T(c) = I(X_c; Y | target lags 1..n_past), surrogate s permutes X_c with */
+/*   stream 0xC000<<48 | c<<24 | s; p(c) = #{s : T_s(c) >= T(c)} / S.        */
+/* est [n_cand_total][1+S] and pvals [n_cand_total]; rows of the target's    */
+/* own variables are left untouched.                                         */
+/* Pinned by: the drivers of a driven system are significant and independent*/
+/* sources are not; T(c) equals the greedy step's first estimate of c.       */
+/* ------------------------------------------------------------------------ */
+#define ORC_TAG_BIVAR 0xC000u
+
+int orc_bivariate_te(const float *series, int n_proc, int64_t T, int target, int n_past,
+                     int min_lag, int max_lag, int k, int n_surr, uint64_t seed, double *est,
+                     double *pvals)
+{
+    if (!series || n_proc < 1 || target < 0 || target >= n_proc || n_past < 0 || min_lag < 1 ||
+        max_lag < min_lag || k < 1 || n_surr < 1 || !est || !pvals)
+        return -1;
+    int n_lags = max_lag - min_lag + 1;
+    int64_t L = max_lag > n_past ? max_lag : n_past;
+    if (T - L < (int64_t)k + 1) return -1;
+    int64_t n = T - L;
+    float *y = (float *)malloc(sizeof(float) * (size_t)n);
+    float *z = (float *)malloc(sizeof(float) * (size_t)n * (size_t)(n_past > 0 ? n_past : 1));
+    float *xc = (float *)malloc(sizeof(float) * (size_t)n);
+    float *xs = (float *)malloc(sizeof(float) * (size_t)n);
+    int64_t *pi = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    orc_gather_lag(series, T, target, 0, L, y);
+    for (int lag = 1; lag <= n_past; ++lag) orc_gather_lag(series, T, target, lag, L, z + (int64_t)(lag - 1) * n);
+    int rc = 0;
+    for (int c = 0; c < n_proc * n_lags && rc == 0; ++c) {
+        int p = c / n_lags, lag = min_lag + c % n_lags;
+        if (p == target) continue;
+        orc_gather_lag(series, T, p, lag, L, xc);
+        double *row = est + (int64_t)c * (1 + n_surr);
+        rc |= orc_cmi_ksg(xc, 1, y, 1, z, n_past, n, n, k, &row[0], NULL, NULL);
+        int count = 0;
+        for (int s = 0; s < n_surr && rc == 0; ++s) {
+            uint64_t stream = ((uint64_t)ORC_TAG_BIVAR << 48) | ((uint64_t)c << 24) | (uint64_t)s;
+            orc_perm(seed, stream, n, pi);
+            orc_permute_rows(xc, 1, n, n, pi, xs);
+            rc |= orc_cmi_ksg(xs, 1, y, 1, z, n_past, n, n, k, &row[1 + s], NULL, NULL);
+            if (row[1 + s] >= row[0]) ++count;
+        }
+        pvals[c] = (double)count / (double)n_surr;
+    }
+    free(y);
+    free(z);
+    free(xc);
+    free(xs);
+    free(pi);
+    return rc;
+}
+
 /* Number of threads the OpenMP runtime will use (1 without OpenMP). */
 int orc_num_threads(void)
 {

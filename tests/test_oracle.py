@@ -455,3 +455,14 @@ def test_post_selection_rejects_bad_arguments():
         args = dict(POST, **bad)
         with pytest.raises(ValueError):
             oracle.prune(s, **args)
+
+
+def test_bivariate_te_finds_drivers_and_matches_the_greedy_estimates():
+    s = _driven_system()
+    est, p = oracle.bivariate_te(s, 0, 1, 1, 1, 4, 40, 11)
+    assert np.isnan(p[0])                         # the target's own variable is not a source
+    assert p[1] == 0.0 and p[2] == 0.0            # the two drivers
+    assert all(p[c] >= 0.05 for c in (3, 4, 5))  # independent sources
+    sel = oracle.select_target(s, 0, 1, 1, 1, 4, 3, 0.05, 11, 1, want_first_step=True)
+    for c in range(1, 6):
+        assert est[c, 0] == sel["first_step"][c, 0]
