@@ -319,6 +319,20 @@ int idtx_mte_seqmax(idtx_ctx *ctx, const float *series, int n_proc, int64_t T, i
                     const idtx_settings *settings, double *stat_out, double *pval_out,
                     int32_t *significant_out, void *stream);
 
+/* Bivariate transfer entropy of every source variable (the paper's Summary
+ * lists bivariate TE among the network inference algorithms; the test is a
+ * reading): for each candidate c = (p, lag) with p != target,
+ * T(c) = I(X_c; Y | target lags 1..n_past), surrogate s permutes X_c with
+ * stream 0xC000 << 48 | c << 24 | s, and p(c) = #{s : T_s(c) >= T(c)} / n_surr
+ * (per source, no correction for the number of sources).  All sources'
+ * estimates run as one batch.  pval_out [n_proc*(max_lag-min_lag+1)] fp64,
+ * NaN at the target's own variables; est_out (nullable) [same][1+n_surr],
+ * rows of the target's own variables untouched.  n_proc >= 2,
+ * settings->mode IDTX_MODE_BATCHED. */
+int idtx_bivariate_te(idtx_ctx *ctx, const float *series, int n_proc, int64_t T, int target,
+                      int n_past, int min_lag, int max_lag, const idtx_settings *settings,
+                      double *est_out, double *pval_out, void *stream);
+
 /* ------------------------------------------------------------------------ */
 /* Learned screen (no counterpart in the paper).                            */
 /* A perceptron F -> H -> H -> 1 with ReLU.  Parameters, flat fp32 master    */

@@ -18,7 +18,7 @@ import threading
 import numpy as np
 
 __all__ = ["IdtxError", "Settings", "Context", "load", "cmi_ksg", "cmi_batch", "mte_step",
-           "mte_select_target", "mte_prune", "mte_omnibus", "mte_seqmax", "library_path", "Screen", "screen_predict", "screen_loss_grad",
+           "mte_select_target", "mte_prune", "mte_omnibus", "mte_seqmax", "bivariate_te", "library_path", "Screen", "screen_predict", "screen_loss_grad",
            "screen_train", "screen_set", "StepResult"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -125,9 +125,11 @@ def load():
                                               ctypes.POINTER(i32), vp]
         lib.idtx_mte_omnibus.argtypes = post + [ctypes.POINTER(Step), vp]
         lib.idtx_mte_seqmax.argtypes = post + [vp, vp, vp, vp]
+        lib.idtx_bivariate_te.argtypes = [vp, vp, i32, i64, i32, i32, i32, i32,
+                                          ctypes.POINTER(Settings), vp, vp, vp]
         lib.idtx_ctx_set_kernel.argtypes = [vp, i32]
         lib.idtx_ctx_set_list_caps.argtypes = [vp, i32, i32]
-        for name in ("idtx_mte_prune", "idtx_mte_omnibus", "idtx_mte_seqmax",
+        for name in ("idtx_mte_prune", "idtx_mte_omnibus", "idtx_mte_seqmax", "idtx_bivariate_te",
                      "idtx_ctx_set_kernel", "idtx_ctx_set_list_caps","idtx_screen_predict", "idtx_screen_loss_grad", "idtx_screen_train",
                      "idtx_screen_set", "idtx_ctx_set_profiling", "idtx_ctx_set_graphs",
                      "idtx_ctx_get_stats", "idtx_ctx_reset_stats",
@@ -536,3 +538,21 @@ def mte_seqmax(series, target: int, n_past: int, min_lag: int, max_lag: int, par
                alpha, seed, timeout_ms, ctx, stats.ctypes.data, pvals.ctypes.data,
                sig.ctypes.data)
     return stats[:m], pvals[:m], sig[:m].astype(bool)
+
+
+def bivariate_te(series, target: int, n_past: int, min_lag: int, max_lag: int, k: int = 4,
+                 n_surr: int = 200, seed: int = 0, timeout_ms: int = 0,
+                 ctx: Context | None = None):
+    """Bivariate TE of every source variable: (est [n_cand][1+n_surr], pvals [n_cand]),
+    NaN at the target's own variables (numpy, host)."""
+    a = _Arr(series, name="series")
+    dev = series.device.index if (_is_torch(series) and series.is_cuda) else 0
+    ctx = ctx or default_context(dev or 0)
+    s = _settings(k, n_surr, seed, 0.05, timeout_ms, MODE_BATCHED)
+    n_cand = a.d * (max_lag - min_lag + 1)
+    est = np.full((n_cand, 1 + n_surr), np.nan, np.float64)
+    pvals = np.zeros(n_cand, np.float64)
+    _check(load().idtx_bivariate_te(ctx.handle, a.ptr, a.d, a.n, int(target), int(n_past),
+                                    int(min_lag), int(max_lag), ctypes.byref(s), est.ctypes.data,
+                                    pvals.ctypes.data, _stream_for(series)))
+    return est, pvals

@@ -503,6 +503,25 @@ __global__ void k_min_stat(const double *est, int m, int n_surr, const int32_t *
     }
 }
 
+// Per-candidate p-values against each candidate's own surrogates (bivariate
+// TE): out[c] = #{s : T_s(c) >= T(c)} / S for candidate ids with a row
+// (row_of[c] >= 0), NaN otherwise.  One thread per candidate id.
+__global__ void k_cand_pvals(const double *est, const int32_t *row_of, int n_cand_total,
+                             int n_surr, double *out)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_cand_total) return;
+    const int r = row_of[c];
+    if (r < 0) {
+        out[c] = NAN;
+        return;
+    }
+    const double *row = est + (int64_t)r * (1 + n_surr);
+    int cnt = 0;
+    for (int sidx = 0; sidx < n_surr; ++sidx) cnt += row[1 + sidx] >= row[0] ? 1 : 0;
+    out[c] = (double)cnt / (double)n_surr;
+}
+
 // Single statistic against its own surrogates (omnibus test): p = #{s : T_s >= T} / S.
 __global__ void k_single_stat(const double *est, int n_surr, double alpha, idtx_step *out)
 {
@@ -2778,6 +2797,85 @@ int idtx_mte_seqmax(idtx_ctx *c, const float *series, int n_proc, int64_t T, int
     IDTX_TRY(out(stat_out, stats_d, (size_t)m * 8));
     IDTX_TRY(out(pval_out, pvals_d, (size_t)m * 8));
     IDTX_TRY(out(significant_out, sig_d, (size_t)m * 4));
+    return finish_call(c, st);
+}
+
+int idtx_bivariate_te(idtx_ctx *c, const float *series, int n_proc, int64_t T, int target,
+                      int n_past, int min_lag, int max_lag, const idtx_settings *s,
+                      double *est_out, double *pval_out, void *stream)
+{
+    if (!c) return fail(IDTX_EINVAL, "ctx is NULL");
+    if (!series || !s || !pval_out) return fail(IDTX_EINVAL, "NULL series/settings/pval_out");
+    if (n_proc < 2 || target < 0 || target >= n_proc || n_past < 0 || min_lag < 1 ||
+        max_lag < min_lag)
+        return fail(IDTX_EINVAL, "bad arguments");
+    const int n_lags = max_lag - min_lag + 1;
+    const int n_cand_total = n_proc * n_lags;
+    if (n_cand_total >= (1 << 24)) return fail(IDTX_EINVAL, "too many candidates");
+    const int64_t L = std::max(max_lag, n_past);
+    if (T <= L || T - L > IDTX_MAX_N) return fail(IDTX_EINVAL, "bad T for the lags");
+    if (s->k < 1 || s->k > IDTX_MAX_K || s->k > T - L - 1) return fail(IDTX_EINVAL, "bad k");
+    if (s->n_surr < 1 || s->n_surr >= (1 << 24)) return fail(IDTX_EINVAL, "n_surr out of range");
+    if (s->mode != IDTX_MODE_BATCHED) return fail(IDTX_EINVAL, "only IDTX_MODE_BATCHED");
+    if (n_past > IDTX_MAX_DZ) return fail(IDTX_EINVAL, "n_past exceeds %d", IDTX_MAX_DZ);
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const float *ser = series;
+    if (!device_accessible(series)) {
+        IDTX_TRY(ensure(c, B_IN, (size_t)n_proc * T * sizeof(float)));
+        IDTX_CUDA(cudaMemcpyAsync(c->buf[B_IN], series, (size_t)n_proc * T * sizeof(float),
+                                  cudaMemcpyHostToDevice, st));
+        ser = (const float *)c->buf[B_IN];
+    }
+    IDTX_TRY(ensure_psi(c, std::max<int64_t>(T - L, s->k) + 1, st));
+    IDTX_TRY(begin_call(c, 1, st));
+    std::vector<int32_t> row_of(n_cand_total, -1), ids;
+    std::vector<Group> gs(1);
+    Group &g = gs[0];
+    g.n = T - L;
+    g.dx = 1;
+    g.dy = 1;
+    g.dz = n_past;
+    g.k = s->k;
+    g.ycols.push_back(Col{ser + (int64_t)target * T, L});
+    for (int lag = 1; lag <= n_past; ++lag) g.zcols.push_back(Col{ser + (int64_t)target * T, L - lag});
+    for (int cid = 0; cid < n_cand_total; ++cid) {
+        if (cid / n_lags == target) continue;
+        const int a = (int)ids.size();
+        row_of[cid] = a;
+        ids.push_back(cid);
+        g.xcols.push_back(Col{ser + (int64_t)(cid / n_lags) * T, L - (min_lag + cid % n_lags)});
+        g.jobs.push_back(Job{a, -1});
+        for (int sidx = 0; sidx < s->n_surr; ++sidx) {
+            g.jobs.push_back(Job{a, (int32_t)g.slot_stream.size()});
+            g.slot_stream.push_back((0xC000ull << 48) | ((uint64_t)cid << 24) | (uint64_t)sidx);
+            g.slot_seed.push_back(s->seed);
+        }
+    }
+    IDTX_TRY(plan(c, g));
+    const size_t row = 1 + (size_t)s->n_surr;
+    IDTX_TRY(run_groups(c, gs, st, timeout_of(s), ids.size() * row));
+    const double *est = (const double *)c->buf[B_CMI];
+    IDTX_TRY(ensure(c, B_STEP, align_up((size_t)n_cand_total * 4, 256) + (size_t)n_cand_total * 8));
+    int32_t *row_of_d = (int32_t *)c->buf[B_STEP];
+    double *p_d = (double *)((unsigned char *)c->buf[B_STEP] + align_up((size_t)n_cand_total * 4, 256));
+    IDTX_CUDA(cudaMemcpyAsync(row_of_d, row_of.data(), (size_t)n_cand_total * 4,
+                              cudaMemcpyHostToDevice, st));
+    k_cand_pvals<<<(n_cand_total + 127) / 128, 128, 0, st>>>(est, row_of_d, n_cand_total,
+                                                             s->n_surr, p_d);
+    IDTX_CUDA(cudaGetLastError());
+    c->stats.kernel_launches += 1;
+    const cudaMemcpyKind pk = device_accessible(pval_out) ? cudaMemcpyDeviceToDevice
+                                                         : cudaMemcpyDeviceToHost;
+    IDTX_CUDA(cudaMemcpyAsync(pval_out, p_d, (size_t)n_cand_total * 8, pk, st));
+    if (est_out) {
+        // rows of the source variables only (the target's own rows are left untouched)
+        const cudaMemcpyKind ek = device_accessible(est_out) ? cudaMemcpyDeviceToDevice
+                                                             : cudaMemcpyDeviceToHost;
+        for (size_t a = 0; a < ids.size(); ++a)
+            IDTX_CUDA(cudaMemcpyAsync(est_out + (size_t)ids[a] * row, est + a * row, row * 8, ek,
+                                      st));
+    }
     return finish_call(c, st);
 }
 
