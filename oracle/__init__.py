@@ -94,6 +94,17 @@ def _load():
         lib.orc_bivariate_te.argtypes = [_F32P, ctypes.c_int, ctypes.c_int64, ctypes.c_int,
                                          ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_int, ctypes.c_uint64, _F64P, _F64P]
+        lib.orc_select_past.argtypes = [_F32P, ctypes.c_int, ctypes.c_int64, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_double, ctypes.c_uint64, ctypes.c_int,
+                                        ctypes.POINTER(OrcStep), ctypes.POINTER(ctypes.c_int),
+                                        _I32P, ctypes.POINTER(ctypes.c_int)]
+        lib.orc_select_sources.argtypes = [_F32P, ctypes.c_int, ctypes.c_int64, ctypes.c_int,
+                                           _I32P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                           ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(OrcStep),
+                                           ctypes.POINTER(ctypes.c_int), _I32P,
+                                           ctypes.POINTER(ctypes.c_int)]
         lib.orc_num_threads.restype = ctypes.c_int
         lib.orc_set_num_threads.argtypes = [ctypes.c_int]
         _lib = lib
@@ -309,6 +320,44 @@ def bivariate_te(series, target: int, n_past: int, min_lag: int, max_lag: int, k
     if rc != 0:
         raise ValueError("orc_bivariate_te: invalid arguments")
     return est, pvals
+
+
+def select_past(series, target: int, min_lag: int, max_lag: int, k: int, n_surr: int,
+                alpha: float, seed: int, max_past: int):
+    """Greedy selection of the target's own past: dict(past=[ids], steps=[...])."""
+    s = np.ascontiguousarray(np.asarray(series, np.float32))
+    steps = (OrcStep * (max_past + 1))()
+    n_steps, n_past = ctypes.c_int(), ctypes.c_int()
+    past = np.zeros(max(1, max_past), np.int32)
+    rc = _load().orc_select_past(_fp(s), s.shape[0], s.shape[1], target, min_lag, max_lag, k,
+                                 n_surr, alpha, ctypes.c_uint64(seed), max_past, steps,
+                                 ctypes.byref(n_steps), past.ctypes.data_as(_I32P),
+                                 ctypes.byref(n_past))
+    if rc != 0:
+        raise ValueError("orc_select_past: invalid arguments")
+    return dict(past=[int(c) for c in past[:n_past.value]],
+                steps=[(steps[i].cand, bool(steps[i].significant), steps[i].stat, steps[i].pval)
+                       for i in range(n_steps.value)])
+
+
+def select_sources(series, target: int, past, min_lag: int, max_lag: int, k: int, n_surr: int,
+                   alpha: float, seed: int, max_parents: int):
+    """Greedy source selection given a past (candidate ids): dict(parents=[ids], steps=[...])."""
+    s = np.ascontiguousarray(np.asarray(series, np.float32))
+    pa = np.ascontiguousarray(np.asarray(past, np.int32))
+    steps = (OrcStep * (max_parents + 1))()
+    n_steps, n_par = ctypes.c_int(), ctypes.c_int()
+    parents = np.zeros(max(1, max_parents), np.int32)
+    rc = _load().orc_select_sources(_fp(s), s.shape[0], s.shape[1], target,
+                                    pa.ctypes.data_as(_I32P), len(pa), min_lag, max_lag, k,
+                                    n_surr, alpha, ctypes.c_uint64(seed), max_parents, steps,
+                                    ctypes.byref(n_steps), parents.ctypes.data_as(_I32P),
+                                    ctypes.byref(n_par))
+    if rc != 0:
+        raise ValueError("orc_select_sources: invalid arguments")
+    return dict(parents=[int(c) for c in parents[:n_par.value]],
+                steps=[(steps[i].cand, bool(steps[i].significant), steps[i].stat, steps[i].pval)
+                       for i in range(n_steps.value)])
 
 
 def num_threads() -> int:

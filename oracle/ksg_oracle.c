@@ -405,6 +405,132 @@ int orc_select_target(const float *series, int n_proc, int64_t T, int target, in
 }
 
 /* ------------------------------------------------------------------------ */
+/* Non-uniform target past (the Summary says the greedy conditioning builds  */
+/* a non-uniform embedding; how the target's own past is chosen is a         */
+/* reading): the past is selected first by the same greedy max-statistic    */
+/* loop restricted to the target's own variables (target, lag), lag in      */
+/* [min_lag, max_lag], with Z = the past lags chosen so far (step s uses     */
+/* stream (0xD000+s)<<48 | c<<24 | i); then the sources are selected with Z  */
+/* starting from that past (candidates: every variable not in the past;     */
+/* step s uses stream s<<48 | c<<24 | i).  Samples t in [max_lag, T).        */
+/* Pinned by: source selection from the past (target, 1..n_past) reproduces */
+/* orc_select_target(n_past) exactly (an independent implementation of the  */
+/* same loop); the past of an AR(2) target is its lags 1 and 2.             */
+/* ------------------------------------------------------------------------ */
+static int orc_greedy(const float *series, int n_proc, int64_t T, int target, int min_lag,
+                      int max_lag, const int32_t *init_ids, int n_init, const char *allowed,
+                      uint64_t step_base, int k, int n_surr, double alpha, uint64_t seed,
+                      int max_sel, orc_step *steps, int *n_steps, int32_t *sel, int *n_sel)
+{
+    const int n_lags = max_lag - min_lag + 1, n_all = n_proc * n_lags;
+    const int64_t L = max_lag, n = T - L;
+    char *open_c = (char *)malloc((size_t)n_all);
+    for (int c = 0; c < n_all; ++c) open_c[c] = allowed[c];
+    for (int i = 0; i < n_init; ++i) open_c[init_ids[i]] = 0;
+    float *y = (float *)malloc(sizeof(float) * (size_t)n);
+    float *z = (float *)malloc(sizeof(float) * (size_t)n * (size_t)(n_init + max_sel + 1));
+    float *x = (float *)malloc(sizeof(float) * (size_t)n);
+    float *xp = (float *)malloc(sizeof(float) * (size_t)n);
+    int64_t *pi = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    double *row = (double *)malloc(sizeof(double) * (size_t)n_all * (size_t)(1 + n_surr));
+    orc_gather_lag(series, T, target, 0, L, y);
+    int dz = 0;
+    for (int i = 0; i < n_init; ++i)
+        orc_gather_lag(series, T, init_ids[i] / n_lags, min_lag + init_ids[i] % n_lags, L,
+                       z + (int64_t)dz++ * n);
+    int rc = 0, ns = 0, nsel = 0;
+    while (rc == 0 && nsel < max_sel) {
+        int left = 0;
+        for (int c = 0; c < n_all; ++c) left += open_c[c];
+        if (!left) break;
+        const uint64_t step = step_base + (uint64_t)ns;
+        for (int c = 0; c < n_all && rc == 0; ++c) {
+            if (!open_c[c]) continue;
+            orc_gather_lag(series, T, c / n_lags, min_lag + c % n_lags, L, x);
+            double *r = row + (int64_t)c * (1 + n_surr);
+            rc |= orc_cmi_ksg(x, 1, y, 1, z, dz, n, n, k, &r[0], NULL, NULL);
+            for (int i = 0; i < n_surr && rc == 0; ++i) {
+                orc_perm(seed, (step << 48) | ((uint64_t)c << 24) | (uint64_t)i, n, pi);
+                orc_permute_rows(x, 1, n, n, pi, xp);
+                rc |= orc_cmi_ksg(xp, 1, y, 1, z, dz, n, n, k, &r[1 + i], NULL, NULL);
+            }
+        }
+        if (rc) break;
+        int best = -1;
+        for (int c = 0; c < n_all; ++c)
+            if (open_c[c] && (best < 0 || row[(int64_t)c * (1 + n_surr)] > row[(int64_t)best * (1 + n_surr)]))
+                best = c;
+        const double t_obs = row[(int64_t)best * (1 + n_surr)];
+        int count = 0;
+        for (int i = 0; i < n_surr; ++i) {
+            double t_i = -INFINITY;
+            for (int c = 0; c < n_all; ++c)
+                if (open_c[c] && row[(int64_t)c * (1 + n_surr) + 1 + i] > t_i)
+                    t_i = row[(int64_t)c * (1 + n_surr) + 1 + i];
+            count += t_i >= t_obs;
+        }
+        steps[ns].cand = best;
+        steps[ns].stat = t_obs;
+        steps[ns].pval = (double)count / (double)n_surr;
+        steps[ns].significant = steps[ns].pval < alpha;
+        if (!steps[ns++].significant) break;
+        sel[nsel++] = best;
+        open_c[best] = 0;
+        orc_gather_lag(series, T, best / n_lags, min_lag + best % n_lags, L, z + (int64_t)dz++ * n);
+    }
+    *n_steps = ns;
+    *n_sel = nsel;
+    free(open_c);
+    free(y);
+    free(z);
+    free(x);
+    free(xp);
+    free(pi);
+    free(row);
+    return rc;
+}
+
+/* The target's past: ids of (target, lag) in selection order. */
+int orc_select_past(const float *series, int n_proc, int64_t T, int target, int min_lag,
+                    int max_lag, int k, int n_surr, double alpha, uint64_t seed, int max_past,
+                    orc_step *steps, int *n_steps, int32_t *past, int *n_past)
+{
+    if (!series || n_proc < 1 || target < 0 || target >= n_proc || min_lag < 1 ||
+        max_lag < min_lag || k < 1 || n_surr < 1 || max_past < 0 || !steps || !n_steps ||
+        !past || !n_past || T - max_lag < (int64_t)k + 1)
+        return -1;
+    const int n_lags = max_lag - min_lag + 1;
+    char *allowed = (char *)calloc((size_t)(n_proc * n_lags), 1);
+    for (int c = target * n_lags; c < (target + 1) * n_lags; ++c) allowed[c] = 1;
+    int rc = orc_greedy(series, n_proc, T, target, min_lag, max_lag, NULL, 0, allowed, 0xD000,
+                        k, n_surr, alpha, seed, max_past, steps, n_steps, past, n_past);
+    free(allowed);
+    return rc;
+}
+
+/* Sources given a past (candidate ids, in order; the past is Z's first columns). */
+int orc_select_sources(const float *series, int n_proc, int64_t T, int target,
+                       const int32_t *past, int n_past_ids, int min_lag, int max_lag, int k,
+                       int n_surr, double alpha, uint64_t seed, int max_parents, orc_step *steps,
+                       int *n_steps, int32_t *parents, int *n_parents)
+{
+    if (!series || n_proc < 1 || target < 0 || target >= n_proc || min_lag < 1 ||
+        max_lag < min_lag || k < 1 || n_surr < 1 || max_parents < 0 || n_past_ids < 0 ||
+        (n_past_ids > 0 && !past) || !steps || !n_steps || !parents || !n_parents ||
+        T - max_lag < (int64_t)k + 1)
+        return -1;
+    const int n_all = n_proc * (max_lag - min_lag + 1);
+    for (int i = 0; i < n_past_ids; ++i)
+        if (past[i] < 0 || past[i] >= n_all) return -1;
+    char *allowed = (char *)malloc((size_t)n_all);
+    memset(allowed, 1, (size_t)n_all);
+    int rc = orc_greedy(series, n_proc, T, target, min_lag, max_lag, past, n_past_ids, allowed, 0,
+                        k, n_surr, alpha, seed, max_parents, steps, n_steps, parents, n_parents);
+    free(allowed);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Tests after the greedy selection (Summary, paragraph 3: the errors of     */
 /* testing many sources must be controlled; the paper describes no test).    */
 /* Readings, for a target, its past Z0 (lags 1..n_past) and a selected       */

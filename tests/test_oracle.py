@@ -466,3 +466,31 @@ def test_bivariate_te_finds_drivers_and_matches_the_greedy_estimates():
     sel = oracle.select_target(s, 0, 1, 1, 1, 4, 3, 0.05, 11, 1, want_first_step=True)
     for c in range(1, 6):
         assert est[c, 0] == sel["first_step"][c, 0]
+
+
+# ---------------------------------------------------------------- non-uniform target past
+def test_source_selection_from_a_uniform_past_equals_select_target():
+    """Two implementations of the greedy loop: starting the source selection
+    from the past (target, lags 1..n_past) reproduces select_target(n_past)."""
+    net = synth.var_network(n_nodes=4, order=3, T=900, density=0.5, weight=0.6, seed=17)
+    for target, n_past in ((0, 2), (2, 1), (3, 3)):
+        ref = oracle.select_target(net.series, target, n_past, 1, 3, 4, 15, 0.05, 8, 4)
+        past = [target * 3 + lag - 1 for lag in range(1, n_past + 1)]
+        got = oracle.select_sources(net.series, target, past, 1, 3, 4, 15, 0.05, 8, 4)
+        assert got["parents"] == ref["parents"]
+        assert got["steps"] == ref["steps"]
+
+
+def test_past_of_an_ar2_target_is_its_first_two_lags():
+    rng = np.random.default_rng(2)
+    T = 1500
+    x = np.zeros((2, T + 100))
+    e = rng.standard_normal((2, T + 100))
+    for t in range(2, T + 100):
+        x[0, t] = 0.6 * x[0, t - 1] - 0.4 * x[0, t - 2] + e[0, t]
+        x[1, t] = e[1, t]
+    s = x[:, 100:].astype(np.float32)
+    r = oracle.select_past(s, 0, 1, 4, 4, 30, 0.05, 5, 4)
+    assert sorted(r["past"]) == [0, 1]            # ids of (target, lag 1) and (target, lag 2)
+    assert r["steps"][-1][1] is False             # stopped by a non-significant step
+    assert all(c < 4 for (c, _, _, _) in r["steps"])   # only the target's own variables
