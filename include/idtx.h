@@ -277,6 +277,27 @@ int idtx_mte_select_target(idtx_ctx *ctx, const float *series, int n_proc, int64
                            int max_parents, int32_t *parents_out, int *n_parents,
                            idtx_step *steps_out, int *n_steps, void *stream);
 
+/* Non-uniform target past (the paper's Summary says the greedy conditioning
+ * builds a non-uniform embedding; how the target's own past is chosen is a
+ * reading).  idtx_mte_select_past runs the greedy loop of idtx_mte_step over
+ * the target's own variables (target, lag), lag in [min_lag, max_lag], only,
+ * with Z = the past chosen so far (step s: step_index 0xD000 + s, n_past 0):
+ *   past_out [max_past] candidate ids in selection order, *n_past;
+ *   steps_out [max_past+1] every executed step, *n_steps.
+ * idtx_mte_select_sources then selects sources with Z starting from that past
+ * (past[0..n_past_ids), candidate ids, in order; step s: step_index s,
+ * n_past 0): every candidate not in the past competes, as in
+ * idtx_mte_select_target, whose result it reproduces exactly when past holds
+ * the target's lags 1..n_past.  Samples t in [max_lag, T). */
+int idtx_mte_select_past(idtx_ctx *ctx, const float *series, int n_proc, int64_t T, int target,
+                         int min_lag, int max_lag, const idtx_settings *settings, int max_past,
+                         int32_t *past_out, int *n_past, idtx_step *steps_out, int *n_steps,
+                         void *stream);
+int idtx_mte_select_sources(idtx_ctx *ctx, const float *series, int n_proc, int64_t T, int target,
+                            const int32_t *past, int n_past_ids, int min_lag, int max_lag,
+                            const idtx_settings *settings, int max_parents, int32_t *parents_out,
+                            int *n_parents, idtx_step *steps_out, int *n_steps, void *stream);
+
 /* Tests after the greedy selection (the paper's Summary asks that the errors
  * of testing many sources be controlled, and describes no test; these are
  * readings).  Common arguments as for idtx_mte_step; parents[0..n_parents)

@@ -18,7 +18,8 @@ import threading
 import numpy as np
 
 __all__ = ["IdtxError", "Settings", "Context", "load", "cmi_ksg", "cmi_batch", "mte_step",
-           "mte_select_target", "mte_prune", "mte_omnibus", "mte_seqmax", "bivariate_te", "library_path", "Screen", "screen_predict", "screen_loss_grad",
+           "mte_select_target", "mte_prune", "mte_omnibus", "mte_seqmax", "bivariate_te",
+           "mte_select_past", "mte_select_sources", "library_path", "Screen", "screen_predict", "screen_loss_grad",
            "screen_train", "screen_set", "StepResult"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -127,9 +128,18 @@ def load():
         lib.idtx_mte_seqmax.argtypes = post + [vp, vp, vp, vp]
         lib.idtx_bivariate_te.argtypes = [vp, vp, i32, i64, i32, i32, i32, i32,
                                           ctypes.POINTER(Settings), vp, vp, vp]
+        lib.idtx_mte_select_past.argtypes = [vp, vp, i32, i64, i32, i32, i32,
+                                             ctypes.POINTER(Settings), i32, vp,
+                                             ctypes.POINTER(i32), ctypes.POINTER(Step),
+                                             ctypes.POINTER(i32), vp]
+        lib.idtx_mte_select_sources.argtypes = [vp, vp, i32, i64, i32, vp, i32, i32, i32,
+                                                ctypes.POINTER(Settings), i32, vp,
+                                                ctypes.POINTER(i32), ctypes.POINTER(Step),
+                                                ctypes.POINTER(i32), vp]
         lib.idtx_ctx_set_kernel.argtypes = [vp, i32]
         lib.idtx_ctx_set_list_caps.argtypes = [vp, i32, i32]
         for name in ("idtx_mte_prune", "idtx_mte_omnibus", "idtx_mte_seqmax", "idtx_bivariate_te",
+                     "idtx_mte_select_past", "idtx_mte_select_sources",
                      "idtx_ctx_set_kernel", "idtx_ctx_set_list_caps","idtx_screen_predict", "idtx_screen_loss_grad", "idtx_screen_train",
                      "idtx_screen_set", "idtx_ctx_set_profiling", "idtx_ctx_set_graphs",
                      "idtx_ctx_get_stats", "idtx_ctx_reset_stats",
@@ -556,3 +566,50 @@ def bivariate_te(series, target: int, n_past: int, min_lag: int, max_lag: int, k
                                     int(min_lag), int(max_lag), ctypes.byref(s), est.ctypes.data,
                                     pvals.ctypes.data, _stream_for(series)))
     return est, pvals
+
+
+def _steps_list(steps, n):
+    return [StepResult(int(steps[i].cand), bool(steps[i].significant), float(steps[i].stat),
+                       float(steps[i].pval), int(steps[i].n_cand), int(steps[i].n_full),
+                       int(steps[i].surr_done)) for i in range(n)]
+
+
+def mte_select_past(series, target: int, min_lag: int, max_lag: int, k: int = 4,
+                    n_surr: int = 200, alpha: float = 0.05, seed: int = 0, max_past: int = 5,
+                    timeout_ms: int = 0, mode: int = MODE_BATCHED, ctx: Context | None = None):
+    """Greedy selection of the target's own past: dict(past=[ids], steps=[...])."""
+    a = _Arr(series, name="series")
+    dev = series.device.index if (_is_torch(series) and series.is_cuda) else 0
+    ctx = ctx or default_context(dev or 0)
+    s = _settings(k, n_surr, seed, alpha, timeout_ms, mode)
+    past = np.zeros(max(1, max_past), np.int32)
+    steps = (Step * (max_past + 1))()
+    n_past, n_steps = ctypes.c_int(), ctypes.c_int()
+    _check(load().idtx_mte_select_past(ctx.handle, a.ptr, a.d, a.n, int(target), int(min_lag),
+                                       int(max_lag), ctypes.byref(s), int(max_past),
+                                       past.ctypes.data, ctypes.byref(n_past), steps,
+                                       ctypes.byref(n_steps), _stream_for(series)))
+    return dict(past=[int(c) for c in past[:n_past.value]], steps=_steps_list(steps, n_steps.value))
+
+
+def mte_select_sources(series, target: int, past, min_lag: int, max_lag: int, k: int = 4,
+                       n_surr: int = 200, alpha: float = 0.05, seed: int = 0,
+                       max_parents: int = 10, timeout_ms: int = 0, mode: int = MODE_BATCHED,
+                       ctx: Context | None = None):
+    """Greedy source selection given a past (candidate ids): dict(parents=[ids], steps=[...])."""
+    a = _Arr(series, name="series")
+    dev = series.device.index if (_is_torch(series) and series.is_cuda) else 0
+    ctx = ctx or default_context(dev or 0)
+    s = _settings(k, n_surr, seed, alpha, timeout_ms, mode)
+    pa = np.ascontiguousarray(np.asarray(past, np.int32))
+    parents = np.zeros(max(1, max_parents), np.int32)
+    steps = (Step * (max_parents + 1))()
+    n_par, n_steps = ctypes.c_int(), ctypes.c_int()
+    _check(load().idtx_mte_select_sources(ctx.handle, a.ptr, a.d, a.n, int(target),
+                                          pa.ctypes.data if len(pa) else None, len(pa),
+                                          int(min_lag), int(max_lag), ctypes.byref(s),
+                                          int(max_parents), parents.ctypes.data,
+                                          ctypes.byref(n_par), steps, ctypes.byref(n_steps),
+                                          _stream_for(series)))
+    return dict(parents=[int(c) for c in parents[:n_par.value]],
+                steps=_steps_list(steps, n_steps.value))

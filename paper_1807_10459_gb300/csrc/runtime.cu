@@ -2080,10 +2080,16 @@ int idtx_cmi_batch(idtx_ctx *c, const idtx_problem *probs, int n_probs, int k, d
     return finish_call(c, st);
 }
 
-int idtx_mte_step(idtx_ctx *c, const float *series, int n_proc, int64_t T, int target, int n_past,
+}  // extern "C"
+
+namespace {
+
+// One greedy step; allowed (nullable) [n_proc * n_lags] limits the candidates
+// to the ids it marks (the target-past selection uses the target's own).
+int mte_step_impl(idtx_ctx *c, const float *series, int n_proc, int64_t T, int target, int n_past,
                   int min_lag, int max_lag, const int32_t *selected, int n_selected,
                   int step_index, const idtx_settings *s, idtx_step *result, double *est_out,
-                  void *stream)
+                  const char *allowed, void *stream)
 {
     if (!c) return fail(IDTX_EINVAL, "ctx is NULL");
     if (!s || !result || !series) return fail(IDTX_EINVAL, "NULL settings/result/series");
@@ -2114,6 +2120,8 @@ int idtx_mte_step(idtx_ctx *c, const float *series, int n_proc, int64_t T, int t
     std::vector<char> alive(n_cand_total, 1);
     for (int lag = min_lag; lag <= std::min(max_lag, n_past); ++lag)
         alive[target * n_lags + (lag - min_lag)] = 0;
+    if (allowed)
+        for (int cid = 0; cid < n_cand_total; ++cid) alive[cid] &= allowed[cid];
     for (int t = 0; t < n_selected; ++t) {
         if (selected[t] < 0 || selected[t] >= n_cand_total)
             return fail(IDTX_EINVAL, "selected id %d out of range", selected[t]);
@@ -2321,6 +2329,19 @@ int idtx_mte_step(idtx_ctx *c, const float *series, int n_proc, int64_t T, int t
                                           kind, st));
     }
     return finish_call(c, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+int idtx_mte_step(idtx_ctx *c, const float *series, int n_proc, int64_t T, int target, int n_past,
+                  int min_lag, int max_lag, const int32_t *selected, int n_selected,
+                  int step_index, const idtx_settings *s, idtx_step *result, double *est_out,
+                  void *stream)
+{
+    return mte_step_impl(c, series, n_proc, T, target, n_past, min_lag, max_lag, selected,
+                         n_selected, step_index, s, result, est_out, nullptr, stream);
 }
 
 // ------------------------------------------------------------------ learned screen
@@ -2566,6 +2587,95 @@ int idtx_mte_select_target(idtx_ctx *c, const float *series, int n_proc, int64_t
         cudaFree(dev_series);
     }
     return rc;
+}
+
+namespace {
+
+// Greedy loop over the candidates `allowed` marks (nullable: all), Z
+// starting from init[0..n_init) (candidate ids), step s with step index
+// step_base + s.  The series is copied to the device once if needed.
+int greedy_loop(idtx_ctx *c, const float *series, int n_proc, int64_t T, int target, int min_lag,
+                int max_lag, const int32_t *init, int n_init, const char *allowed,
+                int step_base, const idtx_settings *s, int max_sel, int32_t *sel_out,
+                int *n_sel, idtx_step *steps_out, int *n_steps, void *stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    const float *ser = series;
+    void *dev_series = nullptr;
+    if (!device_accessible(series)) {
+        IDTX_CUDA(cudaMalloc(&dev_series, (size_t)n_proc * T * sizeof(float)));
+        cudaError_t e = cudaMemcpyAsync(dev_series, series, (size_t)n_proc * T * sizeof(float),
+                                        cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) {
+            cudaFree(dev_series);
+            return fail(IDTX_ECUDA, "series copy failed: %s", cudaGetErrorString(e));
+        }
+        ser = (const float *)dev_series;
+    }
+    const int n_all = n_proc * (max_lag - min_lag + 1);
+    std::vector<int32_t> zsel(init, init + n_init);
+    int n_left = 0;
+    for (int cid = 0; cid < n_all; ++cid)
+        n_left += (!allowed || allowed[cid]) &&
+                  std::find(zsel.begin(), zsel.end(), cid) == zsel.end();
+    int rc = IDTX_OK;
+    for (int step = 0; step < max_sel && n_left > 0; ++step) {
+        idtx_step r;
+        rc = mte_step_impl(c, ser, n_proc, T, target, 0, min_lag, max_lag, zsel.data(),
+                           (int)zsel.size(), step_base + step, s, &r, nullptr, allowed, stream);
+        if (rc != IDTX_OK) break;
+        steps_out[(*n_steps)++] = r;
+        if (!r.significant) break;
+        zsel.push_back(r.cand);
+        sel_out[(*n_sel)++] = r.cand;
+        --n_left;
+    }
+    if (dev_series) {
+        cudaStreamSynchronize(st);
+        cudaFree(dev_series);
+    }
+    return rc;
+}
+
+}  // namespace
+
+int idtx_mte_select_past(idtx_ctx *c, const float *series, int n_proc, int64_t T, int target,
+                         int min_lag, int max_lag, const idtx_settings *s, int max_past,
+                         int32_t *past_out, int *n_past, idtx_step *steps_out, int *n_steps,
+                         void *stream)
+{
+    if (!c) return fail(IDTX_EINVAL, "ctx is NULL");
+    if (!series || max_past < 0 || !n_past || !n_steps || !steps_out ||
+        (max_past > 0 && !past_out))
+        return fail(IDTX_EINVAL, "bad arguments");
+    if (n_proc < 1 || target < 0 || target >= n_proc || min_lag < 1 || max_lag < min_lag)
+        return fail(IDTX_EINVAL, "bad target or lags");
+    *n_past = 0;
+    *n_steps = 0;
+    DeviceGuard guard(c->device);
+    const int n_lags = max_lag - min_lag + 1;
+    std::vector<char> allowed((size_t)n_proc * n_lags, 0);
+    for (int l = 0; l < n_lags; ++l) allowed[(size_t)target * n_lags + l] = 1;
+    return greedy_loop(c, series, n_proc, T, target, min_lag, max_lag, nullptr, 0, allowed.data(),
+                       0xD000, s, max_past, past_out, n_past, steps_out, n_steps, stream);
+}
+
+int idtx_mte_select_sources(idtx_ctx *c, const float *series, int n_proc, int64_t T, int target,
+                            const int32_t *past, int n_past_ids, int min_lag, int max_lag,
+                            const idtx_settings *s, int max_parents, int32_t *parents_out,
+                            int *n_parents, idtx_step *steps_out, int *n_steps, void *stream)
+{
+    if (!c) return fail(IDTX_EINVAL, "ctx is NULL");
+    if (!series || max_parents < 0 || !n_parents || !n_steps || !steps_out ||
+        (max_parents > 0 && !parents_out) || n_past_ids < 0 || (n_past_ids > 0 && !past))
+        return fail(IDTX_EINVAL, "bad arguments");
+    if (n_proc < 1 || target < 0 || target >= n_proc || min_lag < 1 || max_lag < min_lag)
+        return fail(IDTX_EINVAL, "bad target or lags");
+    *n_parents = 0;
+    *n_steps = 0;
+    DeviceGuard guard(c->device);
+    return greedy_loop(c, series, n_proc, T, target, min_lag, max_lag, past, n_past_ids, nullptr,
+                       0, s, max_parents, parents_out, n_parents, steps_out, n_steps, stream);
 }
 
 

@@ -76,3 +76,38 @@ def test_bivariate_te_rejects_bad_arguments(idtx):
         idtx.bivariate_te(net.series[:1], 0, 1, 1, 2)       # no source process
     with pytest.raises(idtx.IdtxError):
         idtx.bivariate_te(net.series, 5, 1, 1, 2)           # target out of range
+
+
+def _steps_equal(got, ref):
+    assert [s[:2] for s in got] == [s[:2] for s in ref]
+    assert [s[3] for s in got] == [s[3] for s in ref]
+    for a, b in zip(got, ref):
+        assert abs(a[2] - b[2]) < TOL
+
+
+def test_target_past_selection_matches_oracle(idtx):
+    net = synth.var_network(n_nodes=4, order=3, T=1200, density=0.5, weight=0.6, seed=23)
+    kw = dict(k=4, n_surr=20, alpha=0.05, seed=3)
+    for target in (0, 2):
+        ref = oracle.select_past(net.series, target, 1, 4, max_past=4, **kw)
+        got = idtx.mte_select_past(torch.from_numpy(net.series).cuda(), target, 1, 4,
+                                   max_past=4, **kw)
+        assert got["past"] == ref["past"]
+        _steps_equal(got["steps"], ref["steps"])
+        # then the sources, from that (non-uniform) past
+        ref_s = oracle.select_sources(net.series, target, ref["past"], 1, 4, max_parents=4, **kw)
+        got_s = idtx.mte_select_sources(net.series, target, got["past"], 1, 4, max_parents=4,
+                                        **kw)
+        assert got_s["parents"] == ref_s["parents"]
+        _steps_equal(got_s["steps"], ref_s["steps"])
+
+
+def test_sources_from_a_uniform_past_equal_select_target(idtx):
+    net = synth.var_network(n_nodes=4, order=3, T=900, density=0.5, weight=0.6, seed=17)
+    kw = dict(k=4, n_surr=15, alpha=0.05, seed=8, max_parents=4)
+    for target, n_past in ((0, 2), (3, 3)):
+        a = idtx.mte_select_target(net.series, target, n_past, 1, 3, **kw)
+        past = [target * 3 + lag - 1 for lag in range(1, n_past + 1)]
+        b = idtx.mte_select_sources(net.series, target, past, 1, 3, **kw)
+        assert a["parents"] == b["parents"]
+        assert [tuple(s) for s in a["steps"]] == [tuple(s) for s in b["steps"]]
