@@ -105,6 +105,10 @@ def _load():
                                            ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(OrcStep),
                                            ctypes.POINTER(ctypes.c_int), _I32P,
                                            ctypes.POINTER(ctypes.c_int)]
+        lib.orc_cmi_surrogates_reps.argtypes = [_F32P, ctypes.c_int, _F32P, ctypes.c_int, _F32P,
+                                                ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
+                                                ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                                ctypes.c_int64, _F64P]
         lib.orc_num_threads.restype = ctypes.c_int
         lib.orc_set_num_threads.argtypes = [ctypes.c_int]
         _lib = lib
@@ -212,6 +216,20 @@ def cmi_surrogates(x, y, z, k: int, n_surr: int, seed: int) -> np.ndarray:
                                     ctypes.c_uint64(seed), out.ctypes.data_as(_F64P))
     if rc != 0:
         raise ValueError("orc_cmi_surrogates: invalid arguments")
+    return out
+
+
+def cmi_surrogates_reps(x, y, z, k: int, n_surr: int, seed: int, n_reps: int) -> np.ndarray:
+    """[1+n_surr]: the estimate and its replication-level surrogates."""
+    x, dx = _cols(x)
+    n = x.shape[1]
+    y, dy = _cols(y)
+    z, dz = _cols(z, n)
+    out = np.empty(1 + n_surr, np.float64)
+    rc = _load().orc_cmi_surrogates_reps(_fp(x), dx, _fp(y), dy, _fp(z), dz, n, n, k, n_surr,
+                                         ctypes.c_uint64(seed), n_reps, out.ctypes.data_as(_F64P))
+    if rc != 0:
+        raise ValueError("orc_cmi_surrogates_reps: invalid arguments")
     return out
 
 

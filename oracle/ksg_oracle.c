@@ -277,6 +277,36 @@ int orc_cmi_surrogates(const float *x, int dx, const float *y, int dy, const flo
     return rc;
 }
 
+/* Replication-level surrogates (a reading of the surrogates the Summary     */
+/* mentions, for data made of n_reps replications of len = n / n_reps        */
+/* consecutive samples): surrogate s moves whole replications of X,          */
+/* X_s[r*len + t] = X[pi_s(r)*len + t], pi_s the permutation of [0, n_reps)  */
+/* keyed (seed, stream = s) as above; Y and Z stay.                          */
+/* Pinned by: with n_reps = n (one sample per replication) it is the         */
+/* sample-level orc_cmi_surrogates exactly.                                  */
+int orc_cmi_surrogates_reps(const float *x, int dx, const float *y, int dy, const float *z, int dz,
+                            int64_t n, int64_t ld, int k, int n_surr, uint64_t seed, int64_t n_reps,
+                            double *out)
+{
+    if (n_surr < 0 || !out || n_reps < 1 || n % n_reps != 0) return -1;
+    if (orc_cmi_ksg(x, dx, y, dy, z, dz, n, ld, k, &out[0], NULL, NULL) != 0) return -1;
+    const int64_t len = n / n_reps;
+    float *xs = (float *)malloc(sizeof(float) * (size_t)dx * (size_t)ld);
+    int64_t *pr = (int64_t *)malloc(sizeof(int64_t) * (size_t)n_reps);
+    int64_t *pi = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    int rc = 0;
+    for (int s = 0; s < n_surr && rc == 0; ++s) {
+        orc_perm(seed, (uint64_t)s, n_reps, pr);
+        for (int64_t i = 0; i < n; ++i) pi[i] = pr[i / len] * len + i % len;
+        orc_permute_rows(x, dx, n, ld, pi, xs);
+        rc = orc_cmi_ksg(xs, dx, y, dy, z, dz, n, ld, k, &out[1 + s], NULL, NULL);
+    }
+    free(xs);
+    free(pr);
+    free(pi);
+    return rc;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Greedy parent selection for one target with max-statistic gating         */
 /* (Summary, paragraph 4: parents are added by maximising a CMI criterion;   */

@@ -494,3 +494,25 @@ def test_past_of_an_ar2_target_is_its_first_two_lags():
     assert sorted(r["past"]) == [0, 1]            # ids of (target, lag 1) and (target, lag 2)
     assert r["steps"][-1][1] is False             # stopped by a non-significant step
     assert all(c < 4 for (c, _, _, _) in r["steps"])   # only the target's own variables
+
+
+# ---------------------------------------------------------------- replication-level surrogates
+def test_replication_surrogates_with_single_sample_replications_are_sample_surrogates():
+    g = synth.gaussian_problem(240, 1, 1, 2, seed=6)
+    a = oracle.cmi_surrogates_reps(g.x, g.y, g.z, 4, 6, 13, n_reps=240)
+    b = oracle.cmi_surrogates(g.x, g.y, g.z, 4, 6, 13)
+    assert np.array_equal(a, b)
+
+
+def test_replication_surrogates_move_whole_replications():
+    """A surrogate equals the estimate with X's replications reordered by the
+    permutation of the replication indices."""
+    g = synth.gaussian_problem(300, 2, 1, 1, seed=7)
+    reps, length = 12, 25
+    out = oracle.cmi_surrogates_reps(g.x, g.y, g.z, 4, 3, 21, n_reps=reps)
+    for s in range(3):
+        pr = oracle.perm(21, s, reps)
+        idx = (pr[:, None] * length + np.arange(length)[None, :]).ravel()
+        assert out[1 + s] == oracle.cmi_ksg(g.x[:, idx], g.y, g.z, 4)
+    with pytest.raises(ValueError):
+        oracle.cmi_surrogates_reps(g.x, g.y, g.z, 4, 3, 21, n_reps=7)   # 300 % 7 != 0
