@@ -216,6 +216,18 @@ int idtx_cmi_ksg(idtx_ctx *ctx, const float *x, int dx, const float *y, int dy, 
                  int dz, int64_t n, int64_t ld, const idtx_settings *settings, double *cmi_out,
                  float *eps_out, int32_t *counts_out, void *stream);
 
+/* idtx_cmi_ksg with replication-level surrogates (a reading of the paper's
+ * surrogates for data made of n_reps replications, e.g. trials, of
+ * len = n / n_reps consecutive samples): surrogate s moves whole
+ * replications of X, X_s[r*len + t] = X[pi_s(r)*len + t], pi_s the
+ * Fisher-Yates permutation of [0, n_reps) keyed (seed, stream s) as above; Y
+ * and Z stay.  n_reps must divide n (n_reps = n gives idtx_cmi_ksg's
+ * surrogates exactly).  Other arguments and outputs as idtx_cmi_ksg. */
+int idtx_cmi_ksg_reps(idtx_ctx *ctx, const float *x, int dx, const float *y, int dy,
+                      const float *z, int dz, int64_t n, int64_t ld, int64_t n_reps,
+                      const idtx_settings *settings, double *cmi_out, float *eps_out,
+                      int32_t *counts_out, void *stream);
+
 /* One problem of a batch: its own columns, shape, surrogate count and seed. */
 typedef struct {
     const float *x, *y, *z;

@@ -103,6 +103,8 @@ def load():
         lib.idtx_cmi_ksg.argtypes = [vp, vp, i32, vp, i32, vp, i32, i64, i64,
                                      ctypes.POINTER(Settings), vp, vp, vp, vp]
         lib.idtx_cmi_batch.argtypes = [vp, ctypes.POINTER(Problem), i32, i32, vp, vp]
+        lib.idtx_cmi_ksg_reps.argtypes = [vp, vp, i32, vp, i32, vp, i32, i64, i64, i64,
+                                          ctypes.POINTER(Settings), vp, vp, vp, vp]
         lib.idtx_mte_step.argtypes = [vp, vp, i32, i64, i32, i32, i32, i32, vp, i32, i32,
                                       ctypes.POINTER(Settings), ctypes.POINTER(Step), vp, vp]
         lib.idtx_mte_select_target.argtypes = [vp, vp, i32, i64, i32, i32, i32, i32,
@@ -138,7 +140,7 @@ def load():
                                                 ctypes.POINTER(i32), vp]
         lib.idtx_ctx_set_kernel.argtypes = [vp, i32]
         lib.idtx_ctx_set_list_caps.argtypes = [vp, i32, i32]
-        for name in ("idtx_mte_prune", "idtx_mte_omnibus", "idtx_mte_seqmax", "idtx_bivariate_te",
+        for name in ("idtx_cmi_ksg_reps", "idtx_mte_prune", "idtx_mte_omnibus", "idtx_mte_seqmax", "idtx_bivariate_te",
                      "idtx_mte_select_past", "idtx_mte_select_sources",
                      "idtx_ctx_set_kernel", "idtx_ctx_set_list_caps","idtx_screen_predict", "idtx_screen_loss_grad", "idtx_screen_train",
                      "idtx_screen_set", "idtx_ctx_set_profiling", "idtx_ctx_set_graphs",
@@ -387,12 +389,13 @@ def _settings(k, n_surr, seed, alpha=0.05, timeout_ms=0, mode=MODE_BATCHED):
 
 def cmi_ksg(x, y, z=None, k: int = 4, n_surr: int = 0, seed: int = 0, want_eps: bool = False,
             want_counts: bool = False, timeout_ms: int = 0, mode: int = MODE_BATCHED,
-            ctx: Context | None = None):
+            n_reps: int = 0, ctx: Context | None = None):
     """One KSG estimate of I(X;Y|Z) plus ``n_surr`` surrogates.
 
     x, y, z: [d][N] float32 (1-D means d = 1; z may be None).  Returns the
     [1+n_surr] fp64 estimates, and (if asked) eps [1+n_surr][N] and counts
     [1+n_surr][3][N] (n_xz, n_yz, n_z), as CUDA tensors when x is one, else numpy.
+    n_reps > 0: surrogates permute n_reps whole replications of X (n_reps divides N).
     """
     ax, ay, az = _Arr(x, name="x"), _Arr(y, name="y"), _Arr(z, name="z")
     n = ax.n
@@ -404,8 +407,13 @@ def cmi_ksg(x, y, z=None, k: int = 4, n_surr: int = 0, seed: int = 0, want_eps: 
     eps, p_eps = _out((1 + n_surr, n), np.float32, x) if want_eps else (None, None)
     cnt, p_cnt = _out((1 + n_surr, 3, n), np.int32, x) if want_counts else (None, None)
     s = _settings(k, n_surr, seed, timeout_ms=timeout_ms, mode=mode)
-    _check(load().idtx_cmi_ksg(ctx.handle, ax.ptr, ax.d, ay.ptr, ay.d, az.ptr, az.d, n, n,
-                               ctypes.byref(s), p_cmi, p_eps, p_cnt, _stream_for(x, y, z)))
+    if n_reps:   # replication-level surrogates
+        _check(load().idtx_cmi_ksg_reps(ctx.handle, ax.ptr, ax.d, ay.ptr, ay.d, az.ptr, az.d, n,
+                                        n, int(n_reps), ctypes.byref(s), p_cmi, p_eps, p_cnt,
+                                        _stream_for(x, y, z)))
+    else:
+        _check(load().idtx_cmi_ksg(ctx.handle, ax.ptr, ax.d, ay.ptr, ay.d, az.ptr, az.d, n, n,
+                                   ctypes.byref(s), p_cmi, p_eps, p_cnt, _stream_for(x, y, z)))
     if want_eps or want_counts:
         out = [cmi]
         if want_eps:

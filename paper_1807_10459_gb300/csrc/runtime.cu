@@ -291,6 +291,20 @@ __global__ void __launch_bounds__(32)
 
 // xi[grp][j][g*dxb + d] = X_job[d][pi_job(order[j])] (job = grp*gb + g; jobs
 // past the end repeat job 0), 0 for d >= dx, +inf for j >= n.
+// Replication-level surrogates: slot s's permutation of the samples moves
+// whole replications of len samples, perm[s][r*len + t] = blk[s][r]*len + t,
+// blk[s] the permutation of the n_reps replications.
+__global__ void k_expand_reps(const int32_t *blk, int n_slots, int64_t n_reps, int64_t len,
+                              int32_t *perm)
+{
+    const int64_t n = n_reps * len, total = (int64_t)n_slots * n;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t slot = idx / n, i = idx - slot * n;
+        perm[idx] = (int32_t)((int64_t)blk[slot * n_reps + i / len] * len + i % len);
+    }
+}
+
 __global__ void k_gather_x(const Col *xc, int dx, int dxb, const Job *jobs, int n_jobs,
                            const int32_t *perm, int64_t n, int64_t n_pad, int gb, int n_groups,
                            const int32_t *order, float *xi, int *err)
@@ -892,6 +906,7 @@ struct Group {
     bool sort = false;   // order the samples along a Morton curve first
     bool plain = false;  // one launch per estimate (IDTX_MODE_PLAIN)
     int work_slot = 0;   // index of the group's work counters in the call
+    int64_t n_reps = 0;     // > 0: surrogates permute n_reps whole replications
     bool use_list = false;  // run the list kernel (ksg_list.cuh)
     bool tune = false;      // time both kernels first (shape not tuned yet)
     int cap_a = 0, cap_b = 0;  // list capacities
@@ -1017,7 +1032,7 @@ CallBuffers bytes_of(const Group &g)
         b.sort_tmp = align_up(tmp, 256);
     }
     b.xi = align_up((size_t)g.n_groups * g.n_pad * g.v->gb * g.v->dx * sizeof(float), 256);
-    b.perm = align_up(g.slot_stream.size() * (size_t)g.n * sizeof(int32_t), 256);
+    b.perm = align_up(g.slot_stream.size() * (size_t)(g.n + g.n_reps) * sizeof(int32_t), 256);
     b.partial = align_up(g.jobs.size() * (size_t)g.n_qt * sizeof(double), 256);
     if (g.use_list || g.tune) b.lists = list_bytes(g.n, g.cap_a, g.cap_b);
     return b;
@@ -1193,7 +1208,17 @@ int prep_group(idtx_ctx *c, const Group &g, cudaStream_t st, const Slices &sl, f
         IDTX_CUDA(cudaStreamWaitEvent(c->side_stream, fork, 0));
         xs = c->side_stream;
     }
-    if (n_slots > 0) IDTX_TRY(enqueue_permutations(perm, streams, seeds, n_slots, g.n, xs, launches));
+    if (n_slots > 0 && g.n_reps > 0) {
+        // permutations of the replications after the sample rows, then expanded
+        int32_t *blk = perm + (int64_t)n_slots * g.n;
+        IDTX_TRY(enqueue_permutations(blk, streams, seeds, n_slots, g.n_reps, xs, launches));
+        k_expand_reps<<<grid_for((int64_t)n_slots * g.n, 256), 256, 0, xs>>>(
+            blk, n_slots, g.n_reps, g.n / g.n_reps, perm);
+        IDTX_CUDA(cudaGetLastError());
+        launches += 1;
+    } else if (n_slots > 0) {
+        IDTX_TRY(enqueue_permutations(perm, streams, seeds, n_slots, g.n, xs, launches));
+    }
     k_gather_x<<<grid_for((int64_t)g.n_groups * g.n_pad * v.gb * v.dx, 256), 256, 0, xs>>>(
         xc, g.dx, v.dx, jobs, n_jobs, perm, g.n, g.n_pad, v.gb, g.n_groups, order, xi, c->d_err);
     IDTX_CUDA(cudaGetLastError());
@@ -1783,9 +1808,10 @@ int idtx_ctx_destroy(idtx_ctx *c)
     return IDTX_OK;
 }
 
-int idtx_cmi_ksg(idtx_ctx *c, const float *x, int dx, const float *y, int dy, const float *z,
-                 int dz, int64_t n, int64_t ld, const idtx_settings *s, double *cmi_out,
-                 float *eps_out, int32_t *counts_out, void *stream)
+static int cmi_ksg_impl(idtx_ctx *c, const float *x, int dx, const float *y, int dy,
+                        const float *z, int dz, int64_t n, int64_t ld, int64_t n_reps,
+                        const idtx_settings *s, double *cmi_out, float *eps_out,
+                        int32_t *counts_out, void *stream)
 {
     if (!c) return fail(IDTX_EINVAL, "ctx is NULL");
     if (!s) return fail(IDTX_EINVAL, "settings is NULL");
@@ -1851,6 +1877,7 @@ int idtx_cmi_ksg(idtx_ctx *c, const float *x, int dx, const float *y, int dy, co
         g.slot_seed.push_back(s->seed);
     }
     g.plain = s->mode == IDTX_MODE_PLAIN;
+    g.n_reps = n_reps;
     IDTX_TRY(plan(c, g));
     std::vector<unsigned char> arena;
     pack_desc(gs, arena);
@@ -1887,6 +1914,24 @@ int idtx_cmi_ksg(idtx_ctx *c, const float *x, int dx, const float *y, int dy, co
         IDTX_CUDA(cudaMemcpyAsync(counts_out, cnt_d, (size_t)n_jobs * 3 * n * sizeof(int32_t),
                                   cudaMemcpyDeviceToHost, st));
     return finish_call(c, st);
+}
+
+int idtx_cmi_ksg(idtx_ctx *c, const float *x, int dx, const float *y, int dy, const float *z,
+                 int dz, int64_t n, int64_t ld, const idtx_settings *s, double *cmi_out,
+                 float *eps_out, int32_t *counts_out, void *stream)
+{
+    return cmi_ksg_impl(c, x, dx, y, dy, z, dz, n, ld, 0, s, cmi_out, eps_out, counts_out, stream);
+}
+
+int idtx_cmi_ksg_reps(idtx_ctx *c, const float *x, int dx, const float *y, int dy, const float *z,
+                      int dz, int64_t n, int64_t ld, int64_t n_reps, const idtx_settings *s,
+                      double *cmi_out, float *eps_out, int32_t *counts_out, void *stream)
+{
+    if (n_reps < 1 || n_reps > n || (n_reps > 0 && n % n_reps != 0))
+        return fail(IDTX_EINVAL, "n_reps=%lld must divide n=%lld", (long long)n_reps,
+                    (long long)n);
+    return cmi_ksg_impl(c, x, dx, y, dy, z, dz, n, ld, n_reps, s, cmi_out, eps_out, counts_out,
+                        stream);
 }
 
 int idtx_cmi_batch(idtx_ctx *c, const idtx_problem *probs, int n_probs, int k, double *out,

@@ -111,3 +111,27 @@ def test_sources_from_a_uniform_past_equal_select_target(idtx):
         b = idtx.mte_select_sources(net.series, target, past, 1, 3, **kw)
         assert a["parents"] == b["parents"]
         assert [tuple(s) for s in a["steps"]] == [tuple(s) for s in b["steps"]]
+
+
+@pytest.mark.parametrize("n,reps,dims", [(600, 20, (1, 1, 2)), (1000, 50, (2, 1, 3)),
+                                         (240, 240, (1, 1, 1)), (3000, 60, (1, 1, 2))])
+def test_replication_surrogates_match_oracle(idtx, n, reps, dims):
+    g = synth.gaussian_problem(n, *dims, seed=n + reps)
+    ref = oracle.cmi_surrogates_reps(g.x, g.y, g.z, 4, 12, 5, n_reps=reps)
+    for kern in (idtx.KERNEL_TILE, idtx.KERNEL_LIST):
+        ctx = idtx.Context(0)
+        ctx.set_kernel(kern)
+        got = idtx.cmi_ksg(torch.from_numpy(g.x).cuda(), torch.from_numpy(g.y).cuda(),
+                           torch.from_numpy(g.z).cuda(), k=4, n_surr=12, seed=5, n_reps=reps,
+                           ctx=ctx).cpu().numpy()
+        assert np.max(np.abs(got - ref)) < TOL
+    if reps == n:    # one sample per replication: the sample-level surrogates
+        plain = idtx.cmi_ksg(g.x, g.y, g.z, k=4, n_surr=12, seed=5)
+        assert np.array_equal(plain, idtx.cmi_ksg(g.x, g.y, g.z, k=4, n_surr=12, seed=5,
+                                                  n_reps=reps))
+
+
+def test_replication_count_must_divide_n(idtx):
+    g = synth.gaussian_problem(300, 1, 1, 1, seed=1)
+    with pytest.raises(idtx.IdtxError):
+        idtx.cmi_ksg(g.x, g.y, g.z, k=4, n_surr=3, n_reps=7)
