@@ -333,6 +333,12 @@ def run_ours(args):
                 "peak_basis": f"{N_SMS} SMs x {LANES_PER_SM} lanes x median SM clock "
                               f"{sm_mhz:.0f} MHz under load (issue-slot peak)",
                 "fused_share_of_step": st["fused_ms"] / ms if ms else None,
+                # the same launch against the brute-force shared-Y/Z work per estimate,
+                # N(N-1)[(4(dy+dz)+2)/(C(1+S)) + 4dx + 9] with dx=dy=1, dz=3 (context: the
+                # kernel's lists skip most of that work, so this exceeds the issue peak)
+                "brute_force_equivalent_tops": (
+                    (w["T"] - 5) * (w["T"] - 6) * (18.0 / est_per_step + 13.0) * est_per_step *
+                    args.steps / (st["fused_ms"] / 1e3) / 1e12) if st["fused_ms"] else None,
                 "list_caps": [st["list_cap_a"], st["list_cap_b"]] if used == "list" else None,
                 "scanned_fraction_of_exhaustive":
                     ((st["scanned_a"] + st["scanned_b"]) / st["exhaustive_pairs"])

@@ -60,6 +60,11 @@
 #ifndef IDTX_LIST_NW
 #define IDTX_LIST_NW 4
 #endif
+// Jobs of a warp whose count walk goes on past the others' (the largest
+// eps) and is finished with the lanes splitting its entries.
+#ifndef IDTX_LIST_TAIL
+#define IDTX_LIST_TAIL 2
+#endif
 #ifndef IDTX_LIST_MINB
 #define IDTX_LIST_MINB 0
 #endif
@@ -99,6 +104,7 @@ __device__ __forceinline__ void ksg_list_cta(const KsgLaunch &a, const int qt, c
     const float kInf = CUDART_INF_F;
 
     constexpr int SA = IDTX_LIST_SA, SB = IDTX_LIST_SB;  // entries per sub-chunk of the walks
+    constexpr int TAIL = IDTX_LIST_TAIL;  // jobs finished after the warp's shared count walk
     __shared__ double s_term[QC][GB];  // digamma term of (query, job)
     __shared__ double s_red[NWS][GB];
     __shared__ __align__(16) int2 s_ent[NW][32];  // per warp: staged list entries
@@ -132,6 +138,7 @@ __device__ __forceinline__ void ksg_list_cta(const KsgLaunch &a, const int qt, c
     };
 
     unsigned long long walk_a = 0, walk_b = 0, brute_a = 0, brute_b = 0, fallbacks = 0;  // per warp
+    unsigned long long tail_b = 0;  // (job, entry) pairs of the count walks' tails
     const long long t_begin = clock64();
 
     while (true) {
@@ -266,10 +273,25 @@ __device__ __forceinline__ void ksg_list_cta(const KsgLaunch &a, const int qt, c
         // Every list A entry below eps lies in the walked prefix (the walk
         // went on until each job's k-th value was at most the next entry).
         if (job_ok && !fb) nyz = list_lower(la, walked_a, eps);
-        // List B up to the largest eps of the jobs it serves (ascending, so
-        // the walk stops at the first entry at or beyond it); n_z is then the
-        // number of walked entries below the job's eps (binary search).
-        const float emax = warp_max((job_ok && !fb) ? eps : -1.0f);
+        // The warp walks list B up to the (TAIL+1)-th largest eps of the jobs
+        // it serves (ascending, so the walk stops at the first entry at or
+        // beyond it); the at most TAIL jobs with a larger eps -- the long
+        // tail of the walk -- finish afterwards one at a time, the 32 lanes
+        // splitting their remaining entries.  n_z is the number of entries
+        // below the job's eps (binary search).
+        const float ev = (job_ok && !fb) ? eps : -1.0f;
+        float emax;
+        {
+            float cur = ev;
+#pragma unroll 1
+            for (int t = 0; t < TAIL; ++t) {
+                const float mx = warp_max(cur);
+                const uint32_t who = __ballot_sync(kFull, cur == mx);
+                if (lane == __ffs(who) - 1) cur = -1.0f;
+            }
+            emax = warp_max(cur);
+        }
+        const bool tail = ev > emax;
         int walked_b = 0;
         {
             int2 nxt = len_b > 0 ? __ldg(lb + lane) : sentinel;
@@ -303,7 +325,36 @@ __device__ __forceinline__ void ksg_list_cta(const KsgLaunch &a, const int qt, c
         }
         if (walked_b > len_b) walked_b = len_b;
         walk_b += walked_b;
-        if (job_ok && !fb) nz = list_lower(lb, walked_b, eps);
+        if (job_ok && !fb && !tail) nz = list_lower(lb, walked_b, eps);
+        uint32_t tmask = __ballot_sync(kFull, tail);
+        while (tmask) {
+            const int f = __ffs(tmask) - 1;
+            tmask &= tmask - 1;
+            const float ef = __shfl_sync(kFull, eps, f);
+            float xf[DX];
+#pragma unroll
+            for (int d = 0; d < DX; ++d) xf[d] = __shfl_sync(kFull, xq[d], f);
+            const float *xgf = xg - lane * DX + f * DX;
+            // every entry below `end` has d_Z < ef; those before walked_b are counted
+            const int end = list_lower(lb, len_b, ef);
+            int cnt = 0;
+#pragma unroll 4
+            for (int e = walked_b + lane; e < end; e += 32) {
+                const int j = __ldg(&lb[e].x);
+                const float *xr = xgf + static_cast<int64_t>(j) * XW;
+                float dx = fabsf(xf[0] - xr[0]);
+#pragma unroll
+                for (int d = 1; d < DX; ++d) dx = fmaxf(dx, fabsf(xf[d] - xr[d]));
+                cnt += dx < ef ? 1 : 0;
+            }
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) cnt += __shfl_xor_sync(kFull, cnt, off);
+            if (lane == f) {
+                nxz += cnt;
+                nz = end;
+            }
+            tail_b += end > walked_b ? end - walked_b : 0;
+        }
         // Jobs whose eps reaches past a list: counts by a full scan, the 32
         // lanes splitting the samples of one such job at a time.
         uint32_t bmask = __ballot_sync(kFull, fb);
@@ -382,6 +433,7 @@ __device__ __forceinline__ void ksg_list_cta(const KsgLaunch &a, const int qt, c
         atomicAdd(&a.work[2], brute_a);
         atomicAdd(&a.work[3], brute_b);
         atomicAdd(&a.work[4], fallbacks);
+        atomicAdd(&a.work[6], tail_b);
         atomicAdd(&a.work[5], static_cast<unsigned long long>(clock64() - t_begin));
     }
     __syncthreads();
