@@ -151,6 +151,7 @@ typedef struct {
     int64_t tune_trials;
     int32_t list_cap_a, list_cap_b;  /* list capacities of the last list launch */
     double list_tail_b;  /* (job, entry) pairs of count walks finished lane-split (2dx+2 lane-ops each) */
+    double list_tail_a;  /* the same for the neighbour walks */
 } idtx_stats;
 
 /* Enable (1) or disable (0) event timing of the fused kernel. */

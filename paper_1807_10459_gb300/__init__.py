@@ -66,7 +66,7 @@ class Stats(ctypes.Structure):
                 ("list_walk_b", ctypes.c_double), ("brute_samples", ctypes.c_double),
                 ("fallbacks", ctypes.c_double), ("tune_trials", ctypes.c_int64),
                 ("list_cap_a", ctypes.c_int32), ("list_cap_b", ctypes.c_int32),
-                ("list_tail_b", ctypes.c_double)]
+                ("list_tail_b", ctypes.c_double), ("list_tail_a", ctypes.c_double)]
 
 
 class Step(ctypes.Structure):

@@ -65,6 +65,9 @@
 #ifndef IDTX_LIST_TAIL
 #define IDTX_LIST_TAIL 2
 #endif
+#ifndef IDTX_LIST_TAIL_A
+#define IDTX_LIST_TAIL_A 2
+#endif
 #ifndef IDTX_LIST_MINB
 #define IDTX_LIST_MINB 0
 #endif
@@ -105,6 +108,7 @@ __device__ __forceinline__ void ksg_list_cta(const KsgLaunch &a, const int qt, c
 
     constexpr int SA = IDTX_LIST_SA, SB = IDTX_LIST_SB;  // entries per sub-chunk of the walks
     constexpr int TAIL = IDTX_LIST_TAIL;  // jobs finished after the warp's shared count walk
+    constexpr int TAIL_A = IDTX_LIST_TAIL_A;  // and after its shared neighbour walk
     __shared__ double s_term[QC][GB];  // digamma term of (query, job)
     __shared__ double s_red[NWS][GB];
     __shared__ __align__(16) int2 s_ent[NW][32];  // per warp: staged list entries
@@ -139,6 +143,7 @@ __device__ __forceinline__ void ksg_list_cta(const KsgLaunch &a, const int qt, c
 
     unsigned long long walk_a = 0, walk_b = 0, brute_a = 0, brute_b = 0, fallbacks = 0;  // per warp
     unsigned long long tail_b = 0;  // (job, entry) pairs of the count walks' tails
+    unsigned long long tail_a = 0;  // (job, entry) pairs of the neighbour walks' tails
     const long long t_begin = clock64();
 
     while (true) {
@@ -175,6 +180,7 @@ __device__ __forceinline__ void ksg_list_cta(const KsgLaunch &a, const int qt, c
         for (int t = 0; t < KH; ++t) h[t] = kInf;
         float th = job_ok ? kInf : -1.0f;  // padding jobs never insert
         int walked_a = 0;
+        uint32_t amask = 0;  // jobs the shared walk left to finish lane-split
         {
             int2 nxt = len_a > 0 ? __ldg(la + lane) : sentinel;
             for (int e = 0; e < len_a; e += 32) {
@@ -186,8 +192,15 @@ __device__ __forceinline__ void ksg_list_cta(const KsgLaunch &a, const int qt, c
                 int u = 0;
                 for (; u < 32; u += SA) {
                     // Ascending list: once the sub-chunk's first entry is out
-                    // of every job's reach, so is everything after it.
-                    if (__all_sync(kFull, !(__int_as_float(ent[u].y) < th))) break;
+                    // of a job's reach, so is everything after it.  When at
+                    // most TAIL_A jobs are still in reach the shared walk
+                    // stops and those finish lane-split below.
+                    const uint32_t act =
+                        __ballot_sync(kFull, __int_as_float(ent[u].y) < th);
+                    if (__popc(act) <= TAIL_A) {
+                        amask = act;
+                        break;
+                    }
                     int jj[SA];
                     float dyz[SA], dd[SA];
 #pragma unroll
@@ -215,6 +228,47 @@ __device__ __forceinline__ void ksg_list_cta(const KsgLaunch &a, const int qt, c
         }
         if (walked_a > len_a) walked_a = len_a;
         walk_a += walked_a;
+        // Lane-split finish of the remaining jobs, one at a time: blocks of 32
+        // entries, one per lane; the distances below the job's k-th value are
+        // inserted smallest first (warp minimum), until a block starts out
+        // of reach.  my_walked: the prefix of list A this lane's job walked.
+        int my_walked = walked_a;
+        while (amask) {
+            const int f = __ffs(amask) - 1;
+            amask &= amask - 1;
+            float xf[DX];
+#pragma unroll
+            for (int d = 0; d < DX; ++d) xf[d] = __shfl_sync(kFull, xq[d], f);
+            const float *xgf = xg - lane * DX + f * DX;
+            float thf = __shfl_sync(kFull, th, f);
+            int pos = walked_a;
+            for (; pos < len_a; pos += 32) {
+                // pos is a multiple of 16, so the block may end past the written
+                // sentinels: lanes beyond the list take a sentinel
+                const int2 en = pos + lane < len_a ? __ldg(la + pos + lane) : sentinel;
+                const float dyz = __int_as_float(en.y);
+                if (!(__shfl_sync(kFull, dyz, 0) < thf)) break;
+                const float *xr = xgf + static_cast<int64_t>(en.x) * XW;
+                float dx = fabsf(xf[0] - xr[0]);
+#pragma unroll
+                for (int d = 1; d < DX; ++d) dx = fmaxf(dx, fabsf(xf[d] - xr[d]));
+                float cand = fmaxf(dx, dyz);
+                if (!(cand < thf)) cand = kInf;
+                while (true) {
+                    const float mn = warp_min(cand);
+                    if (!(mn < thf)) break;
+                    const uint32_t who = __ballot_sync(kFull, cand == mn);
+                    if (lane == __ffs(who) - 1) cand = kInf;
+                    if (lane == f) {
+                        sorted_insert<KH>(h, mn);
+                        th = kth(h);
+                    }
+                    thf = __shfl_sync(kFull, th, f);
+                }
+                tail_a += 32;
+            }
+            if (lane == f) my_walked = pos < len_a ? pos : len_a;
+        }
         // The list ran out before the job's k-th distance dropped to r_A:
         // recompute those jobs over every sample.  For each such job the 32
         // lanes split the samples, keep their own k smallest, and the warp
@@ -272,7 +326,7 @@ __device__ __forceinline__ void ksg_list_cta(const KsgLaunch &a, const int qt, c
         int nz = 0, nyz = 0, nxz = 0;
         // Every list A entry below eps lies in the walked prefix (the walk
         // went on until each job's k-th value was at most the next entry).
-        if (job_ok && !fb) nyz = list_lower(la, walked_a, eps);
+        if (job_ok && !fb) nyz = list_lower(la, my_walked, eps);
         // The warp walks list B up to the (TAIL+1)-th largest eps of the jobs
         // it serves (ascending, so the walk stops at the first entry at or
         // beyond it); the at most TAIL jobs with a larger eps -- the long
@@ -434,6 +488,7 @@ __device__ __forceinline__ void ksg_list_cta(const KsgLaunch &a, const int qt, c
         atomicAdd(&a.work[3], brute_b);
         atomicAdd(&a.work[4], fallbacks);
         atomicAdd(&a.work[6], tail_b);
+        atomicAdd(&a.work[7], tail_a);
         atomicAdd(&a.work[5], static_cast<unsigned long long>(clock64() - t_begin));
     }
     __syncthreads();

@@ -1640,8 +1640,8 @@ int finish_call(idtx_ctx *c, cudaStream_t st)
             // List kernel, per job: a list A entry costs 2dx+2 (X distance,
             // max with d_YZ, compare), a list B entry 2dx+4 (X distance, two
             // compares, two adds); a full-scan sample 2(dx+dy+dz')+2 (pass A)
-            // or +6 (pass B); a (job, entry) pair of a count walk's tail 2dx+2
-            // (X distance, compare, add).  Counters: walked A, walked B,
+            // or +6 (pass B); a (job, entry) pair of a walk's lane-split tail
+            // 2dx+2 (X distance, max or compare, compare or add).  Counters: walked A, walked B,
             // full-scan samples of pass A, of pass B, fallbacks, cycles, tail
             // pairs.
             const double dall = 2.0 * (ws.dx + ws.dy + ws.dz_eff);
@@ -1649,8 +1649,10 @@ int finish_call(idtx_ctx *c, cudaStream_t st)
                                                (double)k[1] * (2.0 * ws.dx + 4.0) +
                                                (double)k[2] * (dall + 2.0) +
                                                (double)k[3] * (dall + 6.0)) +
-                                      (double)k[6] * (2.0 * ws.dx + 2.0);
+                                      (double)k[6] * (2.0 * ws.dx + 2.0) +
+                                      (double)k[7] * (2.0 * ws.dx + 2.0);
             c->stats.list_tail_b += (double)k[6];
+            c->stats.list_tail_a += (double)k[7];
             c->stats.list_walk_a += (double)k[0];
             c->stats.list_walk_b += (double)k[1];
             c->stats.brute_samples += (double)(k[2] + k[3]);
