@@ -34,7 +34,7 @@ N_SMS = 152
 # Tile kernel: profiles/ksg_fused_kernel_greedy_step_small.md (15-surrogate case,
 # 31.68 MB, scaled by job groups 296/24).  List kernel:
 # profiles/ksg_list_kernel_greedy_step_small.md (full-size launch, captured directly).
-TRAFFIC_BYTES = {"tile": 390.7e6, "list": 2.566e9}
+TRAFFIC_BYTES = {"tile": 390.7e6, "list": 2.626e9}
 LANES_PER_SM = 128  # 4 sub-partitions x 32 lanes: one warp instruction per clock each
 
 WORKLOAD = dict(n_proc=10, order=5, T=10000, n_past=3, min_lag=1, max_lag=5, k=4, n_surr=200,
