@@ -516,3 +516,36 @@ def test_replication_surrogates_move_whole_replications():
         assert out[1 + s] == oracle.cmi_ksg(g.x[:, idx], g.y, g.z, 4)
     with pytest.raises(ValueError):
         oracle.cmi_surrogates_reps(g.x, g.y, g.z, 4, 3, 21, n_reps=7)   # 300 % 7 != 0
+
+
+# ---------------------------------------------------------------- multivariate MI inference
+def test_mi_inference_steps_are_ksg_mi_then_cmi_of_the_embedded_columns():
+    """With no target past the first greedy step estimates, per candidate, the
+    plain KSG MI (algorithm 1) of the lagged source column with the target's
+    present; the second step's statistic conditions on the first parent's
+    column only.  Both are recomputed here from an embedding built by hand
+    (samples t = max_lag .. T-1) with the independent numpy brute force."""
+    net = synth.var_network(n_nodes=3, order=2, T=400, density=0.6, weight=0.7, seed=23)
+    s = net.series
+    target, lo, hi, k = 1, 1, 2, 4
+    sel = oracle.select_target(s, target, 0, lo, hi, k, 20, 0.05, 5, 2, want_first_step=True)
+    T = s.shape[1]
+    n = T - hi
+    y = s[target, hi:][None, :]
+
+    def col(c):
+        p, lag = divmod(c, hi - lo + 1)
+        lag += lo
+        return s[p, hi - lag:T - lag][None, :]
+
+    psi = scipy.special.digamma
+    for c in range(3 * (hi - lo + 1)):
+        _, nx, ny, _ = numpy_bruteforce(col(c), y, None, k)
+        mi = psi(k) + psi(n) - np.mean(psi(nx + 1.0) + psi(ny + 1.0))
+        assert abs(sel["first_step"][c, 0] - mi) < 1e-12
+    assert len(sel["steps"]) >= 2 and sel["steps"][0][1]
+    first, second = sel["steps"][0][0], sel["steps"][1][0]
+    assert sel["steps"][0][2] == np.max(sel["first_step"][:, 0])
+    _, nxz, nyz, nz = numpy_bruteforce(col(second), y, col(first), k)
+    cmi = psi(k) + np.mean(psi(nz + 1.0) - psi(nxz + 1.0) - psi(nyz + 1.0))
+    assert abs(sel["steps"][1][2] - cmi) < 1e-12
