@@ -342,14 +342,16 @@ def run_ours(args):
                 "list_caps": [st["list_cap_a"], st["list_cap_b"]] if used == "list" else None,
                 "scanned_fraction_of_exhaustive":
                     ((st["scanned_a"] + st["scanned_b"]) / st["exhaustive_pairs"])
-                    if st["exhaustive_pairs"] else None,
+                    if st["exhaustive_pairs"] and used == "tile" else None,
                 "work_per_step": {k: st[k] / args.steps for k in
-                                  (("list_walk_a", "list_walk_b", "brute_samples", "fallbacks")
+                                  (("list_walk_a", "list_walk_b", "list_tail_a", "list_tail_b",
+                                    "brute_samples", "fallbacks")
                                    if used == "list" else
                                    ("scanned_a", "passed_a", "scanned_b", "passed_b"))},
                 "ops_basis": ("lane-ops per job of the list entries each (query, group of 32 "
                               "jobs) walks (2dx+2 in the neighbour pass, 2dx+4 in the count "
-                              "pass) and of full-scan fallback samples (counted in-kernel)")
+                              "pass), per (job, entry) pair of the lane-split tails (2dx+2) "
+                              "and of full-scan fallback samples (counted in-kernel)")
                              if used == "list" else
                              ("lane-ops the kernel's algorithm needs for the tiles it scans: "
                               "shared scan per (query, reference, job group) plus per-job work "
