@@ -584,7 +584,9 @@ int orc_select_sources(const float *series, int n_proc, int64_t T, int target,
 /* Pinned by: an independent noise source added to true parents is pruned   */
 /* and the true parents kept; the omnibus test of true parents is            */
 /* significant and of independent noise is not; with one parent the three   */
-/* statistics equal the greedy step's estimate of that candidate.            */
+/* statistics equal the greedy step's estimate of that candidate; a test     */
+/* rebuilds every round, statistic and decision from orc_cmi_ksg and the     */
+/* shuffle by the rules above.                                               */
 /* ------------------------------------------------------------------------ */
 #define ORC_TAG_PRUNE 0x9000u
 #define ORC_TAG_OMNIBUS 0xA000u

@@ -549,3 +549,71 @@ def test_mi_inference_steps_are_ksg_mi_then_cmi_of_the_embedded_columns():
     _, nxz, nyz, nz = numpy_bruteforce(col(second), y, col(first), k)
     cmi = psi(k) + np.mean(psi(nz + 1.0) - psi(nxz + 1.0) - psi(nyz + 1.0))
     assert abs(sel["steps"][1][2] - cmi) < 1e-12
+
+
+# ------------------------------------------ tests after selection, recomputed
+def _loo_table(s, parents, tag, n_past, seed, k, n_surr):
+    """Leave-one-out statistics and their surrogates, assembled here from the
+    pinned estimator and permutations (lag-1 candidates: candidate id =
+    node): row i = [T_i, T_i,0 .. T_i,S-1]."""
+    T = s.shape[1]
+    L = max(1, n_past)
+    y = s[0, L:]
+    past = [s[0, L - lag:T - lag] for lag in range(1, n_past + 1)]
+    col = lambda c: s[c, L - 1:T - 1][None, :]
+    out = np.zeros((len(parents), 1 + n_surr))
+    for i, c in enumerate(parents):
+        z = np.stack(past + [col(d)[0] for j, d in enumerate(parents) if j != i])
+        out[i, 0] = oracle.cmi_ksg(col(c), y, z, k)
+        for t in range(n_surr):
+            pi = oracle.perm(seed, (tag << 48) | (c << 24) | t, T - L)
+            out[i, 1 + t] = oracle.cmi_ksg(col(c)[:, pi], y, z, k)
+    return out
+
+
+def test_pruning_omnibus_and_seqmax_recomputed_from_the_estimator():
+    """The three tests' decisions and statistics follow from the estimates by
+    the stated rules: pruning by the minimum statistic (round r tagged
+    0x9000 + r), the omnibus test of the parents jointly, the step-down
+    maximum statistic (tag 0xB000)."""
+    s = _driven_system(T=400, seed=9)
+    kw = dict(POST, n_surr=12, seed=4)
+    S, alpha, seed, k = kw["n_surr"], kw["alpha"], kw["seed"], kw["k"]
+    parents = [1, 3, 4, 2]
+
+    # pruning, round by round
+    ref = oracle.prune(s, parents=parents, **kw)
+    cur, rounds = list(parents), []
+    while cur:
+        e = _loo_table(s, cur, 0x9000 + len(rounds), 1, seed, k, S)
+        at = int(np.argmin(e[:, 0]))                   # first index among ties
+        p = np.count_nonzero(e[:, 1:].min(axis=0) >= e[at, 0]) / S
+        rounds.append((cur[at], p < alpha, e[at, 0], p))
+        if p < alpha:
+            break
+        cur.pop(at)
+    assert ref["kept"] == cur
+    assert ref["rounds"] == rounds
+
+    # omnibus: the parents' columns permuted together
+    T = s.shape[1]
+    x = np.stack([s[c, 0:T - 1] for c in parents])
+    y, z = s[0, 1:], s[0, 0:T - 1][None, :]
+    t_obs = oracle.cmi_ksg(x, y, z, k)
+    surr = [oracle.cmi_ksg(x[:, oracle.perm(seed, (0xA000 << 48) | (0xFFFFFF << 24) | t, T - 1)],
+                           y, z, k) for t in range(S)]
+    p = np.count_nonzero(np.array(surr) >= t_obs) / S
+    assert oracle.omnibus(s, parents=parents, **kw) == (t_obs, p, p < alpha)
+
+    # sequential maximum statistic
+    e = _loo_table(s, parents, 0xB000, 1, seed, k, S)
+    order = sorted(range(len(parents)), key=lambda i: (-e[i, 0], i))
+    pv, sig, still = np.zeros(len(parents)), np.zeros(len(parents), bool), True
+    for r, i in enumerate(order):
+        mx = e[order[r:], 1:].max(axis=0)
+        pv[i] = np.count_nonzero(mx >= e[i, 0]) / S
+        still = still and pv[i] < alpha
+        sig[i] = still
+    stats, pvals, sigs = oracle.seqmax(s, parents=parents, **kw)
+    assert np.array_equal(stats, e[:, 0])
+    assert np.array_equal(pvals, pv) and np.array_equal(np.asarray(sigs, bool), sig)
