@@ -617,3 +617,22 @@ def test_pruning_omnibus_and_seqmax_recomputed_from_the_estimator():
     stats, pvals, sigs = oracle.seqmax(s, parents=parents, **kw)
     assert np.array_equal(stats, e[:, 0])
     assert np.array_equal(pvals, pv) and np.array_equal(np.asarray(sigs, bool), sig)
+
+
+def test_bivariate_te_surrogates_and_pvalues_recomputed():
+    """Each source's surrogates are its column permuted with stream
+    0xC000 << 48 | c << 24 | s, and p(c) counts the surrogates at or above
+    the estimate."""
+    s = _driven_system(T=300, seed=13)
+    S, seed, k = 9, 6, 4
+    est, p = oracle.bivariate_te(s, 0, 1, 1, 1, k, S, seed)
+    T = s.shape[1]
+    y, z = s[0, 1:], s[0, 0:T - 1][None, :]
+    for c in (1, 4):
+        x = s[c, 0:T - 1][None, :]
+        assert est[c, 0] == oracle.cmi_ksg(x, y, z, k)
+        for t in (0, S - 1):
+            pi = oracle.perm(seed, (0xC000 << 48) | (c << 24) | t, T - 1)
+            assert est[c, 1 + t] == oracle.cmi_ksg(x[:, pi], y, z, k)
+    for c in range(1, 6):
+        assert p[c] == np.count_nonzero(est[c, 1:] >= est[c, 0]) / S
