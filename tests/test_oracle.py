@@ -636,3 +636,42 @@ def test_bivariate_te_surrogates_and_pvalues_recomputed():
             assert est[c, 1 + t] == oracle.cmi_ksg(x[:, pi], y, z, k)
     for c in range(1, 6):
         assert p[c] == np.count_nonzero(est[c, 1:] >= est[c, 0]) / S
+
+
+def test_target_past_selection_recomputed():
+    """The greedy loop over the target's own lags, rebuilt here step by step
+    from the pinned estimator and shuffle: step s tags its streams 0xD000 + s,
+    the first maximum wins, p counts surrogate maxima at or above it."""
+    rng = np.random.default_rng(8)
+    T, lo, hi, k, S, seed, alpha = 350, 1, 3, 4, 10, 3, 0.05
+    x = np.zeros((2, T + 100))
+    e = rng.standard_normal((2, T + 100))
+    for t in range(2, T + 100):
+        x[0, t] = 0.5 * x[0, t - 1] - 0.4 * x[0, t - 2] + e[0, t]
+        x[1, t] = e[1, t]
+    s = x[:, 100:].astype(np.float32)
+    ref = oracle.select_past(s, 0, lo, hi, k, S, alpha, seed, hi - lo + 1)
+    n = T - hi
+    y = s[0, hi:][None, :]
+    col = lambda c: s[0, hi - (lo + c):T - (lo + c)][None, :]   # c = lag - lo (target 0)
+    open_c, zcols, steps = list(range(hi - lo + 1)), [], []
+    while open_c:
+        z = np.stack(zcols) if zcols else None
+        tab = {}
+        for c in open_c:
+            row = [oracle.cmi_ksg(col(c), y, z, k)]
+            for i in range(S):
+                pi = oracle.perm(seed, ((0xD000 + len(steps)) << 48) | (c << 24) | i, n)
+                row.append(oracle.cmi_ksg(col(c)[:, pi], y, z, k))
+            tab[c] = row
+        best = max(open_c, key=lambda c: (tab[c][0], -c))
+        t_obs = tab[best][0]
+        p = sum(max(tab[c][1 + i] for c in open_c) >= t_obs for i in range(S)) / S
+        steps.append((best, p < alpha, t_obs, p))
+        if p >= alpha:
+            break
+        open_c.remove(best)
+        zcols.append(col(best)[0])
+    assert ref["steps"] == steps
+    assert ref["past"] == [c for (c, sig, _, _) in steps if sig]
+    assert len(steps) >= 2
