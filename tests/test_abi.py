@@ -1,5 +1,6 @@
 """CPU checks of the C-ABI library: it builds for sm_103a, loads without a GPU,
-and exports every function include/idtx.h declares.  No compute calls."""
+exports every function include/idtx.h declares, and rejects NULL arguments
+before any CUDA call.  No compute calls."""
 import ctypes
 import os
 import re
@@ -50,3 +51,48 @@ def test_package_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(m, "_lib", None)
     with pytest.raises(RuntimeError):
         m.load()
+
+
+_CTYPES = {"int": ctypes.c_int, "int64_t": ctypes.c_int64, "uint64_t": ctypes.c_uint64,
+           "double": ctypes.c_double, "float": ctypes.c_float}
+
+
+def declared_prototypes():
+    """name -> list of ctypes argument types, from the header's prototypes."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    out = {}
+    for m in re.finditer(r"\bint\s+(idtx_[a-z0-9_]+)\s*\(([^;]*?)\)\s*;", text, flags=re.S):
+        args = " ".join(m.group(2).split())
+        types = []
+        if args != "void":
+            for a in args.split(","):
+                a = a.strip()
+                if "*" in a:
+                    types.append(ctypes.c_void_p)
+                else:
+                    base = a.replace("const ", "").split()[0]
+                    types.append(_CTYPES[base])
+        out[m.group(1)] = types
+    return out
+
+
+def test_every_entry_point_rejects_null_arguments_without_touching_the_gpu(lib):
+    """Argument checks come before any CUDA call: with a NULL context (or
+    NULL settings for the context-free call) every entry point returns
+    IDTX_EINVAL with a message; destroying a NULL context is a no-op."""
+    protos = declared_prototypes()
+    assert len(protos) >= 25
+    lib.idtx_last_error.restype = ctypes.c_char_p
+    for name, types in protos.items():
+        if name == "idtx_version":
+            continue
+        fn = getattr(lib, name)
+        fn.argtypes = types
+        fn.restype = ctypes.c_int
+        args = [None if t is ctypes.c_void_p else t(0) for t in types]
+        rc = fn(*args)
+        if name == "idtx_ctx_destroy":
+            assert rc == 0
+            continue
+        assert rc == 1, (name, rc)                   # IDTX_EINVAL
+        assert lib.idtx_last_error(), name
