@@ -675,3 +675,20 @@ def test_target_past_selection_recomputed():
     assert ref["steps"] == steps
     assert ref["past"] == [c for (c, sig, _, _) in steps if sig]
     assert len(steps) >= 2
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 7, 33])
+def test_smallest_problems_every_k(n):
+    """Edge sizes: N from 2 (a single neighbour) upward, every k up to N-1
+    (eps = the largest joint distance), against the numpy brute force, and
+    the estimate against the digamma sum of those counts."""
+    g = synth.gaussian_problem(n, 1, 2, 2, seed=40 + n)
+    for k in range(1, n):
+        got = oracle.ksg_counts(g.x, g.y, g.z, k)
+        ref = numpy_bruteforce(g.x, g.y, g.z, k)
+        for a, b in zip(got, ref):
+            assert np.array_equal(a, b)
+        psi = scipy.special.digamma
+        eps, nxz, nyz, nz = got
+        want = psi(k) + np.mean(psi(nz + 1.0) - psi(nxz + 1.0) - psi(nyz + 1.0))
+        assert abs(oracle.cmi_ksg(g.x, g.y, g.z, k) - want) < 1e-12
