@@ -144,8 +144,11 @@ typedef struct {
      * group of 32 jobs), samples scanned by full-scan fallbacks, fallbacks
      * taken (a (query, group) whose lists did not cover some job), and
      * timed trials run by the kernel choice.  fused_lane_ops of a list
-     * launch counts, per job, 2dx+2 per list A entry, 2dx+4 per list B entry
-     * and 2(dx+dy+dz')+2 / +6 per full-scan sample of the two passes. */
+     * launch counts 2dx+2 per list A entry and 2dx+4 per list B entry for
+     * every job of the (query, group) whose warp walked the entry, 2dx+2 per
+     * (job, entry) pair of a lane-split tail, and 2(dx+dy+dz')+2 / +6 per
+     * sample that a full-scan fallback of the two passes scans for the one
+     * job it recomputes (brute_samples = fallbacks x (N-1)). */
     int64_t list_launches;
     double list_walk_a, list_walk_b, brute_samples, fallbacks;
     int64_t tune_trials;
@@ -427,22 +430,32 @@ int idtx_screen_set(idtx_ctx *ctx, const idtx_screen *screen);
  * the device, paths where a cudaMalloc would synchronise the device, or
  * services that must not grow their footprint after start-up).
  *
- * Same estimate and surrogates as idtx_cmi_ksg (its preparation kernels and
- * its tile kernel; idtx_cmi_ksg's kernels agree bit for bit, so the results
- * are the same), without a context: it runs on the current CUDA device and takes all its
- * scratch from one fixed array of IDTX_NOALLOC_SCRATCH_BYTES bytes in device
- * memory that the library declares at file scope.  Every GPU that loads the
- * library holds that array until the process exits.
+ * Same estimate and surrogates as idtx_cmi_ksg, computed by its preparation
+ * kernels and its tile kernel, without a context: it runs on the current
+ * CUDA device and takes all its scratch from one fixed array of
+ * IDTX_NOALLOC_SCRATCH_BYTES bytes in device memory that the library
+ * declares at file scope.  Every GPU that loads the library holds that array
+ * until the process exits.  The per-sample eps and counts behind the
+ * estimates are the same as idtx_cmi_ksg's; the estimates agree within
+ * 1e-10 nats but not always bit for bit, because this entry point keeps the
+ * samples in their given order (idtx_cmi_ksg sorts them along a Morton curve
+ * for n > 256), so its fp64 partial sums are added in another order.  For
+ * the same reason its tile kernel skips few reference tiles, and for large n
+ * it is markedly slower than idtx_cmi_ksg.
  *   - x, y, z and cmi_out must be device memory; cmi_out [1+n_surr] fp64.
  *   - 0 <= settings->n_surr <= IDTX_NOALLOC_MAX_SURR; a problem whose scratch
  *     does not fit in the array returns IDTX_EINVAL with the bytes it needs.
  *   - It calls no cudaMalloc, cudaFree or other allocating routine.
  *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *     (cudaGetSymbolAddress).  Every call copies its descriptors from host
+ *     memory and synchronises `stream`, so it must not be called while a
+ *     stream is being captured.
  *   - All calls share the one array, which keeps the previous call's
  *     contents: calls that overlap on the GPU (other threads, other streams)
  *     race with each other and must be serialised by the caller.
- *   - Synchronises `stream` before returning. */
+ *   - Synchronises `stream` before returning, on success and on every error
+ *     after its first enqueue, so no kernel of the call is still using the
+ *     array when it returns. */
 #define IDTX_NOALLOC_SCRATCH_BYTES (16u << 20)
 #define IDTX_NOALLOC_MAX_SURR 1000
 int idtx_cmi_ksg_noalloc(const float *x, int dx, const float *y, int dy, const float *z, int dz,

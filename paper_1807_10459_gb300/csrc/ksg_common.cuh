@@ -20,6 +20,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <mutex>
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -58,6 +59,16 @@ constexpr int kNumWork = 8;
 constexpr int kMaxListA = 2048;  // by d_YZ
 constexpr int kMaxListB = 4096;  // by d_Z
 
+// The list kernel's ring of per-query digamma terms (ksg_list.cuh), in global
+// scratch after the lists: per CTA, kListRing query tiles of up to 64
+// queries x 32 jobs (fp64).  The kernel runs at most kListRingCtas CTAs.
+#ifndef IDTX_LIST_RING
+#define IDTX_LIST_RING 8
+#endif
+constexpr int kListRing = IDTX_LIST_RING;
+constexpr int kListRingCtas = 192;
+constexpr size_t kListRingBytes = (size_t)kListRingCtas * kListRing * 64 * 32 * sizeof(double);
+
 struct KsgLaunch {
     const float *sh;
     const float *xi;
@@ -77,6 +88,7 @@ struct KsgLaunch {
     const int2 *list_a;
     const int2 *list_b;
     const int4 *lmeta;
+    double *ring;  // kListRingBytes of scratch for the list kernel's term ring
     int cap_a, cap_b;
 };
 
@@ -138,6 +150,31 @@ cudaError_t mlp_loss(MlpWork &w, const float *targets, const int32_t *order, int
 cudaError_t mlp_backward(MlpWork &w, int B, bool accumulate, cudaStream_t st);
 cudaError_t mlp_adam(float *params, const float *grad, float *m, float *v, int step, float lr,
                      cudaStream_t st);
+
+// One-time set-up per device (kernel attributes, occupancy, SM count).
+// Function attributes and device properties belong to a device, so a process
+// that uses several GPUs needs the set-up once on each; the mutex serialises
+// host threads.  A failed set-up is retried by the next call.
+constexpr int kMaxDevices = 64;
+struct DeviceOnce {
+    std::mutex mu;
+    bool done[kMaxDevices] = {};
+};
+
+// Runs f(device) on the current device unless it already succeeded there.
+template <typename F>
+cudaError_t once_per_device(DeviceOnce &o, F &&f)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(o.mu);
+    if (o.done[dev]) return cudaSuccess;
+    e = f(dev);
+    if (e == cudaSuccess) o.done[dev] = true;
+    return e;
+}
 
 // Registries filled by the instantiation units.
 int ksg_variants_d11(KsgVariant *out);

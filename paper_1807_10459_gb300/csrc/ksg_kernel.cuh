@@ -759,14 +759,12 @@ cudaError_t launch_ksg(const KsgLaunch &a, int n_groups, cudaStream_t stream)
 {
     using S = KsgShape<DX, DY, DZ, K1, EXACT, QC, NWARPS>;
     auto kern = ksg_fused_kernel<DX, DY, DZ, K1, EXACT, QC, NWARPS>;
-    static bool attr_set = false;  // per process; the attribute is per function
-    if (!attr_set) {
-        cudaError_t e =
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(S::SMEM));
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static DeviceOnce attr;  // the attribute is per function and device
+    cudaError_t e = once_per_device(attr, [&](int) {
+        return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(S::SMEM));
+    });
+    if (e != cudaSuccess) return e;
     dim3 grid(static_cast<unsigned>(a.n_qt), static_cast<unsigned>(n_groups));
     kern<<<grid, S::THREADS, S::SMEM, stream>>>(a);
     return cudaGetLastError();
@@ -777,21 +775,23 @@ cudaError_t launch_ksg_table(const KsgTable &t, cudaStream_t stream)
 {
     using S = KsgShape<DX, DY, DZ, K1, EXACT, QC, NWARPS>;
     auto kern = ksg_fused_persistent<DX, DY, DZ, K1, EXACT, QC, NWARPS>;
-    static int resident = 0;  // CTAs per SM and SMs of the device, per process
-    static int n_sms = 0;
-    if (!resident) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    // CTAs per SM and SMs, per device (written once under the set-up's lock)
+    static DeviceOnce setup;
+    static int resident[kMaxDevices], n_sms[kMaxDevices];
+    cudaError_t e = once_per_device(setup, [&](int d) {
+        cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(S::SMEM));
-        if (e != cudaSuccess) return e;
-        int dev = 0;
-        e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, kern, S::THREADS, S::SMEM);
-        if (e != cudaSuccess) return e;
-        if (resident < 1) resident = 1;
-    }
-    const int64_t full = static_cast<int64_t>(resident) * n_sms;
+        if (r == cudaSuccess) r = cudaDeviceGetAttribute(&n_sms[d], cudaDevAttrMultiProcessorCount, d);
+        if (r == cudaSuccess)
+            r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[d], kern, S::THREADS, S::SMEM);
+        if (r == cudaSuccess && resident[d] < 1) resident[d] = 1;
+        return r;
+    });
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const int64_t full = static_cast<int64_t>(resident[dev]) * n_sms[dev];
     const unsigned grid = static_cast<unsigned>(t.n_tasks < full ? t.n_tasks : full);
     if (grid == 0) return cudaSuccess;
     kern<<<grid, S::THREADS, S::SMEM, stream>>>(t);

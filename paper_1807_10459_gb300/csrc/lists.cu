@@ -205,15 +205,13 @@ template <int IA, int IB>
 cudaError_t launch_build(const float *sh, int dsp, int dzb, int dsb, int64_t n, int cap_a,
                          int cap_b, int2 *list_a, int2 *list_b, int4 *meta, cudaStream_t st)
 {
-    static bool attr_set = false;  // per process; the attribute is per function
+    static DeviceOnce attr;  // the attribute is per function and device
     const size_t smem = build_smem(IA, IB, sort_tmp_bytes<IB>(), sort_tmp_bytes<IA>());
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_build_lists<IA, IB>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    cudaError_t e = once_per_device(attr, [&](int) {
+        return cudaFuncSetAttribute(k_build_lists<IA, IB>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
+    if (e != cudaSuccess) return e;
     if (n <= 0) return cudaSuccess;
     k_build_lists<IA, IB><<<(unsigned)n, kLThreads, smem, st>>>(sh, dsp, dzb, dsb, n, cap_a,
                                                                  cap_b, list_a, list_b, meta);

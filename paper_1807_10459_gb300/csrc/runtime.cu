@@ -1010,11 +1010,13 @@ struct CallBuffers {
     size_t sh = 0, xi = 0, perm = 0, partial = 0, order = 0, sort_tmp = 0, lists = 0;
 };
 
-// B_LIST layout for n queries: list_a [n][cap_a] | list_b [n][cap_b] | meta [n].
+// B_LIST layout for n queries: list_a [n][cap_a] | list_b [n][cap_b] | meta [n]
+// | the list kernel's term ring.
 size_t list_bytes(int64_t n, int cap_a, int cap_b)
 {
     return align_up((size_t)n * cap_a * sizeof(int2), 256) +
-           align_up((size_t)n * cap_b * sizeof(int2), 256) + align_up((size_t)n * sizeof(int4), 256);
+           align_up((size_t)n * cap_b * sizeof(int2), 256) +
+           align_up((size_t)n * sizeof(int4), 256) + kListRingBytes;
 }
 
 // B_ORDER layout for n samples: order | idx | keys_in | keys_out | column ranges.
@@ -1075,17 +1077,16 @@ int take_event(idtx_ctx *c, cudaEvent_t *ev)
 }
 
 // Enqueue the surrogate permutations of n_slots rows of length n.
-// One-time attribute of the shared-memory shuffle (per process; the attribute
-// is per function).  Also called before a graph capture.
+// One-time attribute of the shared-memory shuffle (per device; the attribute
+// is per function and device).  Also called before a graph capture.
 int init_permutation_kernel()
 {
-    static bool attr_set = false;
-    if (!attr_set) {
-        IDTX_CUDA(cudaFuncSetAttribute(k_fisher_yates_smem<uint16_t>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(65536 * sizeof(uint16_t))));
-        attr_set = true;
-    }
+    static DeviceOnce attr;
+    IDTX_CUDA(once_per_device(attr, [](int) {
+        return cudaFuncSetAttribute(k_fisher_yates_smem<uint16_t>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(65536 * sizeof(uint16_t)));
+    }));
     return IDTX_OK;
 }
 
@@ -1130,14 +1131,17 @@ void fill_launch(const idtx_ctx *c, const Group &g, const Slices &sl, float *eps
     a.list_a = nullptr;
     a.list_b = nullptr;
     a.lmeta = nullptr;
+    a.ring = nullptr;
     a.cap_a = g.cap_a;
     a.cap_b = g.cap_b;
     if ((g.use_list || g.tune) && sl.lists) {
         const size_t oa = align_up((size_t)g.n * g.cap_a * sizeof(int2), 256);
         const size_t ob = align_up((size_t)g.n * g.cap_b * sizeof(int2), 256);
+        const size_t om = align_up((size_t)g.n * sizeof(int4), 256);
         a.list_a = (const int2 *)sl.lists;
         a.list_b = (const int2 *)(sl.lists + oa);
         a.lmeta = (const int4 *)(sl.lists + oa + ob);
+        a.ring = (double *)(sl.lists + oa + ob + om);
     }
 }
 
@@ -1637,18 +1641,21 @@ int finish_call(idtx_ctx *c, cudaStream_t st)
         const double jobs = ws.gb * ws.job_frac;
         c->stats.exhaustive_pairs += ws.exhaustive_pairs;
         if (ws.list) {
-            // List kernel, per job: a list A entry costs 2dx+2 (X distance,
-            // max with d_YZ, compare), a list B entry 2dx+4 (X distance, two
-            // compares, two adds); a full-scan sample 2(dx+dy+dz')+2 (pass A)
-            // or +6 (pass B); a (job, entry) pair of a walk's lane-split tail
-            // 2dx+2 (X distance, max or compare, compare or add).  Counters: walked A, walked B,
-            // full-scan samples of pass A, of pass B, fallbacks, cycles, tail
-            // pairs.
+            // List kernel.  A list A entry a warp walks costs every job of
+            // the warp 2dx+2 (X distance, max with d_YZ, compare), a list B
+            // entry 2dx+4 (X distance, two compares, two adds): those two
+            // counters are per (query, group) and scale with the jobs.  A
+            // full-scan sample costs 2(dx+dy+dz')+2 (pass A) or +6 (pass B)
+            // for the one job being rescanned, and a (job, entry) pair of a
+            // walk's lane-split tail 2dx+2 (X distance, max or compare,
+            // compare or add): those counters are already per job.
+            // Counters: walked A, walked B, full-scan samples of pass A, of
+            // pass B, fallbacks, cycles, tail pairs.
             const double dall = 2.0 * (ws.dx + ws.dy + ws.dz_eff);
             c->stats.fused_lane_ops += jobs * ((double)k[0] * (2.0 * ws.dx + 2.0) +
-                                               (double)k[1] * (2.0 * ws.dx + 4.0) +
-                                               (double)k[2] * (dall + 2.0) +
-                                               (double)k[3] * (dall + 6.0)) +
+                                               (double)k[1] * (2.0 * ws.dx + 4.0)) +
+                                      (double)k[2] * (dall + 2.0) +
+                                      (double)k[3] * (dall + 6.0) +
                                       (double)k[6] * (2.0 * ws.dx + 2.0) +
                                       (double)k[7] * (2.0 * ws.dx + 2.0);
             c->stats.list_tail_b += (double)k[6];
@@ -2086,6 +2093,12 @@ int idtx_cmi_batch(idtx_ctx *c, const idtx_problem *probs, int n_probs, int k, d
             if (rc == IDTX_OK && v->fn_table(KsgTable{nullptr, nullptr, nullptr, 0, 0}, st) !=
                                      cudaSuccess)
                 rc = fail(IDTX_ECUDA, "kernel attribute setup failed");
+        for (const Group &g : gs)
+            if (rc == IDTX_OK && g.use_list) {
+                KsgLaunch none{};  // no tiles: set-up only
+                if (g.v->fn_list(none, 0, st) != cudaSuccess)
+                    rc = fail(IDTX_ECUDA, "list kernel attribute setup failed");
+            }
         if (rc == IDTX_OK) {
             if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) !=
                 cudaSuccess) {
@@ -3060,7 +3073,6 @@ constexpr size_t kNoAllocDescBytes = 64 * 1024;  // descriptor block at the star
 // the process exits.  Host code must not use the name as an address.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-constexpr int kMaxDevices = 64;
 void *g_noalloc_ptr[kMaxDevices] = {};  // device address of the array, per device
 std::mutex g_noalloc_mu;
 
@@ -3204,8 +3216,6 @@ extern "C" int idtx_cmi_ksg_noalloc(const float *x, int dx, const float *y, int 
         doff += sizeof(uint64_t);
     }
     if (doff > kNoAllocDescBytes) return fail(IDTX_EINTERNAL, "descriptor block overflow");
-    IDTX_CUDA(cudaMemcpyAsync(base, host_desc, doff, cudaMemcpyHostToDevice, st));
-
     int *err = (int *)(base + at_err);
     double *psi = (double *)(base + at_psi);
     float *sh = (float *)(base + at_sh);
@@ -3213,53 +3223,64 @@ extern "C" int idtx_cmi_ksg_noalloc(const float *x, int dx, const float *y, int 
     int32_t *perm = (int32_t *)(base + at_perm);
     double *partial = (double *)(base + at_partial);
     const int64_t psi_n = std::max<int64_t>(n, s->k) + 1;
-
-    // The error word must start at zero; every other region is fully written
-    // before it is read, so the previous call's contents do not matter.
-    IDTX_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
-    k_psi_table<<<grid_for(psi_n + 1, 256), 256, 0, st>>>(psi, psi_n);
-    IDTX_CUDA(cudaGetLastError());
-    k_pack_shared<<<grid_for(n_pad * v->dsp, 256), 256, 0, st>>>(
-        (const Col *)(base + o_z), dz, v->dz, (const Col *)(base + o_y), dy, v->dy, v->dsp, n,
-        n_pad, nullptr, sh, err);
-    IDTX_CUDA(cudaGetLastError());
-    k_tile_boxes<<<(unsigned)(n_pad / kTJ), kTJ, 0, st>>>(sh, v->dsp, n);
-    IDTX_CUDA(cudaGetLastError());
-    if (n_slots > 0) {
-        k_iota<<<grid_for((int64_t)n_slots * n, 256), 256, 0, st>>>(perm, n_slots, n);
-        IDTX_CUDA(cudaGetLastError());
-        k_fisher_yates<<<(n_slots + 31) / 32, 32, 0, st>>>(
-            perm, (const uint64_t *)(base + o_streams), (const uint64_t *)(base + o_seeds),
-            n_slots, n);
-        IDTX_CUDA(cudaGetLastError());
-    }
-    k_gather_x<<<grid_for((int64_t)n_groups * n_pad * v->gb * v->dx, 256), 256, 0, st>>>(
-        (const Col *)(base + o_x), dx, v->dx, (const Job *)(base + o_jobs), n_jobs, perm, n,
-        n_pad, v->gb, n_groups, nullptr, xi, err);
-    IDTX_CUDA(cudaGetLastError());
-    KsgLaunch a;
-    a.sh = sh;
-    a.xi = xi;
-    a.psi = psi;
-    a.partial = partial;
-    a.eps_out = nullptr;
-    a.cnt_out = nullptr;
-    a.order = nullptr;
-    a.work = nullptr;
-    a.err = err;
-    a.n = n;
-    a.n_pad = n_pad;
-    a.n_jobs = n_jobs;
-    a.n_qt = n_qt;
-    a.k = s->k;
-    a.timeout_ns = timeout_of(s);
-    IDTX_CUDA(v->fn(a, n_groups, st));
-    k_finalize<<<(n_jobs + 127) / 128, 128, 0, st>>>(partial, n_jobs, n_qt, psi, s->k, n,
-                                                      cmi_out);
-    IDTX_CUDA(cudaGetLastError());
     int h_err = 0;
-    IDTX_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st));
-    IDTX_CUDA(cudaStreamSynchronize(st));
+    // Everything from the first enqueue on: on an error the stream is
+    // synchronised before returning, so no kernel of this call still uses
+    // the shared array when the caller retries.
+    auto enqueue = [&]() -> int {
+        IDTX_CUDA(cudaMemcpyAsync(base, host_desc, doff, cudaMemcpyHostToDevice, st));
+        // The error word must start at zero; every other region is fully
+        // written before it is read, so the previous call's contents do not
+        // matter.
+        IDTX_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+        k_psi_table<<<grid_for(psi_n + 1, 256), 256, 0, st>>>(psi, psi_n);
+        IDTX_CUDA(cudaGetLastError());
+        k_pack_shared<<<grid_for(n_pad * v->dsp, 256), 256, 0, st>>>(
+            (const Col *)(base + o_z), dz, v->dz, (const Col *)(base + o_y), dy, v->dy, v->dsp, n,
+            n_pad, nullptr, sh, err);
+        IDTX_CUDA(cudaGetLastError());
+        k_tile_boxes<<<(unsigned)(n_pad / kTJ), kTJ, 0, st>>>(sh, v->dsp, n);
+        IDTX_CUDA(cudaGetLastError());
+        if (n_slots > 0) {
+            k_iota<<<grid_for((int64_t)n_slots * n, 256), 256, 0, st>>>(perm, n_slots, n);
+            IDTX_CUDA(cudaGetLastError());
+            k_fisher_yates<<<(n_slots + 31) / 32, 32, 0, st>>>(
+                perm, (const uint64_t *)(base + o_streams), (const uint64_t *)(base + o_seeds),
+                n_slots, n);
+            IDTX_CUDA(cudaGetLastError());
+        }
+        k_gather_x<<<grid_for((int64_t)n_groups * n_pad * v->gb * v->dx, 256), 256, 0, st>>>(
+            (const Col *)(base + o_x), dx, v->dx, (const Job *)(base + o_jobs), n_jobs, perm, n,
+            n_pad, v->gb, n_groups, nullptr, xi, err);
+        IDTX_CUDA(cudaGetLastError());
+        KsgLaunch a;
+        a.sh = sh;
+        a.xi = xi;
+        a.psi = psi;
+        a.partial = partial;
+        a.eps_out = nullptr;
+        a.cnt_out = nullptr;
+        a.order = nullptr;
+        a.work = nullptr;
+        a.err = err;
+        a.n = n;
+        a.n_pad = n_pad;
+        a.n_jobs = n_jobs;
+        a.n_qt = n_qt;
+        a.k = s->k;
+        a.timeout_ns = timeout_of(s);
+        IDTX_CUDA(v->fn(a, n_groups, st));
+        k_finalize<<<(n_jobs + 127) / 128, 128, 0, st>>>(partial, n_jobs, n_qt, psi, s->k, n,
+                                                          cmi_out);
+        IDTX_CUDA(cudaGetLastError());
+        IDTX_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        return IDTX_OK;
+    };
+    const int rc = enqueue();
+    const cudaError_t se = cudaStreamSynchronize(st);
+    if (rc != IDTX_OK) return rc;
+    if (se != cudaSuccess)
+        return fail(IDTX_ECUDA, "cudaStreamSynchronize failed: %s", cudaGetErrorString(se));
     if (h_err & kErrNonFinite) return fail(IDTX_EINVAL, "input contains NaN or Inf");
     if (h_err & kErrTimeout) return fail(IDTX_ETIMEOUT, "a bounded device wait ran out");
     if (h_err) return fail(IDTX_EINTERNAL, "device error word 0x%x", h_err);

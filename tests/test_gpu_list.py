@@ -103,6 +103,29 @@ def test_short_lists_fall_back_exactly(idtx, caps):
     _check(idtx, g.x, g.y, g.z, 4, 20, 9, caps=caps, expect_fallbacks=True)
 
 
+def test_lane_op_count_counts_each_fallback_once(idtx):
+    """The lane-operation count behind the roofline figure.  Walked list
+    entries are counted once per (query, group of 32 jobs) and cost every job
+    of the group; a full-scan fallback recomputes ONE job, scanning the N-1
+    other samples once.  With lists of 32 entries most jobs fall back, so a
+    count that charged each scanned sample to every job of the group would
+    exceed the upper bound below by an order of magnitude."""
+    n, S, dx, dy, dz = 900, 20, 1, 1, 3
+    g = synth.gaussian_problem(n, dx, dy, dz, seed=12)
+    ctx = _ctx(idtx, idtx.KERNEL_LIST, (32, 32))
+    _run(idtx, ctx, g.x, g.y, g.z, 4, S, 9)
+    st = ctx.stats()
+    assert st["fallbacks"] > 0
+    assert st["brute_samples"] == st["fallbacks"] * (n - 1)
+    jobs = 1 + S                                      # one group of 32 lanes
+    walks = jobs * (st["list_walk_a"] * (2 * dx + 2) + st["list_walk_b"] * (2 * dx + 4))
+    tails = (st["list_tail_a"] + st["list_tail_b"]) * (2 * dx + 2)
+    dall = 2 * (dx + dy + dz)
+    lo = walks + tails + st["brute_samples"] * (dall + 2)
+    hi = walks + tails + st["brute_samples"] * (dall + 6)
+    assert lo <= st["fused_lane_ops"] <= hi
+
+
 def test_short_lists_other_k_and_dims(idtx):
     g = synth.gaussian_problem(517, 2, 2, 4, seed=3)
     _check(idtx, g.x, g.y, g.z, 7, 9, 2, caps=(32, 32), expect_fallbacks=True)
