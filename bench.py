@@ -28,24 +28,18 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "KSG CMI estimates/s incl. surrogates (N=1e4,k=4); batched/screened vs plain"
-N_SMS = 152
 # DRAM bytes (read + write) per launch of the 200-surrogate step, from ncu
 # captures (profiles/), per kernel; None until the current kernel is captured.
 # Tile kernel: profiles/ksg_fused_kernel_greedy_step_small.md (15-surrogate case,
-# 31.68 MB, scaled by job groups 296/24).  List kernel:
-# profiles/ksg_list_kernel_greedy_step_small.md (full-size launch, captured directly).
-TRAFFIC_BYTES = {"tile": 390.7e6, "list": 2.626e9}
-LANES_PER_SM = 128  # 4 sub-partitions x 32 lanes: one warp instruction per clock each
+# 31.68 MB, scaled by job groups 296/24).  List kernel: captured directly on the
+# full-size launch (profiles/ksg_list_kernel_greedy_step_small.md).
+TRAFFIC_BYTES = {"tile": 390.7e6, "list": None}
+# Pipe utilisation of the list kernel from its committed full ncu capture
+# (small case of the same step; profiles/ksg_list_kernel_greedy_step_small.md).
+PIPES_FROM_PROFILE = None
 
 WORKLOAD = dict(n_proc=10, order=5, T=10000, n_past=3, min_lag=1, max_lag=5, k=4, n_surr=200,
                 alpha=0.05, seed=20181029)
-
-
-def _peaks():
-    try:
-        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        return {}
 
 
 class ClockSampler:
@@ -96,6 +90,31 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(loaded) if loaded else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
                 "samples": len(rows)}
+
+
+def _timed(fn, min_s=1.0, sampler_gpu=0):
+    """Call fn() once untimed, then repeatedly for at least min_s with CUDA
+    events around the loop and nvidia-smi clocks sampled meanwhile; returns
+    (ms per call, calls, clocks)."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(sampler_gpu)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    calls, t0 = 0, time.perf_counter()
+    e0.record()
+    while True:
+        fn()
+        calls += 1
+        if calls >= 3 and time.perf_counter() - t0 >= min_s:
+            torch.cuda.synchronize()
+            if time.perf_counter() - t0 >= min_s:
+                break
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    return e0.elapsed_time(e1) / calls, calls, clocks
 
 
 def _dist_setup():
@@ -173,6 +192,53 @@ def _config():
             "l2": "flushed by a 256 MiB device write before every step"}
 
 
+def workloads_result(device: int) -> dict:
+    """The other configurations, each timed for about a second with its own
+    clock record (device time, inputs resident, every call synchronised):
+    the Gaussian CMI problem (dx = dy = 1, dz = 2, k = 4, 100 surrogates) at
+    N = 1e3 and 1e4; the logistic-map chain (50 replications x 1997 samples,
+    joint dimension 12, 200 surrogates) with sample-level surrogates under
+    the library's kernel choice and with each kernel forced, and with
+    replication-level surrogates; and full greedy inference on the 50-node
+    network in exact, screened and network-free mode."""
+    import torch
+    import paper_1807_10459_gb300 as idtx
+    from paper_1807_10459_gb300 import synth
+    dev = torch.device("cuda", device)
+    out = {}
+
+    def kernel_of(ctx):
+        return "list" if ctx.stats()["list_launches"] > 0 else "tile"
+
+    for n in (1000, 10000):
+        g = synth.gaussian_problem(n, 1, 1, 2, seed=synth.BASE_SEED + 1)
+        x, y, z = (torch.from_numpy(a).to(dev) for a in (g.x, g.y, g.z))
+        ctx = idtx.Context(device)
+        ms, calls, clocks = _timed(lambda: idtx.cmi_ksg(x, y, z, k=4, n_surr=100, seed=1,
+                                                        ctx=ctx), 1.0, device)
+        out[f"gaussian_n{n}"] = {
+            "config": f"Gaussian CMI, N={n}, dx=dy=1, dz=2, k=4, 100 surrogates",
+            "estimates_per_s": 101 / (ms / 1e3), "ms_per_call": ms, "calls": calls,
+            "kernel": kernel_of(ctx), "clocks": clocks}
+
+    lx, ly, lz = synth.logistic_problem(dx=1, dy=1, dz=10)
+    n = lx.shape[1]
+    x, y, z = (torch.from_numpy(a).to(dev) for a in (lx, ly, lz))
+    logi = {"config": f"logistic-map chain, 50 replications x {n // 50} samples (N={n}), "
+                      "dx=dy=1, dz=10, k=4, 200 surrogates"}
+    for name, kern, reps in (("auto", idtx.KERNEL_AUTO, 0), ("list", idtx.KERNEL_LIST, 0),
+                             ("tile", idtx.KERNEL_TILE, 0), ("replications", idtx.KERNEL_AUTO, 50)):
+        ctx = idtx.Context(device)
+        ctx.set_kernel(kern)
+        ms, calls, clocks = _timed(lambda: idtx.cmi_ksg(x, y, z, k=4, n_surr=200, seed=3,
+                                                        n_reps=reps, ctx=ctx), 1.0, device)
+        logi[name] = {"estimates_per_s": 201 / (ms / 1e3), "ms_per_call": ms, "calls": calls,
+                      "kernel": kernel_of(ctx), "clocks": clocks}
+    out["logistic_n1e5"] = logi
+    out["var50_greedy"] = var50_result(device)
+    return out
+
+
 def run_ours(args):
     import torch
     import paper_1807_10459_gb300 as idtx
@@ -193,6 +259,7 @@ def run_ours(args):
     ctx.set_kernel({"auto": idtx.KERNEL_AUTO, "tile": idtx.KERNEL_TILE,
                     "list": idtx.KERNEL_LIST}[args.kernel])
     ctx.set_list_caps(*args.list_caps)
+    rates = idtx.probe_issue_rates(local)  # the roofline's denominator, measured here
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     est_per_step = 47 * (1 + w["n_surr"])
 
@@ -317,45 +384,55 @@ def run_ours(args):
         if dist:
             dist.destroy_process_group()
         return
-    sm_mhz = (clocks or {}).get("sm_mhz") or _peaks().get("clocks_under_load", {}).get(
-        "sm_mhz_median", 1477.0)
-    peak = N_SMS * LANES_PER_SM * sm_mhz * 1e6 / 1e12
-    achieved = st["fused_lane_ops"] / (st["fused_ms"] / 1e3) / 1e12 if st["fused_ms"] else None
+    sm_mhz = (clocks or {}).get("sm_mhz") or rates["sm_clock_mhz"]
+    # Peak: the fastest lane-operation rate the probes measured (per SM per
+    # clock), times the SMs and the median SM clock of the timed region.
+    rate_keys = ("fadd_per_sm_clk", "fmnmx_per_sm_clk", "fsetp_add_per_sm_clk",
+                 "iadd_per_sm_clk", "count_mix_per_sm_clk")
+    best = max(rate_keys, key=lambda k2: rates[k2])
+    peak = rates[best] * rates["n_sms"] * sm_mhz * 1e6 / 1e12
+    sec = st["fused_ms"] / 1e3 if st["fused_ms"] else None
+    achieved = st["fused_lane_ops"] / sec / 1e12 if sec else None
     used = "list" if st["list_launches"] > 0 else "tile"
+    useful = st["useful_lane_ops"] / sec / 1e12 if (sec and used == "list") else None
     traffic = TRAFFIC_BYTES[used] if w["n_surr"] == 200 else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                 "frac": (achieved / peak) if achieved else None,
+                "useful_achieved": useful, "useful_frac": (useful / peak) if useful else None,
                 "traffic": traffic,
                 "traffic_unit": "DRAM bytes read + written per launch (ncu)",
                 "kernel": ("ksg_list_kernel" if used == "list" else "ksg_fused_kernel") +
-                          ("<DX=1,DY=1,DZ=3,K1=5,exact,QC=64,NW=8,LNW=4>" if used == "list" else
-                           "<DX=1,DY=1,DZ=3,K1=5,exact,QC=64,NW=8>"),
-                "peak_basis": f"{N_SMS} SMs x {LANES_PER_SM} lanes x median SM clock "
-                              f"{sm_mhz:.0f} MHz under load (issue-slot peak)",
-                "fused_share_of_step": st["fused_ms"] / ms if ms else None,
-                # the same launch against the brute-force shared-Y/Z work per estimate,
-                # N(N-1)[(4(dy+dz)+2)/(C(1+S)) + 4dx + 9] with dx=dy=1, dz=3 (context: the
-                # kernel's lists skip most of that work, so this exceeds the issue peak)
-                "brute_force_equivalent_tops": (
-                    (w["T"] - 5) * (w["T"] - 6) * (18.0 / est_per_step + 13.0) * est_per_step *
-                    args.steps / (st["fused_ms"] / 1e3) / 1e12) if st["fused_ms"] else None,
+                          "<DX=1,DY=1,DZ=3,K1=5,exact,QC=64,NW=8>",
+                "peak_basis": f"{best} measured by idtx_probe_issue_rates "
+                              f"({rates[best]:.1f} lane-ops/SM/clk) x {rates['n_sms']} SMs x "
+                              f"median SM clock {sm_mhz:.0f} MHz of the timed region",
+                "issue_rates_per_sm_clk": {k2: rates[k2] for k2 in rate_keys},
+                "probe_sm_clock_mhz": rates["sm_clock_mhz"],
+                "pipes_from_profile": PIPES_FROM_PROFILE,
+                "estimator_share_of_step": st["fused_ms"] / ms if ms else None,
                 "list_caps": [st["list_cap_a"], st["list_cap_b"]] if used == "list" else None,
                 "scanned_fraction_of_exhaustive":
                     ((st["scanned_a"] + st["scanned_b"]) / st["exhaustive_pairs"])
                     if st["exhaustive_pairs"] and used == "tile" else None,
-                "work_per_step": {k: st[k] / args.steps for k in
+                "work_per_step": {k2: st[k2] / args.steps for k2 in
                                   (("list_walk_a", "list_walk_b", "list_tail_a", "list_tail_b",
-                                    "brute_samples", "fallbacks")
+                                    "brute_samples", "fallbacks", "list_sum_nz", "list_sum_nyz",
+                                    "fused_lane_ops", "useful_lane_ops")
                                    if used == "list" else
-                                   ("scanned_a", "passed_a", "scanned_b", "passed_b"))},
-                "ops_basis": ("lane-ops per job of the list entries each (query, group of 32 "
-                              "jobs) walks (2dx+2 in the neighbour pass, 2dx+4 in the count "
-                              "pass), per (job, entry) pair of the lane-split tails (2dx+2) "
-                              "and of full-scan fallback samples (counted in-kernel)")
+                                   ("scanned_a", "passed_a", "scanned_b", "passed_b",
+                                    "fused_lane_ops"))},
+                "ops_basis": ("achieved: lane-operations the kernel executes -- 2dx+2 per "
+                              "(job, list A entry) and 2dx+4 per (job, list B entry) for every "
+                              "lane of a shared walk, the same per (job, entry) pair of the "
+                              "repacked count phases and neighbour tails, 2(dx+dy+dz')+2/+6 per "
+                              "sample of a full-scan fallback; useful_achieved: only the "
+                              "(2dx+2) n_yz + (2dx+4) n_z per (query, job) that a walk visiting "
+                              "exactly the entries each job needs would do (counted in-kernel)")
                              if used == "list" else
                              ("lane-ops the kernel's algorithm needs for the tiles it scans: "
                               "shared scan per (query, reference, job group) plus per-job work "
                               "for pairs passing the shared bound (counted in-kernel)")}
+    workloads = workloads_result(local) if (world == 1 and not args.no_workloads) else None
     cpu = cpu_oracle_sample(net.series, target, budget_s=12.0) if world == 1 else None
     line = {"metric": METRIC, "value": value, "unit": "estimates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -369,44 +446,54 @@ def run_ours(args):
             "modes": {"batched": value, "plain": plain["value"] if plain else None,
                       "batched_over_plain": value / plain["value"] if plain else None,
                       "plain_sample": plain["sample"] if plain else None,
-                      "screened": screened}}
+                      "screened": screened},
+            "workloads": workloads}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
 
 
 def run_var50(args):
+    print(json.dumps(var50_result(0)), flush=True)
+
+
+def var50_result(device: int) -> dict:
     """Full greedy inference on a 50-node in-degree-3 VAR(3) network (T=5000,
     lags 1..3, history 3, k=4, 200 surrogates): every target in exact
-    (batched) and screened mode; parent-set agreement and wall-time speedup."""
+    (batched) and screened mode; parent-set agreement and wall-time speedup,
+    with the SM clocks sampled during each mode."""
     import torch
     import paper_1807_10459_gb300 as idtx
     from paper_1807_10459_gb300 import synth
     net = synth.var_network_indegree(n_nodes=50, order=3, indegree=3, T=5000)
-    s = torch.from_numpy(net.series).cuda()
-    ctx = idtx.Context(0)
+    s = torch.from_numpy(net.series).to(torch.device("cuda", device))
+    ctx = idtx.Context(device)
     trained = idtx.Screen.load(os.path.join(ROOT, "paper_1807_10459_gb300",
                                             "screen_weights.npz"))
     # the network-free rule the trained network improves on: cheap maximum plus
     # a constant margin calibrated the same way (an all-zero network)
     free = idtx.Screen(params=np.zeros(idtx.SCREEN_NPARAMS, np.float32), s0=trained.s0,
                        delta=float(trained.meta["network_free_margin"]))
-    ctx_free = idtx.Context(0)
+    ctx_free = idtx.Context(device)
     idtx.screen_set(trained, ctx=ctx)
     idtx.screen_set(free, ctx=ctx_free)
     kw = dict(k=4, n_surr=200, alpha=0.05, seed=20181031, max_parents=10, ctx=ctx)
     idtx.mte_select_target(s, 0, 3, 1, 3, **kw)      # warm-up
+    idtx.mte_select_target(s, 0, 3, 1, 3, mode=idtx.MODE_SCREENED, **kw)
     torch.cuda.synchronize()
-    res = {}
+    res, clocks = {}, {}
     for mode_name, mode, c in (("exact", idtx.MODE_BATCHED, ctx),
                                ("screened", idtx.MODE_SCREENED, ctx),
                                ("network_free", idtx.MODE_SCREENED, ctx_free)):
         kw["ctx"] = c
+        sampler = ClockSampler(device)
+        sampler.start()
         out, t0 = [], time.perf_counter()
         for t in range(50):
             out.append(idtx.mte_select_target(s, t, 3, 1, 3, mode=mode, **kw))
         torch.cuda.synchronize()
         res[mode_name] = (out, time.perf_counter() - t0)
+        clocks[mode_name] = sampler.stop()
     nf = res["network_free"][0]
     ex, sc = res["exact"][0], res["screened"][0]
     same = [a["parents"] == b["parents"] for a, b in zip(ex, sc)]
@@ -435,8 +522,9 @@ def run_var50(args):
             "screen": {"delta": trained.delta, "s0": trained.s0,
                        "quantile": trained.meta.get("quantile")},
             "exact_true_positive_edges": len(found & truth), "true_edges": len(truth),
-            "exact_false_positive_edges": len(found - truth), "data": "synthetic"}
-    print(json.dumps(line), flush=True)
+            "exact_false_positive_edges": len(found - truth), "clocks": clocks,
+            "data": "synthetic"}
+    return line
 
 
 def run_post(args):
@@ -611,6 +699,8 @@ def main():
                     help="estimator kernel of the timed step (auto: the library's timed choice)")
     ap.add_argument("--list-caps", type=int, nargs=2, default=(0, 0), metavar=("A", "B"),
                     help="list capacities of the list kernel (0 0: the library's choice)")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the other configurations (Gaussian, logistic, 50-node network)")
     ap.add_argument("--n-surr", type=int, default=WORKLOAD["n_surr"],
                     help="surrogates per candidate (200 is the benchmarked workload; smaller "
                          "values give a small case for profiling)")

@@ -145,17 +145,48 @@ typedef struct {
      * taken (a (query, group) whose lists did not cover some job), and
      * timed trials run by the kernel choice.  fused_lane_ops of a list
      * launch counts 2dx+2 per list A entry and 2dx+4 per list B entry for
-     * every job of the (query, group) whose warp walked the entry, 2dx+2 per
-     * (job, entry) pair of a lane-split tail, and 2(dx+dy+dz')+2 / +6 per
+     * every job of the (query, group) whose warp walked the entry shared,
+     * 2dx+4 per (job, entry) pair of the count walk's repacked phases, 2dx+2
+     * per pair of a neighbour walk's lane-split tail, and 2(dx+dy+dz')+2 / +6 per
      * sample that a full-scan fallback of the two passes scans for the one
      * job it recomputes (brute_samples = fallbacks x (N-1)). */
     int64_t list_launches;
     double list_walk_a, list_walk_b, brute_samples, fallbacks;
     int64_t tune_trials;
     int32_t list_cap_a, list_cap_b;  /* list capacities of the last list launch */
-    double list_tail_b;  /* (job, entry) pairs of count walks finished lane-split (2dx+2 lane-ops each) */
-    double list_tail_a;  /* the same for the neighbour walks */
+    double list_tail_b;  /* (job, entry) pairs of the count walks' repacked phases (2dx+4 lane-ops each) */
+    double list_tail_a;  /* (job, entry) pairs of the neighbour walks' lane-split tails (2dx+2 each) */
+    /* List kernel: the sums of n_z and n_yz over every (query, job), and the
+     * lane-operations a walk visiting exactly the list entries each job needs
+     * would do, (2dx+4) sum n_z + (2dx+2) sum n_yz (the useful part of
+     * fused_lane_ops). */
+    double list_sum_nz, list_sum_nyz, useful_lane_ops;
 } idtx_stats;
+
+/* Measured instruction-issue rates of a device (no counterpart in the paper:
+ * the denominator of the estimator kernels' roofline figure, which is
+ * instruction issue on the CUDA cores -- the path has no contraction and its
+ * DRAM traffic is a few percent of the HBM bandwidth).  Each rate comes from
+ * a probe kernel that runs one instruction class in eight register chains
+ * per thread at full occupancy, each step reading the next chain's value (so
+ * nothing can be folded), with no memory traffic in its timed loop: FADD,
+ * FMNMX, FADD with a compare and the predicated add that consumes it (3
+ * lane-operations), IADD, and the count pass's step per (job, entry)
+ * (subtract, absolute value, two compares, two adds: 6 lane-operations).
+ * The assembler may pair independent FP32 operations into one instruction,
+ * so a rate can exceed one lane-operation per lane and clock.
+ * *_per_sm_clk: lane-operations per SM per SM clock;
+ * *_per_s: lane-operations per second over the whole device; sm_clock_mhz:
+ * the SM clock the probes ran at (cycle counts over event time).  Takes a few
+ * tens of milliseconds; allocates and frees a few bytes of device memory. */
+typedef struct {
+    double fadd_per_sm_clk, fmnmx_per_sm_clk, fsetp_add_per_sm_clk, iadd_per_sm_clk;
+    double count_mix_per_sm_clk;
+    double fadd_per_s, fmnmx_per_s, fsetp_add_per_s, iadd_per_s, count_mix_per_s;
+    double sm_clock_mhz;
+    int n_sms;
+} idtx_issue_rates;
+int idtx_probe_issue_rates(int device, idtx_issue_rates *out);
 
 /* Enable (1) or disable (0) event timing of the fused kernel. */
 int idtx_ctx_set_profiling(idtx_ctx *ctx, int enable);

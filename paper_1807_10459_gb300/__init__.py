@@ -20,7 +20,7 @@ import numpy as np
 __all__ = ["IdtxError", "Settings", "Context", "load", "cmi_ksg", "cmi_batch", "mte_step",
            "mte_select_target", "mte_prune", "mte_omnibus", "mte_seqmax", "bivariate_te",
            "mte_select_past", "mte_select_sources", "library_path", "Screen", "screen_predict", "screen_loss_grad",
-           "screen_train", "screen_set", "StepResult"]
+           "screen_train", "screen_set", "StepResult", "probe_issue_rates"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libidtx.so")
@@ -66,7 +66,18 @@ class Stats(ctypes.Structure):
                 ("list_walk_b", ctypes.c_double), ("brute_samples", ctypes.c_double),
                 ("fallbacks", ctypes.c_double), ("tune_trials", ctypes.c_int64),
                 ("list_cap_a", ctypes.c_int32), ("list_cap_b", ctypes.c_int32),
-                ("list_tail_b", ctypes.c_double), ("list_tail_a", ctypes.c_double)]
+                ("list_tail_b", ctypes.c_double), ("list_tail_a", ctypes.c_double),
+                ("list_sum_nz", ctypes.c_double), ("list_sum_nyz", ctypes.c_double),
+                ("useful_lane_ops", ctypes.c_double)]
+
+
+class IssueRates(ctypes.Structure):
+    _fields_ = [("fadd_per_sm_clk", ctypes.c_double), ("fmnmx_per_sm_clk", ctypes.c_double),
+                ("fsetp_add_per_sm_clk", ctypes.c_double), ("iadd_per_sm_clk", ctypes.c_double),
+                ("count_mix_per_sm_clk", ctypes.c_double), ("fadd_per_s", ctypes.c_double),
+                ("fmnmx_per_s", ctypes.c_double), ("fsetp_add_per_s", ctypes.c_double),
+                ("iadd_per_s", ctypes.c_double), ("count_mix_per_s", ctypes.c_double),
+                ("sm_clock_mhz", ctypes.c_double), ("n_sms", ctypes.c_int32)]
 
 
 class Step(ctypes.Structure):
@@ -139,6 +150,7 @@ def load():
                                                 ctypes.POINTER(Settings), i32, vp,
                                                 ctypes.POINTER(i32), ctypes.POINTER(Step),
                                                 ctypes.POINTER(i32), vp]
+        lib.idtx_probe_issue_rates.argtypes = [i32, ctypes.POINTER(IssueRates)]
         lib.idtx_ctx_set_kernel.argtypes = [vp, i32]
         lib.idtx_ctx_set_list_caps.argtypes = [vp, i32, i32]
         for name in ("idtx_cmi_ksg_reps", "idtx_mte_prune", "idtx_mte_omnibus", "idtx_mte_seqmax", "idtx_bivariate_te",
@@ -147,10 +159,20 @@ def load():
                      "idtx_screen_set", "idtx_ctx_set_profiling", "idtx_ctx_set_graphs",
                      "idtx_ctx_get_stats", "idtx_ctx_reset_stats",
                      "idtx_ctx_create", "idtx_ctx_destroy", "idtx_cmi_ksg", "idtx_cmi_batch",
-                     "idtx_mte_step", "idtx_mte_select_target", "idtx_version"):
+                     "idtx_mte_step", "idtx_mte_select_target", "idtx_version",
+                     "idtx_probe_issue_rates"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
+
+
+def probe_issue_rates(device: int = 0) -> dict:
+    """Measured lane-operation rates of the device (idtx_probe_issue_rates)."""
+    out = IssueRates()
+    rc = load().idtx_probe_issue_rates(device, ctypes.byref(out))
+    if rc != IDTX_OK:
+        raise IdtxError(rc, "issue-rate probe failed")
+    return {name: getattr(out, name) for name, _ in IssueRates._fields_}
 
 
 def _check(rc):

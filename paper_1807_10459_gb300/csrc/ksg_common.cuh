@@ -51,9 +51,11 @@ constexpr int kTileRows = kTJ + 2;  // samples + bounding box rows
 // The list kernel (ksg_list.cuh) writes, per (query, group of jobs):
 //   [0] list A entries walked, [1] list B entries walked, [2] / [3] samples
 //   scanned by pass-A / pass-B full-scan fallbacks, [4] fallbacks taken,
-//   [5] cycles as above, [6] / [7] (job, entry) pairs of the count / neighbour
-//   walks' lane-split tails.
-constexpr int kNumWork = 8;
+//   [5] cycles as above, [6] (job, entry) pairs of the count walk's repacked
+//   phases, [7] (job, entry) pairs of the neighbour walk's lane-split tails,
+//   [8] / [9] the sums of n_z / n_yz over (query, job): the list entries a
+//   walk that visited exactly the entries each job needs would touch.
+constexpr int kNumWork = 10;
 
 // Capacities of the per-query neighbour lists (entries; multiples of 32).
 constexpr int kMaxListA = 2048;  // by d_YZ

@@ -583,8 +583,12 @@ __global__ void __launch_bounds__(ListShape<DX, DY, DZ, K1, EXACT, QCTA, NWARPS>
                     co[2 * a.n + orig] = nz;
                 }
             }
+            const int snz = __reduce_add_sync(kFull, job_ok ? nz : 0);
+            const int snyz = __reduce_add_sync(kFull, job_ok ? nyz : 0);
             if (lane == 0) {
                 unsigned long long *w = sm.work[warp];
+                w[8] += static_cast<unsigned>(snz);
+                w[9] += static_cast<unsigned>(snyz);
                 w[0] += static_cast<unsigned>(walked_a);
                 w[1] += static_cast<unsigned>(walked_b);
                 w[2] += static_cast<unsigned long long>(nfa) * static_cast<unsigned long long>(a.n - 1);

@@ -1641,23 +1641,28 @@ int finish_call(idtx_ctx *c, cudaStream_t st)
         const double jobs = ws.gb * ws.job_frac;
         c->stats.exhaustive_pairs += ws.exhaustive_pairs;
         if (ws.list) {
-            // List kernel.  A list A entry a warp walks costs every job of
-            // the warp 2dx+2 (X distance, max with d_YZ, compare), a list B
-            // entry 2dx+4 (X distance, two compares, two adds): those two
-            // counters are per (query, group) and scale with the jobs.  A
-            // full-scan sample costs 2(dx+dy+dz')+2 (pass A) or +6 (pass B)
-            // for the one job being rescanned, and a (job, entry) pair of a
-            // walk's lane-split tail 2dx+2 (X distance, max or compare,
-            // compare or add): those counters are already per job.
-            // Counters: walked A, walked B, full-scan samples of pass A, of
-            // pass B, fallbacks, cycles, tail pairs.
+            // List kernel.  A list A entry a warp walks shared costs every
+            // job of the warp 2dx+2 (X distance, max with d_YZ, compare), a
+            // list B entry 2dx+4 (X distance, two compares, two adds): those
+            // two counters are per (query, group) and scale with the jobs.
+            // A full-scan sample costs 2(dx+dy+dz')+2 (pass A) or +6 (pass
+            // B) for the one job being rescanned, a (job, entry) pair of the
+            // count walk's repacked phases 2dx+4 and of the neighbour walk's
+            // lane-split tails 2dx+2: those counters are already per job.
+            // The useful part: n_yz entries of list A and n_z of list B per
+            // (query, job), what a walk visiting exactly the entries each job
+            // needs would do.
             const double dall = 2.0 * (ws.dx + ws.dy + ws.dz_eff);
             c->stats.fused_lane_ops += jobs * ((double)k[0] * (2.0 * ws.dx + 2.0) +
                                                (double)k[1] * (2.0 * ws.dx + 4.0)) +
                                       (double)k[2] * (dall + 2.0) +
                                       (double)k[3] * (dall + 6.0) +
-                                      (double)k[6] * (2.0 * ws.dx + 2.0) +
+                                      (double)k[6] * (2.0 * ws.dx + 4.0) +
                                       (double)k[7] * (2.0 * ws.dx + 2.0);
+            c->stats.useful_lane_ops += (double)k[8] * (2.0 * ws.dx + 4.0) +
+                                        (double)k[9] * (2.0 * ws.dx + 2.0);
+            c->stats.list_sum_nz += (double)k[8];
+            c->stats.list_sum_nyz += (double)k[9];
             c->stats.list_tail_b += (double)k[6];
             c->stats.list_tail_a += (double)k[7];
             c->stats.list_walk_a += (double)k[0];

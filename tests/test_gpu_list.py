@@ -113,17 +113,30 @@ def test_lane_op_count_counts_each_fallback_once(idtx):
     n, S, dx, dy, dz = 900, 20, 1, 1, 3
     g = synth.gaussian_problem(n, dx, dy, dz, seed=12)
     ctx = _ctx(idtx, idtx.KERNEL_LIST, (32, 32))
-    _run(idtx, ctx, g.x, g.y, g.z, 4, S, 9)
+    _, _, cnt = _run(idtx, ctx, g.x, g.y, g.z, 4, S, 9)
     st = ctx.stats()
     assert st["fallbacks"] > 0
     assert st["brute_samples"] == st["fallbacks"] * (n - 1)
     jobs = 1 + S                                      # one group of 32 lanes
     walks = jobs * (st["list_walk_a"] * (2 * dx + 2) + st["list_walk_b"] * (2 * dx + 4))
-    tails = (st["list_tail_a"] + st["list_tail_b"]) * (2 * dx + 2)
+    tails = st["list_tail_a"] * (2 * dx + 2) + st["list_tail_b"] * (2 * dx + 4)
     dall = 2 * (dx + dy + dz)
     lo = walks + tails + st["brute_samples"] * (dall + 2)
     hi = walks + tails + st["brute_samples"] * (dall + 6)
     assert lo <= st["fused_lane_ops"] <= hi
+    # the useful part: exactly the counts the call returned
+    assert st["list_sum_nz"] == cnt[:, 2].sum() and st["list_sum_nyz"] == cnt[:, 1].sum()
+    assert st["useful_lane_ops"] == (2 * dx + 4) * cnt[:, 2].sum() + (2 * dx + 2) * cnt[:, 1].sum()
+
+
+def test_useful_work_counters_match_counts(idtx):
+    """Default list capacities, a multi-group call: the kernel's sums of n_z
+    and n_yz equal the sums of the counts it returns."""
+    g = synth.gaussian_problem(2000, 1, 1, 3, seed=41)
+    ctx = _ctx(idtx, idtx.KERNEL_LIST)
+    _, _, cnt = _run(idtx, ctx, g.x, g.y, g.z, 4, 70, 5)
+    st = ctx.stats()
+    assert st["list_sum_nz"] == cnt[:, 2].sum() and st["list_sum_nyz"] == cnt[:, 1].sum()
 
 
 def test_short_lists_other_k_and_dims(idtx):
