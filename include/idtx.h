@@ -231,6 +231,16 @@ int idtx_ctx_set_kernel(idtx_ctx *ctx, int kernel);
  * [32, default].  Returns IDTX_EINVAL otherwise. */
 int idtx_ctx_set_list_caps(idtx_ctx *ctx, int cap_a, int cap_b);
 
+/* Bound every device wait of this context's calls (the tile kernel's staged-
+ * tile and lock waits, the list kernel's tile-ring waits) by ns nanoseconds
+ * instead of settings->timeout_ms; 0 restores the settings' bound.  No
+ * counterpart in the paper: with a bound shorter than a tile copy the waits
+ * run out, the call returns IDTX_ETIMEOUT, and the context stays usable, so
+ * this exercises the time-out path without stalling the GPU.  A CTA that
+ * gives up still waits for its own copies in flight (at least a second)
+ * before it exits.  Returns IDTX_EINVAL for a NULL ctx or ns < 0. */
+int idtx_ctx_set_wait_limit_ns(idtx_ctx *ctx, int64_t ns);
+
 /* Read the counters accumulated since creation or the last reset. */
 int idtx_ctx_get_stats(idtx_ctx *ctx, idtx_stats *out);
 

@@ -153,6 +153,7 @@ def load():
         lib.idtx_probe_issue_rates.argtypes = [i32, ctypes.POINTER(IssueRates)]
         lib.idtx_ctx_set_kernel.argtypes = [vp, i32]
         lib.idtx_ctx_set_list_caps.argtypes = [vp, i32, i32]
+        lib.idtx_ctx_set_wait_limit_ns.argtypes = [vp, i64]
         for name in ("idtx_cmi_ksg_reps", "idtx_mte_prune", "idtx_mte_omnibus", "idtx_mte_seqmax", "idtx_bivariate_te",
                      "idtx_mte_select_past", "idtx_mte_select_sources",
                      "idtx_ctx_set_kernel", "idtx_ctx_set_list_caps","idtx_screen_predict", "idtx_screen_loss_grad", "idtx_screen_train",
@@ -160,7 +161,7 @@ def load():
                      "idtx_ctx_get_stats", "idtx_ctx_reset_stats",
                      "idtx_ctx_create", "idtx_ctx_destroy", "idtx_cmi_ksg", "idtx_cmi_batch",
                      "idtx_mte_step", "idtx_mte_select_target", "idtx_version",
-                     "idtx_probe_issue_rates"):
+                     "idtx_probe_issue_rates", "idtx_ctx_set_wait_limit_ns"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -206,6 +207,10 @@ class Context:
     def set_list_caps(self, cap_a: int = 0, cap_b: int = 0):
         """Capacities of the list kernel's per-query lists (0: defaults)."""
         _check(load().idtx_ctx_set_list_caps(self.handle, int(cap_a), int(cap_b)))
+
+    def set_wait_limit_ns(self, ns: int = 0):
+        """Bound of this context's device waits in ns (0: settings' timeout_ms)."""
+        _check(load().idtx_ctx_set_wait_limit_ns(self.handle, int(ns)))
 
     def stats(self) -> dict:
         st = Stats()

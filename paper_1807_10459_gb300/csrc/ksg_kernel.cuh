@@ -654,13 +654,17 @@ __device__ __forceinline__ bool ksg_cta(const KsgLaunch &a, const int qt, const 
 
     __syncthreads();
     if (*abort_flag) {
-        // Wait (bounded) for this CTA's copies that may still be in flight, then leave.
+        // Wait (bounded) for this CTA's copies that may still be in flight,
+        // then leave.  A copy always lands, so this wait gets at least a
+        // second whatever the call's wait limit: the CTA must not exit while
+        // a copy into its shared memory is pending.
+        const long long drain_ns = a.timeout_ns > 1000000000ll ? a.timeout_ns : 1000000000ll;
         if (tid == 0)
             for (int st = 0; st < ST; ++st)
                 if (s_last[st] >= 0)
                     (void)mbar_wait_bounded(&s_bar[st],
                                             static_cast<uint32_t>((s_last[st] / ST) & 1),
-                                            a.timeout_ns);
+                                            drain_ns);
         __syncthreads();
         return false;
     }

@@ -74,7 +74,8 @@
 #ifndef IDTX_LIST_REPACK
 #define IDTX_LIST_REPACK 8
 #endif
-// Consecutive query tiles a CTA takes at a time (the ring's depth,
+// Most consecutive query tiles a CTA takes at a time (fewer when the call
+// has too few tiles to give every SM two chunks; the ring's depth,
 // kListRing, is in ksg_common.cuh).
 #ifndef IDTX_LIST_CHUNK
 #define IDTX_LIST_CHUNK 8
@@ -120,7 +121,6 @@ struct ListShape {
     static constexpr int NW = (DX > 2 || K1 > 8) ? 16 : 32;
     static constexpr int THREADS = NW * 32;
     static constexpr int RING = kListRing;
-    static constexpr int CHUNK = IDTX_LIST_CHUNK;
     static_assert(QC <= 64, "the term ring holds tiles of up to 64 queries");
     struct Smem {
         int2 ent[NW][32];  // per warp: staged list entries
@@ -147,13 +147,13 @@ __device__ __forceinline__ bool wait_slot(const int *owner, int want, long long 
 
 template <int DX, int DY, int DZ, int K1, bool EXACT, int QCTA, int NWARPS>
 __global__ void __launch_bounds__(ListShape<DX, DY, DZ, K1, EXACT, QCTA, NWARPS>::THREADS, 1)
-    ksg_list_kernel(const KsgLaunch a, const int n_groups, const int n_chunks)
+    ksg_list_kernel(const KsgLaunch a, const int n_groups, const int n_chunks, const int chunk_lg)
 {
     using S = KsgShape<DX, DY, DZ, K1, EXACT, QCTA, NWARPS>;
     using LS = ListShape<DX, DY, DZ, K1, EXACT, QCTA, NWARPS>;
     constexpr int DS = S::DS, DSP = S::DSP, XW = S::XW, GB = S::GB, QC = S::QC;
     constexpr int NWS = S::NW;  // interleaved sums of the tile kernel
-    constexpr int NW = LS::NW, RING = LS::RING, CHUNK = LS::CHUNK;
+    constexpr int NW = LS::NW, RING = LS::RING;
     constexpr int KH = K1 - 1;  // smallest distances kept (EXACT: exactly k)
     constexpr int kShStage = kTileRows * DSP;
     constexpr unsigned kFull = 0xffffffffu;
@@ -184,13 +184,13 @@ __global__ void __launch_bounds__(ListShape<DX, DY, DZ, K1, EXACT, QCTA, NWARPS>
 
     while (true) {
         // ---------------- take the CTA's next query: tile lt of its stream,
-        // chunk blockIdx.x + (lt / CHUNK) * gridDim.x of the tile sequence
+        // in chunk blockIdx.x + (lt >> chunk_lg) * gridDim.x of the tiles
         int p = 0;
         if (lane == 0) p = atomicAdd(&sm.next, 1);
         p = __shfl_sync(kFull, p, 0);
         const int lt = p / QC, m = p - lt * QC;
-        const int64_t chunk = blockIdx.x + static_cast<int64_t>(lt / CHUNK) * gridDim.x;
-        const int64_t T = chunk * CHUNK + lt % CHUNK;
+        const int64_t chunk = blockIdx.x + static_cast<int64_t>(lt >> chunk_lg) * gridDim.x;
+        const int64_t T = (chunk << chunk_lg) + (lt & ((1 << chunk_lg) - 1));
         if (chunk >= n_chunks || T >= total_tiles) break;
         const int slot = lt % RING;
         int ok = 1;
@@ -672,11 +672,14 @@ cudaError_t launch_ksg_list(const KsgLaunch &a, int n_groups, cudaStream_t strea
     int dev = 0;
     e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    const int64_t chunks = (tiles + LS::CHUNK - 1) / LS::CHUNK;
+    int chunk_lg = 0;  // the largest chunk (up to IDTX_LIST_CHUNK) giving every SM two chunks
+    while ((2 << chunk_lg) <= IDTX_LIST_CHUNK && (tiles >> (chunk_lg + 1)) >= 2 * n_sms[dev])
+        ++chunk_lg;
+    const int64_t chunks = (tiles + (1 << chunk_lg) - 1) >> chunk_lg;
     int64_t grid = chunks < n_sms[dev] ? chunks : n_sms[dev];
     if (grid > kListRingCtas) grid = kListRingCtas;
-    kern<<<static_cast<unsigned>(grid), LS::THREADS, LS::SMEM, stream>>>(a, n_groups,
-                                                                    static_cast<int>(chunks));
+    kern<<<static_cast<unsigned>(grid), LS::THREADS, LS::SMEM, stream>>>(
+        a, n_groups, static_cast<int>(chunks), chunk_lg);
     return cudaGetLastError();
 }
 

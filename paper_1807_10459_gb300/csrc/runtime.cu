@@ -788,6 +788,7 @@ struct idtx_ctx {
     };
     std::map<std::pair<const KsgVariant *, int>, Choice> tuned;
     int cap_a = 0, cap_b = 0;
+    long long wait_ns = 0;  // bound of device waits (0: settings->timeout_ms)
 };
 
 void drop_graph(idtx_ctx *c)
@@ -1704,6 +1705,13 @@ long long timeout_of(const idtx_settings *s)
     return ms * 1000000ll;
 }
 
+// The bound of the device waits of a call on c: the context's limit if one
+// is set (idtx_ctx_set_wait_limit_ns), else the settings'.
+long long timeout_of(const idtx_ctx *c, const idtx_settings *s)
+{
+    return c->wait_ns > 0 ? c->wait_ns : timeout_of(s);
+}
+
 int check_cols(const float *p, int dims, const char *name)
 {
     if (dims > 0 && !p) return fail(IDTX_EINVAL, "%s is NULL", name);
@@ -1787,6 +1795,14 @@ int idtx_ctx_set_list_caps(idtx_ctx *c, int cap_a, int cap_b)
     c->cap_b = cap_b;
     c->tuned.clear();
     drop_graph(c);
+    return IDTX_OK;
+}
+
+int idtx_ctx_set_wait_limit_ns(idtx_ctx *c, int64_t ns)
+{
+    if (!c) return fail(IDTX_EINVAL, "ctx is NULL");
+    if (ns < 0) return fail(IDTX_EINVAL, "wait limit %lld ns is negative", (long long)ns);
+    c->wait_ns = ns;
     return IDTX_OK;
 }
 
@@ -1922,7 +1938,7 @@ static int cmi_ksg_impl(idtx_ctx *c, const float *x, int dx, const float *y, int
     float *eps_d = eps_out ? (eps_dev ? eps_out : (float *)c->buf[B_EPS]) : nullptr;
     int32_t *cnt_d = counts_out ? (cnt_dev ? counts_out : (int32_t *)c->buf[B_CNT]) : nullptr;
     double *cmi_d = (double *)c->buf[B_CMI];
-    IDTX_TRY(enqueue_group(c, g, st, cmi_d, eps_d, cnt_d, timeout_of(s)));
+    IDTX_TRY(enqueue_group(c, g, st, cmi_d, eps_d, cnt_d, timeout_of(c, s)));
     IDTX_CUDA(cudaMemcpyAsync(cmi_out, cmi_d, (size_t)n_jobs * sizeof(double),
                               cmi_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
     if (eps_out && !eps_dev)
@@ -2053,7 +2069,7 @@ int idtx_cmi_batch(idtx_ctx *c, const idtx_problem *probs, int n_probs, int k, d
     }
     std::vector<unsigned char> arena;
     pack_desc(gs, arena);
-    const long long tmo = timeout_of(nullptr);
+    const long long tmo = timeout_of(c, nullptr);
     IDTX_TRY(ensure_psi(c, std::max<int64_t>(n_max, k) + 1, st));
     // Shapes met for the first time: time both kernels on them now (on the
     // context's own buffers, before any capture).
@@ -2277,7 +2293,7 @@ int mte_step_impl(idtx_ctx *c, const float *series, int n_proc, int64_t T, int t
     IDTX_TRY(upload(ga, arena, cmi_bytes));
     double *cmi_a = (double *)c->buf[B_CMI];
     double *cmi_b = cmi_a + jobs_a;
-    IDTX_TRY(enqueue_group(c, ga[0], st, cmi_a, nullptr, nullptr, timeout_of(s)));
+    IDTX_TRY(enqueue_group(c, ga[0], st, cmi_a, nullptr, nullptr, timeout_of(c, s)));
 
     // ids (and, in screened mode, the keep list) live in the step buffer
     unsigned char *stepbuf = (unsigned char *)c->buf[B_STEP];
@@ -2357,7 +2373,7 @@ int mte_step_impl(idtx_ctx *c, const float *series, int n_proc, int64_t T, int t
             IDTX_TRY(plan(c, gb[0]));
             std::vector<unsigned char> arena_b;
             IDTX_TRY(upload(gb, arena_b, cmi_bytes));
-            IDTX_TRY(enqueue_group(c, gb[0], st, cmi_b + off, nullptr, nullptr, timeout_of(s)));
+            IDTX_TRY(enqueue_group(c, gb[0], st, cmi_b + off, nullptr, nullptr, timeout_of(c, s)));
             k_gate_chunk<<<1, 256, 0, st>>>(cmi_b + off, n_keep, hi - lo, step_d, count_d);
             IDTX_CUDA(cudaGetLastError());
             c->stats.kernel_launches += 1;
@@ -2845,7 +2861,7 @@ int enqueue_loo(idtx_ctx *c, const float *ser, int64_t T, int64_t L, int target,
         g.off_cmi = off;
         off += 1 + (size_t)s->n_surr;
     }
-    return run_groups(c, gs, st, timeout_of(s), off);
+    return run_groups(c, gs, st, timeout_of(c, s), off);
 }
 
 }  // namespace
@@ -2925,7 +2941,7 @@ int idtx_mte_omnibus(idtx_ctx *c, const float *series, int n_proc, int64_t T, in
         g.slot_seed.push_back(s->seed);
     }
     IDTX_TRY(plan(c, g));
-    IDTX_TRY(run_groups(c, gs, st, timeout_of(s), 1 + (size_t)s->n_surr));
+    IDTX_TRY(run_groups(c, gs, st, timeout_of(c, s), 1 + (size_t)s->n_surr));
     IDTX_TRY(ensure(c, B_STEP, sizeof(idtx_step) + 64));
     idtx_step *step_d = (idtx_step *)c->buf[B_STEP];
     k_single_stat<<<1, 256, 0, st>>>((const double *)c->buf[B_CMI], s->n_surr, s->alpha, step_d);
@@ -3033,7 +3049,7 @@ int idtx_bivariate_te(idtx_ctx *c, const float *series, int n_proc, int64_t T, i
     }
     IDTX_TRY(plan(c, g));
     const size_t row = 1 + (size_t)s->n_surr;
-    IDTX_TRY(run_groups(c, gs, st, timeout_of(s), ids.size() * row));
+    IDTX_TRY(run_groups(c, gs, st, timeout_of(c, s), ids.size() * row));
     const double *est = (const double *)c->buf[B_CMI];
     IDTX_TRY(ensure(c, B_STEP, align_up((size_t)n_cand_total * 4, 256) + (size_t)n_cand_total * 8));
     int32_t *row_of_d = (int32_t *)c->buf[B_STEP];
