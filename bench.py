@@ -336,8 +336,11 @@ def run_ours(args):
         plain_step()
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
+        n = w["T"] - 5
+        w_plain = n * (n - 1) * (4 * 5 + 9)  # brute-force lane-ops per estimate, d = 5
         plain = {"value": 47 * 5 / dt, "unit": "estimates/s",
-                 "sample": "the step's 47 candidates with 4 surrogates each, one launch each"}
+                 "sample": "the step's 47 candidates with 4 surrogates each, one launch each",
+                 "w_plain_lane_ops_per_estimate": w_plain, "w_plain_tops": 47 * 5 / dt * w_plain / 1e12}
 
     # screened schedule with the shipped screen, on the same step
     screened = None
@@ -444,6 +447,8 @@ def run_ours(args):
             "kernels": {"chosen": used, "tile": kernels.get("tile"), "list": kernels.get("list"),
                         "unit": "estimates/s, the same step with the kernel forced"},
             "modes": {"batched": value, "plain": plain["value"] if plain else None,
+                      "plain_frac_of_peak_by_w_plain": (plain["w_plain_tops"] / peak)
+                      if plain else None,
                       "batched_over_plain": value / plain["value"] if plain else None,
                       "plain_sample": plain["sample"] if plain else None,
                       "screened": screened},

@@ -466,6 +466,27 @@ int idtx_screen_train(idtx_ctx *ctx, idtx_screen *screen, const float *feats,
 /* Install the screen used by IDTX_MODE_SCREENED on this context (copied). */
 int idtx_screen_set(idtx_ctx *ctx, const idtx_screen *screen);
 
+/* Read a screen from the file at `path` and install it as idtx_screen_set
+ * does.  File layout (little-endian, no padding): the 8 bytes "IDTXSCR1";
+ * uint32 version (1), F (IDTX_SCREEN_F), H (IDTX_SCREEN_H), parameter count
+ * (IDTX_SCREEN_NPARAMS); int32 s0; float32 delta; then float32 params
+ * [IDTX_SCREEN_NPARAMS], feat_mean [F], feat_scale [F], and nothing after
+ * them.  The library ships its trained screen in this form
+ * (paper_1807_10459_gb300/screen_weights.bin).  Returns IDTX_EINVAL for a
+ * file that cannot be read, has another layout, or holds non-finite values;
+ * the context's screen is then unchanged. */
+int idtx_screen_load(idtx_ctx *ctx, const char *path);
+
+/* The screen's features (definition above) of n_cand candidates, computed
+ * by the kernel the screened greedy step uses.  est: host or device
+ * [n_cand][1 + s0] fp64, each row a candidate's estimate followed by its
+ * first s0 surrogate estimates; n: samples of the estimates; dx, dy, dz, k,
+ * n_surr as in the step.  feats_out: host or device [n_cand][IDTX_SCREEN_F]
+ * fp32.  Synchronises `stream`.  Training data built with it has exactly
+ * the features the screened step feeds the network. */
+int idtx_screen_features(idtx_ctx *ctx, const double *est, int n_cand, int s0, int64_t n, int dx,
+                         int dy, int dz, int k, int n_surr, float *feats_out, void *stream);
+
 /* Allocation-free estimate (no counterpart in the paper; it exists for
  * callers that cannot allocate device memory -- code whose memory pool owns
  * the device, paths where a cudaMalloc would synchronise the device, or

@@ -20,7 +20,8 @@ import numpy as np
 __all__ = ["IdtxError", "Settings", "Context", "load", "cmi_ksg", "cmi_batch", "mte_step",
            "mte_select_target", "mte_prune", "mte_omnibus", "mte_seqmax", "bivariate_te",
            "mte_select_past", "mte_select_sources", "library_path", "Screen", "screen_predict", "screen_loss_grad",
-           "screen_train", "screen_set", "StepResult", "probe_issue_rates"]
+           "screen_train", "screen_set", "StepResult", "probe_issue_rates", "screen_load",
+           "screen_features"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libidtx.so")
@@ -131,6 +132,9 @@ def load():
                                           ctypes.c_float, ctypes.c_float, u64,
                                           ctypes.POINTER(ctypes.c_double), vp]
         lib.idtx_screen_set.argtypes = [vp, ctypes.POINTER(ScreenC)]
+        lib.idtx_screen_load.argtypes = [vp, ctypes.c_char_p]
+        lib.idtx_screen_features.argtypes = [vp, vp, i32, i32, i64, i32, i32, i32, i32, i32,
+                                             vp, vp]
         lib.idtx_ctx_set_profiling.argtypes = [vp, i32]
         lib.idtx_ctx_set_graphs.argtypes = [vp, i32]
         lib.idtx_ctx_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
@@ -161,7 +165,8 @@ def load():
                      "idtx_ctx_get_stats", "idtx_ctx_reset_stats",
                      "idtx_ctx_create", "idtx_ctx_destroy", "idtx_cmi_ksg", "idtx_cmi_batch",
                      "idtx_mte_step", "idtx_mte_select_target", "idtx_version",
-                     "idtx_probe_issue_rates", "idtx_ctx_set_wait_limit_ns"):
+                     "idtx_probe_issue_rates", "idtx_ctx_set_wait_limit_ns",
+                     "idtx_screen_load", "idtx_screen_features"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -292,6 +297,16 @@ class Screen:
                  delta=np.float32(self.delta), s0=np.int32(self.s0),
                  meta=np.array(json.dumps(meta)))
 
+    def save_bin(self, path: str):
+        """Write the screen in the flat layout idtx_screen_load reads."""
+        import struct
+        with open(path, "wb") as f:
+            f.write(b"IDTXSCR1")
+            f.write(struct.pack("<IIIIif", 1, SCREEN_F, SCREEN_H, SCREEN_NPARAMS, self.s0,
+                                self.delta))
+            for a in (self.params, self.feat_mean, self.feat_scale):
+                f.write(np.ascontiguousarray(a, "<f4").tobytes())
+
     @classmethod
     def load(cls, path: str) -> "Screen":
         import ast
@@ -304,6 +319,24 @@ class Screen:
         except ValueError:
             sc.meta = ast.literal_eval(raw)
         return sc
+
+
+def screen_load(path: str, ctx: Context | None = None):
+    """Install the screen stored at ``path`` (idtx_screen_load's layout)."""
+    ctx = ctx or default_context(0)
+    _check(load().idtx_screen_load(ctx.handle, os.fsencode(path)))
+
+
+def screen_features(est, n: int, dz: int, k: int, n_surr: int, s0: int, dx: int = 1,
+                    dy: int = 1, ctx: Context | None = None) -> np.ndarray:
+    """The screen's features of each row of est [n_cand][>= 1 + s0] (estimate,
+    then surrogate estimates), computed as the screened step computes them."""
+    e = np.ascontiguousarray(np.asarray(est, np.float64)[:, :1 + s0])
+    out = np.empty((e.shape[0], SCREEN_F), np.float32)
+    ctx = ctx or default_context(0)
+    _check(load().idtx_screen_features(ctx.handle, e.ctypes.data, e.shape[0], s0, n, dx, dy,
+                                       dz, k, n_surr, out.ctypes.data, None))
+    return out
 
 
 def screen_predict(screen: Screen, feats, ctx: Context | None = None) -> np.ndarray:

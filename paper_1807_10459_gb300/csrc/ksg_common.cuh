@@ -96,6 +96,13 @@ struct KsgLaunch {
 
 typedef cudaError_t (*KsgLaunchFn)(const KsgLaunch &, int n_groups, cudaStream_t);
 
+// One estimate of one job by the plain schedule (ksg_plain.cuh): sh the
+// group's tiles, xj the job's X values [n_pad][dx bucket], partial the job's
+// n_pad / 8 partial sums.
+typedef cudaError_t (*KsgPlainFn)(const float *sh, const float *xj, const double *psi, int64_t n,
+                                  int64_t n_pad, int k, double *partial, cudaStream_t);
+constexpr int kPlainQueriesPerPartial = 8;
+
 // Several problems of one kernel variant in one persistent launch.  Task t
 // (0 <= t < n_tasks) belongs to the problem p with start[p] <= t < start[p+1];
 // its local index l = t - start[p] is query tile l % n_qt of job group
@@ -121,6 +128,7 @@ struct KsgVariant {
     KsgLaunchFn fn;
     KsgTableFn fn_table;  // persistent multi-problem form
     KsgLaunchFn fn_list;  // the same estimates over sorted neighbour lists
+    KsgPlainFn fn_plain;  // one estimate per launch (the plain schedule)
 };
 
 // Per-query sorted neighbour lists of a group prepared into sh (lists.cu):

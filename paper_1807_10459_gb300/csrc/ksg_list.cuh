@@ -55,6 +55,7 @@
 #pragma once
 
 #include "ksg_kernel.cuh"
+#include "ksg_plain.cuh"
 
 // List entries per sub-chunk of the neighbour-pass and count-pass walks
 // (even divisors of 32; compile-time knobs, the defaults are the tuned values).
@@ -685,7 +686,8 @@ cudaError_t launch_ksg_list(const KsgLaunch &a, int n_groups, cudaStream_t strea
 
 // One compiled specialisation: the tile kernel (ksg_kernel.cuh), its
 // persistent form, and the list kernel, all with the same launch shape so
-// that their digamma partial sums agree bit for bit.
+// that their digamma partial sums agree bit for bit; and the plain schedule
+// (ksg_plain.cuh) of the same dimension bucket.
 template <int DX, int DY, int DZ, int K1, bool EXACT, int QC, int NWARPS>
 KsgVariant make_variant()
 {
@@ -693,7 +695,8 @@ KsgVariant make_variant()
     return KsgVariant{DX, DY, DZ, K1, EXACT ? 1 : 0, S::GB, S::DSP, S::QC,
                       &launch_ksg<DX, DY, DZ, K1, EXACT, QC, NWARPS>,
                       &launch_ksg_table<DX, DY, DZ, K1, EXACT, QC, NWARPS>,
-                      &launch_ksg_list<DX, DY, DZ, K1, EXACT, QC, NWARPS>};
+                      &launch_ksg_list<DX, DY, DZ, K1, EXACT, QC, NWARPS>,
+                      &launch_ksg_plain<DX, DY, DZ, K1, EXACT, QC, NWARPS>};
 }
 
 }  // namespace idtx

@@ -349,72 +349,6 @@ __global__ void k_finalize(const double *partial, int n_jobs, int n_qt, const do
     cmi[job] = psi[k] + s / (double)n;
 }
 
-// One estimate per launch, the "plain" schedule: thread per query, brute
-// force over every reference in sample order, no sharing with other
-// estimates, no ordering and no pruning.  Same definitions as the fused
-// kernel: the (k+1) smallest joint distances including the sample itself,
-// strict-radius counts with the self pair removed.  The job's X values are
-// read from column g of its xi group (stride xw), its Y/Z from sh.
-constexpr int kPlainThreads = 128;
-
-__global__ void __launch_bounds__(kPlainThreads)
-    k_ksg_plain(const float *sh, int dsp, int dz, int dzb, int dy, const float *xg, int xw,
-                int dx, int64_t n, int k, const double *psi, double *partial)
-{
-    __shared__ double s_red[kPlainThreads / 32];
-    const int64_t i = blockIdx.x * (int64_t)kPlainThreads + threadIdx.x;
-    const bool valid = i < n;
-    auto row = [&](int64_t j) { return sh + ((j / kTJ) * kTileRows + (j % kTJ)) * dsp; };
-    float q[IDTX_MAX_DZ + IDTX_MAX_DY], xq[IDTX_MAX_DX];
-    const int ndz = dz > 0 ? dz : 1;  // dz = 0 uses the bucket's zero column
-    for (int d = 0; d < ndz; ++d) q[d] = valid ? row(i)[d] : 0.0f;
-    for (int d = 0; d < dy; ++d) q[ndz + d] = valid ? row(i)[dzb + d] : 0.0f;
-    for (int d = 0; d < dx; ++d) xq[d] = valid ? xg[i * xw + d] : 0.0f;
-    float h[IDTX_MAX_K + 1];
-    for (int t = 0; t <= k; ++t) h[t] = INFINITY;
-    auto dists = [&](int64_t j, float &dzv, float &dyv, float &dxv) {
-        const float *r = row(j);
-        dzv = 0.0f;
-        for (int d = 0; d < ndz; ++d) dzv = fmaxf(dzv, fabsf(q[d] - r[d]));
-        dyv = 0.0f;
-        for (int d = 0; d < dy; ++d) dyv = fmaxf(dyv, fabsf(q[ndz + d] - r[dzb + d]));
-        dxv = 0.0f;
-        for (int d = 0; d < dx; ++d) dxv = fmaxf(dxv, fabsf(xq[d] - xg[j * xw + d]));
-    };
-    for (int64_t j = 0; j < n; ++j) {
-        float a, b, c;
-        dists(j, a, b, c);
-        const float dd = fmaxf(fmaxf(a, b), c);
-        if (dd < h[k]) {
-            int t = k;
-            while (t > 0 && h[t - 1] > dd) {
-                h[t] = h[t - 1];
-                --t;
-            }
-            h[t] = dd;
-        }
-    }
-    const float e = h[k];
-    int cxz = 0, cyz = 0, cz = 0;
-    for (int64_t j = 0; j < n; ++j) {
-        float a, b, c;
-        dists(j, a, b, c);
-        cz += a < e ? 1 : 0;
-        cyz += fmaxf(a, b) < e ? 1 : 0;
-        cxz += fmaxf(a, c) < e ? 1 : 0;
-    }
-    const int self = e > 0.0f ? 1 : 0;
-    double t = valid ? psi[cz - self + 1] - psi[cxz - self + 1] - psi[cyz - self + 1] : 0.0;
-    for (int off = 16; off >= 1; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
-    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = t;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double sum = 0.0;
-        for (int w = 0; w < kPlainThreads / 32; ++w) sum += s_red[w];
-        partial[blockIdx.x] = sum;
-    }
-}
-
 // Max-statistic gate.  est_a [n_cand][1 + sa]: every candidate's estimate and
 // its first sa surrogates; est_b [n_keep][n_surr - sa]: the remaining
 // surrogates of the candidates listed in keep (screened mode; n_keep = 0 and
@@ -948,7 +882,7 @@ int plan(idtx_ctx *c, Group &g)
     g.n_groups = (int)((g.jobs.size() + g.v->gb - 1) / g.v->gb);
     if (g.n_groups > 65535) return fail(IDTX_EINVAL, "too many estimates in one group");
     g.sort = !g.plain && g.n > 2 * kTJ;
-    if (g.plain) g.n_qt = (int)(g.n_pad / kPlainThreads);
+    if (g.plain) g.n_qt = (int)(g.n_pad / kPlainQueriesPerPartial);
     // The list kernel needs a Z subspace (with dz = 0 list B would hold every
     // sample) and lists that fit the memory budget.
     g.use_list = g.tune = false;
@@ -1224,8 +1158,12 @@ int prep_group(idtx_ctx *c, const Group &g, cudaStream_t st, const Slices &sl, f
     } else if (n_slots > 0) {
         IDTX_TRY(enqueue_permutations(perm, streams, seeds, n_slots, g.n, xs, launches));
     }
-    k_gather_x<<<grid_for((int64_t)g.n_groups * g.n_pad * v.gb * v.dx, 256), 256, 0, xs>>>(
-        xc, g.dx, v.dx, jobs, n_jobs, perm, g.n, g.n_pad, v.gb, g.n_groups, order, xi, c->d_err);
+    // X of every job, permuted: gb jobs interleaved per sample row for the
+    // fused kernels; the plain schedule takes each job's values on their own
+    // ([job][n_pad][dx], the same bytes).
+    const int gx = g.plain ? 1 : v.gb, ngx = g.plain ? n_jobs : g.n_groups;
+    k_gather_x<<<grid_for((int64_t)ngx * g.n_pad * gx * v.dx, 256), 256, 0, xs>>>(
+        xc, g.dx, v.dx, jobs, n_jobs, perm, g.n, g.n_pad, gx, ngx, order, xi, c->d_err);
     IDTX_CUDA(cudaGetLastError());
     if (a.list_a) {
         IDTX_CUDA(cudaEventRecord(join, xs));
@@ -1358,14 +1296,10 @@ int enqueue_group(idtx_ctx *c, const Group &g, cudaStream_t st, double *cmi, flo
         IDTX_CUDA(cudaEventRecord(ev0, st));
     }
     if (g.plain) {
-        const int xw = v.gb * v.dx;
-        for (int jb = 0; jb < n_jobs; ++jb) {
-            const float *xg = xi + (size_t)(jb / v.gb) * g.n_pad * xw + (jb % v.gb) * v.dx;
-            k_ksg_plain<<<(unsigned)g.n_qt, kPlainThreads, 0, st>>>(
-                sl.sh, v.dsp, g.dz, v.dz, g.dy, xg, xw, g.dx, g.n, g.k, c->psi,
-                partial + (size_t)jb * g.n_qt);
-            IDTX_CUDA(cudaGetLastError());
-        }
+        // one launch per estimate; prep_group gathered each job's X on its own
+        for (int jb = 0; jb < n_jobs; ++jb)
+            IDTX_CUDA(v.fn_plain(sl.sh, xi + (size_t)jb * g.n_pad * v.dx, c->psi, g.n, g.n_pad,
+                                 g.k, partial + (size_t)jb * g.n_qt, st));
     } else if (use_list) {
         IDTX_CUDA(v.fn_list(a, g.n_groups, st));
         c->stats.list_cap_a = a.cap_a;
@@ -2485,6 +2419,71 @@ extern "C" int idtx_screen_set(idtx_ctx *c, const idtx_screen *sc)
     IDTX_TRY(check_screen(sc));
     c->screen = *sc;
     c->has_screen = true;
+    return IDTX_OK;
+}
+
+// The screen file (idtx.h): "IDTXSCR1", version, F, H, parameter count,
+// s0, delta, then params, feat_mean, feat_scale; little-endian.
+extern "C" int idtx_screen_load(idtx_ctx *c, const char *path)
+{
+    if (!c) return fail(IDTX_EINVAL, "ctx is NULL");
+    if (!path) return fail(IDTX_EINVAL, "path is NULL");
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return fail(IDTX_EINVAL, "cannot open screen file %s", path);
+    struct Header {
+        char magic[8];
+        uint32_t version, nf, nh, np;
+        int32_t s0;
+        float delta;
+    } h;
+    static_assert(sizeof(Header) == 32, "screen file header is 32 bytes");
+    idtx_screen sc;
+    bool ok = std::fread(&h, sizeof(h), 1, f) == 1;
+    if (ok) ok = std::memcmp(h.magic, "IDTXSCR1", 8) == 0 && h.version == 1 &&
+                 h.nf == kScreenF && h.nh == IDTX_SCREEN_H && h.np == (uint32_t)kScreenP;
+    if (ok) ok = std::fread(sc.params, sizeof(float), kScreenP, f) == (size_t)kScreenP &&
+                 std::fread(sc.feat_mean, sizeof(float), kScreenF, f) == (size_t)kScreenF &&
+                 std::fread(sc.feat_scale, sizeof(float), kScreenF, f) == (size_t)kScreenF;
+    if (ok) ok = std::fgetc(f) == EOF;  // nothing after the arrays
+    std::fclose(f);
+    if (!ok) return fail(IDTX_EINVAL, "%s is not a screen file of this library's layout", path);
+    sc.s0 = h.s0;
+    sc.delta = h.delta;
+    if (sc.s0 < 1) return fail(IDTX_EINVAL, "screen file s0=%d", sc.s0);
+    return idtx_screen_set(c, &sc);
+}
+
+extern "C" int idtx_screen_features(idtx_ctx *c, const double *est, int n_cand, int s0,
+                                    int64_t n, int dx, int dy, int dz, int k, int n_surr,
+                                    float *feats_out, void *stream)
+{
+    if (!c) return fail(IDTX_EINVAL, "ctx is NULL");
+    if (!est || !feats_out) return fail(IDTX_EINVAL, "est or feats_out is NULL");
+    if (n_cand < 0 || s0 < 1 || n < 2 || n_surr < 1)
+        return fail(IDTX_EINVAL, "bad n_cand=%d s0=%d n=%lld n_surr=%d", n_cand, s0,
+                    (long long)n, n_surr);
+    if (n_cand == 0) return IDTX_OK;
+    DeviceGuard dg(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t est_bytes = (size_t)n_cand * (1 + s0) * sizeof(double);
+    const size_t feat_bytes = (size_t)n_cand * kScreenF * sizeof(float);
+    IDTX_TRY(ensure(c, B_TRAIN, align_up(est_bytes, 256) + feat_bytes));
+    const double *est_d = est;
+    if (!device_accessible(est)) {
+        IDTX_CUDA(cudaMemcpyAsync(c->buf[B_TRAIN], est, est_bytes, cudaMemcpyHostToDevice, st));
+        est_d = (const double *)c->buf[B_TRAIN];
+    }
+    const bool dev_out = device_accessible(feats_out);
+    float *f_d = dev_out ? feats_out
+                         : (float *)((unsigned char *)c->buf[B_TRAIN] + align_up(est_bytes, 256));
+    k_screen_features<<<(n_cand + 127) / 128, 128, 0, st>>>(
+        est_d, n_cand, s0, (float)std::log((double)n), dx, dy, dz, k,
+        (float)std::log((double)n_surr), f_d);
+    IDTX_CUDA(cudaGetLastError());
+    c->stats.kernel_launches += 1;
+    if (!dev_out)
+        IDTX_CUDA(cudaMemcpyAsync(feats_out, f_d, feat_bytes, cudaMemcpyDeviceToHost, st));
+    IDTX_CUDA(cudaStreamSynchronize(st));
     return IDTX_OK;
 }
 

@@ -4,7 +4,8 @@ Data: exact (batched-mode) greedy parent selection on synthetic networks drawn
 by ``synth`` with seeds disjoint from every evaluation network: 10-node sparse
 VAR(5) networks (T = 10000), 20-node in-degree-3 VAR(3) networks (T = 5000) and
 4-map coupled logistic chains (T = 4000).  Every executed greedy step yields
-one sample per candidate: the screen's features (definition in include/idtx.h)
+one sample per candidate: the screen's features (definition in include/idtx.h,
+computed by the same kernel as in the screened step, idtx_screen_features)
 and the target: by how much the largest of all its surrogate estimates exceeds
 the largest of its s0 cheap ones.
 
@@ -18,14 +19,13 @@ summary also reports the network-free rule it improves on: a constant margin
 (1.25 x the largest training excess) over the cheap maximum.
 
 Usage (GPU):  python -m paper_1807_10459_gb300.screen_train [--out PATH] [--quick]
-Writes PATH (default: screen_weights.npz next to this file) and prints a JSON
-summary.
+Writes PATH (default: screen_weights.npz next to this file), the same screen in
+idtx_screen_load's flat layout beside it (.bin), and prints a JSON summary.
 """
 from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import sys
 import time
@@ -43,13 +43,6 @@ N_SURR = 200
 S0 = 8
 
 
-def features(est_row, n, dz, k=K, n_surr=N_SURR, s0=S0):
-    """Screen features of one candidate from its estimate row [1 + n_surr]."""
-    cheap = est_row[1:1 + s0].astype(np.float64)
-    return np.array([est_row[0], math.log(n), 1.0, 1.0, float(dz), float(k), cheap.mean(),
-                     cheap.std(), cheap.max(), math.log(n_surr)], np.float32)
-
-
 def greedy_samples(series, target, n_past, max_lag, seed, ctx, max_steps=4):
     """Run the exact greedy loop for one target; return (features, targets)."""
     import torch
@@ -62,8 +55,9 @@ def greedy_samples(series, target, n_past, max_lag, seed, ctx, max_steps=4):
                                  n_surr=N_SURR, seed=seed, want_estimates=True, ctx=ctx)
         alive = np.flatnonzero(~np.isnan(est[:, 0]))
         dz = n_past + len(selected)
+        # the features the screened step computes (idtx_screen_features)
+        X += list(idtx.screen_features(est[alive], n, dz, K, N_SURR, S0, ctx=ctx))
         for c in alive:
-            X.append(features(est[c], n, dz))
             Y.append(np.float32(est[c, 1:].max() - est[c, 1:1 + S0].max()))
         if not res[1] or len(alive) <= 1:
             break
@@ -145,6 +139,7 @@ def main():
                    data_seconds=round(t_data, 1), train_seconds=round(t_train, 1),
                    epochs=args.epochs, s0=S0, n_surr=N_SURR, k=K)
     sc.save(args.out, **summary)
+    sc.save_bin(os.path.splitext(args.out)[0] + ".bin")  # for idtx_screen_load
     print(json.dumps(summary))
 
 

@@ -132,6 +132,17 @@ def test_plain_mode_matches_batched_and_oracle(idtx):
     assert np.max(np.abs(plain - oracle.cmi_surrogates(g.x, g.y, None, 7, 3, 4))) < TOL
 
 
+@pytest.mark.parametrize("n,dims,k", [(129, (1, 1, 2), 4), (700, (2, 1, 4), 1),
+                                      (333, (3, 2, 5), 6), (515, (1, 2, 16), 4)])
+def test_plain_mode_buckets_match_oracle(idtx, n, dims, k):
+    """The plain schedule (one launch per estimate) in the k = 4 buckets and the
+    runtime-k one, ragged N: estimates against the oracle."""
+    g = synth.gaussian_problem(n, *dims, seed=n + k)
+    plain = idtx.cmi_ksg(_dev(g.x), _dev(g.y), _dev(g.z), k=k, n_surr=5, seed=8,
+                         mode=idtx.MODE_PLAIN).cpu().numpy()
+    assert np.max(np.abs(plain - oracle.cmi_surrogates(g.x, g.y, g.z, k, 5, 8))) < TOL
+
+
 def test_plain_greedy_step_matches_batched(idtx):
     net = synth.var_network(n_nodes=4, order=2, T=500, density=0.5, weight=0.6, seed=5)
     a, ea = idtx.mte_step(_dev(net.series), 1, 1, 1, 2, (), 0, k=4, n_surr=10, seed=2,
@@ -241,16 +252,60 @@ def test_config2_full_size_sampled(idtx):
 
 
 @pytest.mark.slow
-def test_large_n_sampled_queries(idtx):
+def test_benchmark_size_sampled_eps_and_counts_both_kernels(idtx):
+    """At the benchmarked size and the default list capacities -- N = 9995,
+    joint dimension 5 (a candidate of the benchmarked greedy step: node 2 at
+    lag 1 for target 0, whose lags 1..3 are Z), 200 surrogates -- eps and the
+    three counts of 64 sampled queries in 4 estimates bit-exact against the
+    oracle, under the list kernel and under the tile kernel; all 201
+    estimates identical between the two, the original within 1e-10 of the
+    oracle's."""
+    net = synth.var_network()
+    L, T = 5, net.series.shape[1]
+    n = T - L
+    y = net.series[0, L:][None, :]
+    z = np.stack([net.series[0, L - lag:T - lag] for lag in (1, 2, 3)])
+    x = net.series[2, L - 1:T - 1][None, :]
+    S, seed = 200, 20181029
+    out = {}
+    for name, kern in (("list", idtx.KERNEL_LIST), ("tile", idtx.KERNEL_TILE)):
+        ctx = idtx.Context(0)
+        ctx.set_kernel(kern)
+        cmi, eps, cnt = idtx.cmi_ksg(_dev(x), _dev(y), _dev(z), k=4, n_surr=S, seed=seed,
+                                     want_eps=True, want_counts=True, ctx=ctx)
+        out[name] = (cmi.cpu().numpy(), eps.cpu().numpy(), cnt.cpu().numpy())
+        st = ctx.stats()
+        assert st["list_launches"] == (1 if name == "list" else 0)
+        if name == "list":
+            assert (st["list_cap_a"], st["list_cap_b"]) == (2048, 4096)
+    idx = np.random.default_rng(2).choice(n, 64, replace=False)
+    for s in (0, 1, 117, 200):
+        xs = x if s == 0 else x[:, oracle.perm(seed, s - 1, n)]
+        e, a, b, c = oracle.ksg_counts_at(xs, y, z, 4, idx)
+        for name, (_, eps, cnt) in out.items():
+            assert np.array_equal(eps[s, idx], e), name
+            assert np.array_equal(cnt[s, 0, idx], a), name
+            assert np.array_equal(cnt[s, 1, idx], b), name
+            assert np.array_equal(cnt[s, 2, idx], c), name
+    assert np.array_equal(out["list"][0], out["tile"][0])
+    assert abs(out["list"][0][0] - oracle.cmi_ksg(x, y, z, 4)) < TOL
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("kernel", ["list", "tile"])
+def test_large_n_sampled_queries(idtx, kernel):
     """N = 99850 logistic-map problem, joint dim 12, 200 surrogates (the large
-    single-problem configuration): sampled queries of the original and of two
-    surrogates, eps and counts exact; estimates of those within 1e-10 through
-    their per-sample terms."""
+    single-problem configuration), with each kernel forced: sampled queries of
+    the original and of two surrogates, eps and counts exact; estimates of
+    those within 1e-10 through their per-sample terms."""
     x, y, z = synth.logistic_problem(1, 1, 10)
     n = x.shape[1]
     S, seed = 200, 4
+    ctx = idtx.Context(0)
+    ctx.set_kernel(idtx.KERNEL_LIST if kernel == "list" else idtx.KERNEL_TILE)
     cmi, eps, cnt = idtx.cmi_ksg(_dev(x), _dev(y), _dev(z), k=4, n_surr=S, seed=seed,
-                                 want_eps=True, want_counts=True)
+                                 want_eps=True, want_counts=True, ctx=ctx)
+    assert ctx.stats()["list_launches"] == (1 if kernel == "list" else 0)
     cmi, eps, cnt = cmi.cpu().numpy(), eps.cpu().numpy(), cnt.cpu().numpy()
     idx = np.random.default_rng(1).choice(n, 48, replace=False)
     for s in (0, 1, 137):

@@ -175,3 +175,65 @@ def test_trained_screen_gains_over_the_network_free_rule(idtx):
         full_t += sum(st.n_full for st in tr["steps"])
         full_f += sum(st.n_full for st in fr["steps"])
     assert full_t < full_f
+
+
+def _shipped(idtx, ext):
+    import os
+    return os.path.join(os.path.dirname(idtx.__file__), "screen_weights" + ext)
+
+
+def test_screen_loaded_from_file_through_the_c_abi(idtx):
+    """idtx_screen_load of the shipped flat file installs the same screen as
+    idtx_screen_set of the trained parameters: a screened step gives the same
+    decision, statistic, p-value, kept candidates and estimates."""
+    net = synth.var_network(n_nodes=6, order=3, T=3000, density=0.4, weight=0.5, seed=31)
+    args = (torch.from_numpy(net.series).cuda(), 0, 3, 1, 3, (), 0)
+    kw = dict(k=4, n_surr=200, seed=9, want_estimates=True, mode=idtx.MODE_SCREENED)
+    c_file, c_set = idtx.Context(0), idtx.Context(0)
+    idtx.screen_load(_shipped(idtx, ".bin"), ctx=c_file)
+    idtx.screen_set(idtx.Screen.load(_shipped(idtx, ".npz")), ctx=c_set)
+    a, ea = idtx.mte_step(*args, ctx=c_file, **kw)
+    b, eb = idtx.mte_step(*args, ctx=c_set, **kw)
+    assert tuple(a) == tuple(b) and a.n_full == b.n_full and a.surr_done == b.surr_done
+    assert np.array_equal(np.isnan(ea), np.isnan(eb))
+    ok = ~np.isnan(ea)
+    assert np.array_equal(ea[ok], eb[ok])
+
+
+def test_bad_screen_files_are_rejected_and_leave_the_screen(idtx, tmp_path):
+    good = open(_shipped(idtx, ".bin"), "rb").read()
+    ctx = idtx.Context(0)
+    idtx.screen_load(_shipped(idtx, ".bin"), ctx=ctx)
+    for name, data in (("short", good[:-4]), ("long", good + b"\0"),
+                       ("magic", b"IDTXSCR2" + good[8:]), ("missing", None)):
+        path = tmp_path / name
+        if data is not None:
+            path.write_bytes(data)
+        with pytest.raises(idtx.IdtxError) as err:
+            idtx.screen_load(str(path), ctx=ctx)
+        assert err.value.code == idtx.IDTX_EINVAL
+    # the installed screen still works (screened step runs)
+    net = _net()
+    idtx.mte_step(torch.from_numpy(net.series).cuda(), 0, 2, 1, 3, (), 0, k=4, n_surr=30,
+                  seed=3, mode=idtx.MODE_SCREENED, ctx=ctx)
+
+
+def test_screen_features_follow_the_header_definition(idtx):
+    """The features the screened step computes (idtx_screen_features, also the
+    training features) against the definition in idtx.h written out in numpy:
+    (I_c, ln N, dx, dy, dz, k, mean, std (divisor s0), max of the first s0
+    surrogate estimates, ln n_surr)."""
+    net = _net()
+    s0, n_surr, n = 8, 30, 900 - 3
+    _, est = idtx.mte_step(torch.from_numpy(net.series).cuda(), 0, 2, 1, 3, (), 0, k=4,
+                           n_surr=n_surr, seed=3, want_estimates=True)
+    rows = est[~np.isnan(est[:, 0])]
+    got = idtx.screen_features(rows, n, 2, 4, n_surr, s0)
+    cheap = rows[:, 1:1 + s0]
+    ref = np.stack([rows[:, 0], np.full(len(rows), np.log(n)), np.ones(len(rows)),
+                    np.ones(len(rows)), np.full(len(rows), 2.0), np.full(len(rows), 4.0),
+                    cheap.mean(axis=1), cheap.std(axis=1), cheap.max(axis=1),
+                    np.full(len(rows), np.log(n_surr))], axis=1).astype(np.float32)
+    exact_cols = [0, 1, 2, 3, 4, 5, 8, 9]
+    assert np.array_equal(got[:, exact_cols], ref[:, exact_cols])
+    assert np.allclose(got[:, 6:8], ref[:, 6:8], rtol=1e-6, atol=1e-9)
