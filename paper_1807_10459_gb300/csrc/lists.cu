@@ -26,14 +26,21 @@ constexpr int kBins = 4096;          // bins on bits 30..19 of a non-negative fl
 constexpr int kBinShift = 19;
 constexpr int kBinsPerThread = kBins / kLThreads;
 
-__device__ __forceinline__ void dists(const float *q, const float *row, int dzb, int dsb,
-                                      float &dz, float &dyz)
+constexpr int kMaxRow4 = 5;  // float4 columns of a row of sh: dsp <= 20 (dz' <= 16, dy <= 4)
+constexpr int kUnrollJ = 4;  // samples a thread has in flight per step of a distance pass
+
+// Fold float4 column c of a row into the running maxima of d_Z (the first
+// dzb columns) and d_YZ (the first dsb): the estimator's fp32 |a-b| and maxima.
+__device__ __forceinline__ void fold4(const float4 q, const float4 r, int c, int dzb, int dsb,
+                                      float &mz, float &my)
 {
-    float m = 0.0f;
-    for (int d = 0; d < dzb; ++d) m = fmaxf(m, fabsf(q[d] - row[d]));
-    dz = m;
-    for (int d = dzb; d < dsb; ++d) m = fmaxf(m, fabsf(q[d] - row[d]));
-    dyz = m;
+    const float a[4] = {fabsf(q.x - r.x), fabsf(q.y - r.y), fabsf(q.z - r.z), fabsf(q.w - r.w)};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int d = 4 * c + e;
+        if (d < dzb) mz = fmaxf(mz, a[e]);
+        if (d < dsb) my = fmaxf(my, a[e]);
+    }
 }
 
 // First bin b with (count of bins <= b) > cap, or kBins if the total fits.
@@ -118,7 +125,6 @@ __global__ void __launch_bounds__(kLThreads, 3)
                   int2 *list_a, int2 *list_b, int4 *meta)
 {
     extern __shared__ __align__(16) unsigned char l_smem[];
-    __shared__ float s_q[32];
     __shared__ int s_part[kLThreads / 32];
     __shared__ int s_cut;
     __shared__ int s_cnt[2];
@@ -126,17 +132,55 @@ __global__ void __launch_bounds__(kLThreads, 3)
     int *hist_b = hist_a + kBins;
     const int64_t i = blockIdx.x;
     const int tid = threadIdx.x;
-    auto row_of = [&](int64_t j) { return sh + ((j / kTJ) * kTileRows + (j % kTJ)) * dsp; };
+    const int nc = dsp / 4;  // float4 columns per row
+    auto row4 = [&](int64_t j) {
+        return reinterpret_cast<const float4 *>(sh + ((j / kTJ) * kTileRows + (j % kTJ)) * dsp);
+    };
+    float4 q4[kMaxRow4];
+    {
+        const float4 *qr = row4(i);
+#pragma unroll
+        for (int c = 0; c < kMaxRow4; ++c) q4[c] = c < nc ? qr[c] : make_float4(0, 0, 0, 0);
+    }
+    // Distances of samples j, j + kLThreads, ... (kUnrollJ of them, their rows
+    // loaded back to back); the query itself and samples past n get +inf.
+    auto dists_step = [&](int64_t j0, float (&dz)[kUnrollJ], float (&dyz)[kUnrollJ]) {
+        const float4 *r[kUnrollJ];
+#pragma unroll
+        for (int u = 0; u < kUnrollJ; ++u) {
+            const int64_t j = j0 + (int64_t)u * kLThreads;
+            r[u] = row4(j < n ? j : 0);
+            dz[u] = dyz[u] = 0.0f;
+        }
+#pragma unroll
+        for (int c = 0; c < kMaxRow4; ++c) {
+            if (c < nc) {
+                float4 v[kUnrollJ];
+#pragma unroll
+                for (int u = 0; u < kUnrollJ; ++u) v[u] = r[u][c];
+#pragma unroll
+                for (int u = 0; u < kUnrollJ; ++u) fold4(q4[c], v[u], c, dzb, dsb, dz[u], dyz[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kUnrollJ; ++u) {
+            const int64_t j = j0 + (int64_t)u * kLThreads;
+            if (j >= n || j == i) dz[u] = dyz[u] = INFINITY;
+        }
+    };
+    const int64_t step = (int64_t)kLThreads * kUnrollJ;
 
-    if (tid < dsb) s_q[tid] = row_of(i)[tid];
     for (int b = tid; b < 2 * kBins; b += kLThreads) hist_a[b] = 0;
     __syncthreads();
-    for (int64_t j = tid; j < n; j += kLThreads) {
-        if (j == i) continue;
-        float dz, dyz;
-        dists(s_q, row_of(j), dzb, dsb, dz, dyz);
-        atomicAdd(&hist_a[__float_as_uint(dyz) >> kBinShift], 1);
-        atomicAdd(&hist_b[__float_as_uint(dz) >> kBinShift], 1);
+    for (int64_t j0 = tid; j0 < n; j0 += step) {
+        float dz[kUnrollJ], dyz[kUnrollJ];
+        dists_step(j0, dz, dyz);
+#pragma unroll
+        for (int u = 0; u < kUnrollJ; ++u) {
+            if (dz[u] == INFINITY) continue;  // the query itself or past n
+            atomicAdd(&hist_a[__float_as_uint(dyz[u]) >> kBinShift], 1);
+            atomicAdd(&hist_b[__float_as_uint(dz[u]) >> kBinShift], 1);
+        }
     }
     __syncthreads();
     const int cut_a = cut_bin(hist_a, cap_a, s_part, &s_cut);
@@ -144,29 +188,46 @@ __global__ void __launch_bounds__(kLThreads, 3)
     const float r_a = cut_a >= kBins ? INFINITY : __uint_as_float((unsigned)cut_a << kBinShift);
     const float r_b = cut_b >= kBins ? INFINITY : __uint_as_float((unsigned)cut_b << kBinShift);
 
-    // Collect the samples below the cuts (in order of arrival).
+    // Collect the samples below the cuts (in order of arrival; a warp claims
+    // the slots of all its qualifying lanes with one atomic per list).
     uint32_t *key_a = reinterpret_cast<uint32_t *>(l_smem);
     int32_t *val_a = reinterpret_cast<int32_t *>(key_a + kLThreads * IA);
     uint32_t *key_b = reinterpret_cast<uint32_t *>(val_a + kLThreads * IA);
     int32_t *val_b = reinterpret_cast<int32_t *>(key_b + kLThreads * IB);
     if (tid < 2) s_cnt[tid] = 0;
     __syncthreads();  // histograms are dead from here on
-    for (int64_t j = tid; j < n; j += kLThreads) {
-        if (j == i) continue;
-        float dz, dyz;
-        dists(s_q, row_of(j), dzb, dsb, dz, dyz);
-        if (dyz < r_a) {
-            const int at = atomicAdd(&s_cnt[0], 1);
-            if (at < cap_a) {
-                key_a[at] = __float_as_uint(dyz);
-                val_a[at] = (int32_t)j;
+    const int lane = tid & 31;
+    const uint32_t below = (1u << lane) - 1u;
+    const int64_t n_round = (n + step - 1) / step * step;  // whole warps iterate
+    for (int64_t j0 = tid; j0 < n_round; j0 += step) {
+        float dz[kUnrollJ], dyz[kUnrollJ];
+        dists_step(j0, dz, dyz);
+#pragma unroll
+        for (int u = 0; u < kUnrollJ; ++u) {
+            const int64_t j = j0 + (int64_t)u * kLThreads;
+            const bool in_a = dyz[u] < r_a, in_b = dz[u] < r_b;
+            const uint32_t ma = __ballot_sync(0xffffffffu, in_a);
+            const uint32_t mb = __ballot_sync(0xffffffffu, in_b);
+            int base_a = 0, base_b = 0;
+            if (lane == 0) {
+                if (ma) base_a = atomicAdd(&s_cnt[0], __popc(ma));
+                if (mb) base_b = atomicAdd(&s_cnt[1], __popc(mb));
             }
-        }
-        if (dz < r_b) {
-            const int at = atomicAdd(&s_cnt[1], 1);
-            if (at < cap_b) {
-                key_b[at] = __float_as_uint(dz);
-                val_b[at] = (int32_t)j;
+            base_a = __shfl_sync(0xffffffffu, base_a, 0);
+            base_b = __shfl_sync(0xffffffffu, base_b, 0);
+            if (in_a) {
+                const int at = base_a + __popc(ma & below);
+                if (at < cap_a) {
+                    key_a[at] = __float_as_uint(dyz[u]);
+                    val_a[at] = (int32_t)j;
+                }
+            }
+            if (in_b) {
+                const int at = base_b + __popc(mb & below);
+                if (at < cap_b) {
+                    key_b[at] = __float_as_uint(dz[u]);
+                    val_b[at] = (int32_t)j;
+                }
             }
         }
     }

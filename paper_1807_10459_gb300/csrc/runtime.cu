@@ -223,70 +223,70 @@ __global__ void k_morton_keys(const Col *zc, int dz, const Col *yc, int nk, int 
     }
 }
 
-__global__ void k_iota(int32_t *perm, int n_slots, int64_t n)
-{
-    const int64_t total = (int64_t)n_slots * n;
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x)
-        perm[idx] = (int32_t)(idx % n);
-}
-
-// Fisher-Yates (Durstenfeld) shuffle of slot's row, driven by SplitMix64 from
-// the state seed ^ mix64(stream): for i = n-1 .. 1 swap a[i], a[hi64(r*(i+1))].
-__global__ void k_fisher_yates(int32_t *perm, const uint64_t *streams, const uint64_t *seeds,
-                               int n_slots, int64_t n)
-{
-    const int slot = blockIdx.x * blockDim.x + threadIdx.x;
-    if (slot >= n_slots) return;
-    int32_t *a = perm + (int64_t)slot * n;
-    uint64_t state = seeds[slot] ^ mix64(streams[slot]);
-    for (int64_t i = n - 1; i >= 1; --i) {
-        state += 0x9E3779B97F4A7C15ull;
-        const uint64_t r = mix64(state);
-        const int64_t j = (int64_t)__umul64hi(r, (uint64_t)(i + 1));
-        const int32_t t = a[i];
-        a[i] = a[j];
-        a[j] = t;
-    }
-}
-
-// The same shuffle with the row in shared memory, one warp per slot: the
-// warp draws the next 32 SplitMix64 outputs and their indices in parallel
-// (the state before step s is seed ^ mix64(stream) + (s+1) * gamma), then
-// lane 0 performs the 32 swaps in order.  T holds an index (uint16_t for
-// n <= 65536).  Dynamic shared memory: n * sizeof(T) bytes.
-template <typename T>
+// Fisher-Yates (Durstenfeld) shuffle of a slot's row, driven by SplitMix64
+// from the state seed ^ mix64(stream): for step s = 0 .. n-2, i = n-1-s,
+// r = mix64(state_s) with state_s = seed ^ mix64(stream) + (s+1) * gamma,
+// swap a[i] and a[hi64(r * (i+1))].  One warp per slot.  The steps are
+// sequential, but steps on disjoint positions commute: the warp draws the
+// next 32 steps in parallel (lane t takes step s0 + t) and performs at once
+// the longest prefix of them in which no step draws the same j as an earlier
+// one or has its position i drawn by an earlier one (an earlier step cannot
+// touch a later one's j, since j <= i), then continues after that prefix.
+// The result is the sequential shuffle's, bit for bit.  T: the index type
+// of the row in shared memory (SMEM, uint16_t for n <= 65536; dynamic
+// shared memory n * sizeof(T) bytes) or int32_t for a row shuffled in place
+// in global memory (loads and stores through L2).
+template <typename T, bool SMEM>
 __global__ void __launch_bounds__(32)
-    k_fisher_yates_smem(int32_t *perm, const uint64_t *streams, const uint64_t *seeds, int64_t n)
+    k_fisher_yates(int32_t *perm, const uint64_t *streams, const uint64_t *seeds, int64_t n)
 {
     extern __shared__ __align__(16) unsigned char fy_raw[];
-    T *a = reinterpret_cast<T *>(fy_raw);
+    constexpr unsigned kFull = 0xffffffffu;
     const int slot = blockIdx.x;
     const int lane = threadIdx.x;
-    for (int64_t i = lane; i < n; i += 32) a[i] = (T)i;
+    int32_t *out = perm + (int64_t)slot * n;
+    T *a = SMEM ? reinterpret_cast<T *>(fy_raw) : reinterpret_cast<T *>(out);
+    auto ld = [&](int64_t p) -> T { return SMEM ? a[p] : (T)__ldcg(reinterpret_cast<int32_t *>(a) + p); };
+    auto st = [&](int64_t p, T v) {
+        if (SMEM)
+            a[p] = v;
+        else
+            __stcg(reinterpret_cast<int32_t *>(a) + p, (int32_t)v);
+    };
+    for (int64_t i = lane; i < n; i += 32) st(i, (T)i);
     __syncwarp();
     const uint64_t base = seeds[slot] ^ mix64(streams[slot]);
-    for (int64_t s0 = 0; s0 < n - 1; s0 += 32) {
+    const uint32_t below = (1u << lane) - 1u;
+    int64_t s0 = 0;
+    while (s0 < n - 1) {
         const int64_t s = s0 + lane;
-        int j = 0;
-        if (s < n - 1) {
+        const bool valid = s < n - 1;
+        const int64_t i = n - 1 - s;
+        int64_t j = 0;
+        if (valid) {
             const uint64_t r = mix64(base + (uint64_t)(s + 1) * 0x9E3779B97F4A7C15ull);
-            j = (int)__umul64hi(r, (uint64_t)(n - s));  // step s works on i = n-1-s
+            j = (int64_t)__umul64hi(r, (uint64_t)(i + 1));
         }
-        const int cnt = (int)((n - 1 - s0) < 32 ? (n - 1 - s0) : 32);
-        for (int t = 0; t < cnt; ++t) {
-            const int jt = __shfl_sync(0xffffffffu, j, t);
-            if (lane == 0) {
-                const int64_t i = n - 1 - (s0 + t);
-                const T x = a[i];
-                a[i] = a[jt];
-                a[jt] = x;
-            }
+        const uint32_t live = __ballot_sync(kFull, valid);
+        // same j as an earlier lane
+        const uint32_t same = __match_any_sync(kFull, valid ? (int)j : -1 - lane);
+        const uint32_t dup = __ballot_sync(kFull, valid && (same & below) != 0);
+        // position i drawn by an earlier lane: lane a marks lane n-1-s0-j_a
+        const int64_t b = n - 1 - s0 - j;
+        const uint32_t hit =
+            __reduce_or_sync(kFull, (valid && b > lane && b < 32) ? (1u << (int)b) : 0u);
+        const uint32_t bad = (dup | hit) & live;
+        const int run = bad ? __ffs(bad) - 1 : __popc(live);
+        if (lane < run) {
+            const T x = ld(i), y = ld(j);
+            st(i, y);
+            st(j, x);
         }
         __syncwarp();
+        s0 += run;
     }
-    int32_t *out = perm + (int64_t)slot * n;
-    for (int64_t i = lane; i < n; i += 32) out[i] = (int32_t)a[i];
+    if (SMEM)
+        for (int64_t i = lane; i < n; i += 32) out[i] = (int32_t)a[i];
 }
 
 // xi[grp][j][g*dxb + d] = X_job[d][pi_job(order[j])] (job = grp*gb + g; jobs
@@ -1018,7 +1018,7 @@ int init_permutation_kernel()
 {
     static DeviceOnce attr;
     IDTX_CUDA(once_per_device(attr, [](int) {
-        return cudaFuncSetAttribute(k_fisher_yates_smem<uint16_t>,
+        return cudaFuncSetAttribute(k_fisher_yates<uint16_t, true>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)(65536 * sizeof(uint16_t)));
     }));
@@ -1028,19 +1028,17 @@ int init_permutation_kernel()
 int enqueue_permutations(int32_t *perm, const uint64_t *streams, const uint64_t *seeds,
                          int n_slots, int64_t n, cudaStream_t st, int &launches)
 {
+    if (n_slots <= 0) return IDTX_OK;
     if (n <= 65536) {
         const int bytes = (int)(n * sizeof(uint16_t));
         IDTX_TRY(init_permutation_kernel());
-        k_fisher_yates_smem<uint16_t><<<(unsigned)n_slots, 32, bytes, st>>>(perm, streams, seeds, n);
-        IDTX_CUDA(cudaGetLastError());
-        launches += 1;
-        return IDTX_OK;
+        k_fisher_yates<uint16_t, true><<<(unsigned)n_slots, 32, bytes, st>>>(perm, streams, seeds,
+                                                                             n);
+    } else {
+        k_fisher_yates<int32_t, false><<<(unsigned)n_slots, 32, 0, st>>>(perm, streams, seeds, n);
     }
-    k_iota<<<grid_for((int64_t)n_slots * n, 256), 256, 0, st>>>(perm, n_slots, n);
     IDTX_CUDA(cudaGetLastError());
-    k_fisher_yates<<<(n_slots + 31) / 32, 32, 0, st>>>(perm, streams, seeds, n_slots, n);
-    IDTX_CUDA(cudaGetLastError());
-    launches += 2;
+    launches += 1;
     return IDTX_OK;
 }
 
@@ -2589,8 +2587,7 @@ extern "C" int idtx_screen_train(idtx_ctx *c, idtx_screen *sc, const float *feat
     for (int ep = 0; ep < epochs; ++ep) {
         const uint64_t rs[2] = {(uint64_t)ep, seed};
         IDTX_CUDA(cudaMemcpyAsync(rng, rs, sizeof(rs), cudaMemcpyHostToDevice, st));
-        k_iota<<<grid_for(n, 256), 256, 0, st>>>(order, 1, n);
-        k_fisher_yates<<<1, 32, 0, st>>>(order, rng, rng + 1, 1, n);
+        k_fisher_yates<int32_t, false><<<1, 32, 0, st>>>(order, rng, rng + 1, n);
         IDTX_CUDA(cudaGetLastError());
         for (int start = 0; start < n; start += batch) {
             const int bsz = std::min(batch, n - start);
@@ -3262,11 +3259,8 @@ extern "C" int idtx_cmi_ksg_noalloc(const float *x, int dx, const float *y, int 
         k_tile_boxes<<<(unsigned)(n_pad / kTJ), kTJ, 0, st>>>(sh, v->dsp, n);
         IDTX_CUDA(cudaGetLastError());
         if (n_slots > 0) {
-            k_iota<<<grid_for((int64_t)n_slots * n, 256), 256, 0, st>>>(perm, n_slots, n);
-            IDTX_CUDA(cudaGetLastError());
-            k_fisher_yates<<<(n_slots + 31) / 32, 32, 0, st>>>(
-                perm, (const uint64_t *)(base + o_streams), (const uint64_t *)(base + o_seeds),
-                n_slots, n);
+            k_fisher_yates<int32_t, false><<<(unsigned)n_slots, 32, 0, st>>>(
+                perm, (const uint64_t *)(base + o_streams), (const uint64_t *)(base + o_seeds), n);
             IDTX_CUDA(cudaGetLastError());
         }
         k_gather_x<<<grid_for((int64_t)n_groups * n_pad * v->gb * v->dx, 256), 256, 0, st>>>(
