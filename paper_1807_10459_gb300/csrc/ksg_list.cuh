@@ -30,9 +30,10 @@
 // bit-identical estimates and either may serve a call.
 //
 // Design (GB300).  The kernel is persistent: one CTA of 32 warps per SM, one
-// job per lane.  A CTA takes chunks of consecutive query tiles (in group-major
-// order, so a chunk lies in one or two job groups), and its warps take the
-// chunk's queries one at a time from a shared counter.  So at any moment the
+// job per lane.  A CTA takes chunks of up to 8 consecutive query tiles of one
+// job group (chunks ordered query block by query block, so the CTAs in flight
+// share the lists of one block of queries), and its warps take the chunk's
+// queries one at a time from a shared counter.  So at any moment the
 // SM's warps serve ~32 consecutive queries of one group: samples are in Morton
 // order of (Z, Y), the neighbourhoods of consecutive queries overlap, and the
 // X rows the walks gather (one 128-byte row of xi per list entry: the 32 jobs'
@@ -74,6 +75,10 @@
 // many jobs (a power of two <= 16) still need entries.
 #ifndef IDTX_LIST_REPACK
 #define IDTX_LIST_REPACK 8
+#endif
+// Job groups per super-block of the chunk order (see the kernel).
+#ifndef IDTX_LIST_GSB
+#define IDTX_LIST_GSB 16
 #endif
 // Most consecutive query tiles a CTA takes at a time (fewer when the call
 // has too few tiles to give every SM two chunks; the ring's depth,
@@ -177,22 +182,26 @@ __global__ void __launch_bounds__(ListShape<DX, DY, DZ, K1, EXACT, QCTA, NWARPS>
 
     int2 *ent = sm.ent[warp];
     const int2 sentinel = make_int2(0, __float_as_int(CUDART_INF_F));
-    const int64_t total_tiles = static_cast<int64_t>(n_groups) * a.n_qt;
     const int kk = a.k;
     auto kth = [&](const float(&h)[KH]) { return EXACT ? h[KH - 1] : select_kth<KH>(h, kk - 1); };
     auto sh_row = [&](int64_t j) { return a.sh + (j / kTJ) * kShStage + (j % kTJ) * DSP; };
     const long long t_begin = clock64();
 
     while (true) {
-        // ---------------- take the CTA's next query: tile lt of its stream,
-        // in chunk blockIdx.x + (lt >> chunk_lg) * gridDim.x of the tiles
+        // ---------------- take the CTA's next query: tile lt of its stream is
+        // tile lt mod 2^chunk_lg of chunk blockIdx.x + (lt >> chunk_lg) *
+        // gridDim.x.  Chunks run in super-blocks of GSB groups, query block
+        // by query block within a super-block, so the CTAs in flight share a
+        // few groups' X rows and a range of queries' lists in L2, while each
+        // CTA's warps serve consecutive queries of one group.  Tiles past a
+        // group's last one (its last block may be short) are claimed as
+        // empty.
         int p = 0;
         if (lane == 0) p = atomicAdd(&sm.next, 1);
         p = __shfl_sync(kFull, p, 0);
         const int lt = p / QC, m = p - lt * QC;
         const int64_t chunk = blockIdx.x + static_cast<int64_t>(lt >> chunk_lg) * gridDim.x;
-        const int64_t T = (chunk << chunk_lg) + (lt & ((1 << chunk_lg) - 1));
-        if (chunk >= n_chunks || T >= total_tiles) break;
+        if (chunk >= n_chunks) break;
         const int slot = lt % RING;
         int ok = 1;
         if (lane == 0) ok = wait_slot(&sm.owner[slot], lt, a.timeout_ns) ? 1 : 0;
@@ -202,9 +211,16 @@ __global__ void __launch_bounds__(ListShape<DX, DY, DZ, K1, EXACT, QCTA, NWARPS>
             break;
         }
         __threadfence_block();
-        const int grp = static_cast<int>(T / a.n_qt);
-        const int qt = static_cast<int>(T - static_cast<int64_t>(grp) * a.n_qt);
-        const int64_t qi = static_cast<int64_t>(qt) * QC + m;
+        const int n_qb = (a.n_qt + (1 << chunk_lg) - 1) >> chunk_lg;
+        const int64_t per_sb = static_cast<int64_t>(IDTX_LIST_GSB) * n_qb;
+        const int64_t sb = chunk / per_sb;
+        const int g0 = static_cast<int>(sb * IDTX_LIST_GSB);
+        const int gs = n_groups - g0 < IDTX_LIST_GSB ? n_groups - g0 : IDTX_LIST_GSB;
+        const int64_t rc = chunk - sb * per_sb;
+        const int64_t qblock = rc / gs;
+        const int grp = g0 + static_cast<int>(rc - qblock * gs);
+        const int qt = static_cast<int>((qblock << chunk_lg) + (lt & ((1 << chunk_lg) - 1)));
+        const int64_t qi = static_cast<int64_t>(qt) * QC + m;  // >= n_pad past the last tile
         const int job = grp * GB + lane;
         const bool job_ok = job < a.n_jobs;
         double term = 0.0;
@@ -624,7 +640,7 @@ __global__ void __launch_bounds__(ListShape<DX, DY, DZ, K1, EXACT, QCTA, NWARPS>
                 }
                 s += tsum;
             }
-            if (job_ok) a.partial[static_cast<int64_t>(job) * a.n_qt + qt] = s;
+            if (job_ok && qt < a.n_qt) a.partial[static_cast<int64_t>(job) * a.n_qt + qt] = s;
             __syncwarp();
             if (lane == 0) {
                 sm.done[slot] = 0;
@@ -676,7 +692,8 @@ cudaError_t launch_ksg_list(const KsgLaunch &a, int n_groups, cudaStream_t strea
     int chunk_lg = 0;  // the largest chunk (up to IDTX_LIST_CHUNK) giving every SM two chunks
     while ((2 << chunk_lg) <= IDTX_LIST_CHUNK && (tiles >> (chunk_lg + 1)) >= 2 * n_sms[dev])
         ++chunk_lg;
-    const int64_t chunks = (tiles + (1 << chunk_lg) - 1) >> chunk_lg;
+    // every group's query tiles in blocks of 2^chunk_lg (the last block may be short)
+    const int64_t chunks = static_cast<int64_t>(n_groups) * ((a.n_qt + (1 << chunk_lg) - 1) >> chunk_lg);
     int64_t grid = chunks < n_sms[dev] ? chunks : n_sms[dev];
     if (grid > kListRingCtas) grid = kListRingCtas;
     kern<<<static_cast<unsigned>(grid), LS::THREADS, LS::SMEM, stream>>>(
