@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(ListShape<DX, DY, DZ, K1, EXACT, QCTA, NWARPS>
         if (lane == 0) p = atomicAdd(&sm.next, 1);
         p = __shfl_sync(kFull, p, 0);
         const int lt = p / QC, m = p - lt * QC;
-        const int64_t chunk = blockIdx.x + static_cast<int64_t>(lt >> chunk_lg) * gridDim.x;
+        const int chunk = static_cast<int>(blockIdx.x) + (lt >> chunk_lg) * static_cast<int>(gridDim.x);
         if (chunk >= n_chunks) break;
         const int slot = lt % RING;
         int ok = 1;
@@ -211,15 +211,16 @@ __global__ void __launch_bounds__(ListShape<DX, DY, DZ, K1, EXACT, QCTA, NWARPS>
             break;
         }
         __threadfence_block();
+        // (32-bit: n_chunks, the chunk count, fits an int; see the launcher)
         const int n_qb = (a.n_qt + (1 << chunk_lg) - 1) >> chunk_lg;
-        const int64_t per_sb = static_cast<int64_t>(IDTX_LIST_GSB) * n_qb;
-        const int64_t sb = chunk / per_sb;
-        const int g0 = static_cast<int>(sb * IDTX_LIST_GSB);
+        const int per_sb = IDTX_LIST_GSB * n_qb;
+        const int sb = chunk / per_sb;
+        const int g0 = sb * IDTX_LIST_GSB;
         const int gs = n_groups - g0 < IDTX_LIST_GSB ? n_groups - g0 : IDTX_LIST_GSB;
-        const int64_t rc = chunk - sb * per_sb;
-        const int64_t qblock = rc / gs;
-        const int grp = g0 + static_cast<int>(rc - qblock * gs);
-        const int qt = static_cast<int>((qblock << chunk_lg) + (lt & ((1 << chunk_lg) - 1)));
+        const int rc = chunk - sb * per_sb;
+        const int qblock = rc / gs;
+        const int grp = g0 + (rc - qblock * gs);
+        const int qt = (qblock << chunk_lg) + (lt & ((1 << chunk_lg) - 1));
         const int64_t qi = static_cast<int64_t>(qt) * QC + m;  // >= n_pad past the last tile
         const int job = grp * GB + lane;
         const bool job_ok = job < a.n_jobs;
@@ -694,6 +695,7 @@ cudaError_t launch_ksg_list(const KsgLaunch &a, int n_groups, cudaStream_t strea
         ++chunk_lg;
     // every group's query tiles in blocks of 2^chunk_lg (the last block may be short)
     const int64_t chunks = static_cast<int64_t>(n_groups) * ((a.n_qt + (1 << chunk_lg) - 1) >> chunk_lg);
+    if (chunks > 0x3fffffff) return cudaErrorInvalidValue;  // the kernel's chunk arithmetic is 32-bit
     int64_t grid = chunks < n_sms[dev] ? chunks : n_sms[dev];
     if (grid > kListRingCtas) grid = kListRingCtas;
     kern<<<static_cast<unsigned>(grid), LS::THREADS, LS::SMEM, stream>>>(
