@@ -73,8 +73,9 @@ typedef struct idtx_ctx idtx_ctx;
  * IDTX_MODE_BATCHED: all estimates of a call that share Y and Z (the original
  *   and its surrogates, or every candidate of a greedy step) run in one fused
  *   launch that computes their shared distances once.
- * IDTX_MODE_PLAIN: one launch per estimate, thread-per-query brute force with
- *   no sharing between estimates (the reference point for batching). */
+ * IDTX_MODE_PLAIN: one launch per estimate, a warp per query scanning every
+ *   sample, no sharing between estimates and no sample ordering (the
+ *   reference point for batching); eps and counts outputs as in batched mode. */
 #define IDTX_MODE_BATCHED 0
 #define IDTX_MODE_PLAIN 1
 /* IDTX_MODE_SCREENED (greedy calls only, no counterpart in the paper): every

@@ -100,7 +100,8 @@ typedef cudaError_t (*KsgLaunchFn)(const KsgLaunch &, int n_groups, cudaStream_t
 // group's tiles, xj the job's X values [n_pad][dx bucket], partial the job's
 // n_pad / 8 partial sums.
 typedef cudaError_t (*KsgPlainFn)(const float *sh, const float *xj, const double *psi, int64_t n,
-                                  int64_t n_pad, int k, double *partial, cudaStream_t);
+                                  int64_t n_pad, int k, double *partial, float *eps,
+                                  int32_t *cnt, cudaStream_t);
 constexpr int kPlainQueriesPerPartial = 8;
 
 // Several problems of one kernel variant in one persistent launch.  Task t

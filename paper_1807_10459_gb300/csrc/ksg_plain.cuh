@@ -24,11 +24,12 @@ constexpr int kPlainWarps = kPlainQueriesPerPartial;  // queries per CTA of the 
 
 // sh: the group's shared-coordinate tiles (DZ z columns, then DY y columns,
 // rows of DSP floats); xj: this job's X values [n_pad][DX]; partial: this
-// job's [n_pad / kPlainWarps] partial sums.
+// job's [n_pad / kPlainWarps] partial sums; eps (nullable): this job's [n]
+// eps_i; cnt (nullable): this job's [3][n] n_xz, n_yz, n_z.
 template <int DX, int DY, int DZ, int K1, bool EXACT, int DSP>
 __global__ void __launch_bounds__(kPlainWarps * 32)
     k_ksg_plain(const float *sh, const float *xj, int64_t n, int k, const double *psi,
-                double *partial)
+                double *partial, float *eps, int32_t *cnt)
 {
     constexpr int DS = DZ + DY;
     constexpr int KH = K1;  // the k+1 smallest including the query (EXACT: exactly)
@@ -98,6 +99,14 @@ __global__ void __launch_bounds__(kPlainWarps * 32)
         cxz = __reduce_add_sync(kFull, cxz);
         const int self = e > 0.0f ? 1 : 0;
         term = psi[cz - self + 1] - psi[cxz - self + 1] - psi[cyz - self + 1];
+        if (lane == 0) {
+            if (eps) eps[i] = e;
+            if (cnt) {
+                cnt[i] = cxz - self;
+                cnt[n + i] = cyz - self;
+                cnt[2 * n + i] = cz - self;
+            }
+        }
     }
     if (lane == 0) s_t[warp] = term;
     __syncthreads();
@@ -113,14 +122,15 @@ __global__ void __launch_bounds__(kPlainWarps * 32)
 // ones, so that every partial of the job is written (0 past n).
 template <int DX, int DY, int DZ, int K1, bool EXACT, int QC, int NWARPS>
 cudaError_t launch_ksg_plain(const float *sh, const float *xj, const double *psi, int64_t n,
-                             int64_t n_pad, int k, double *partial, cudaStream_t stream)
+                             int64_t n_pad, int k, double *partial, float *eps, int32_t *cnt,
+                             cudaStream_t stream)
 {
     using S = KsgShape<DX, DY, DZ, K1, EXACT, QC, NWARPS>;
     const int64_t blocks = n_pad / kPlainWarps;
     if (blocks <= 0) return cudaSuccess;
     k_ksg_plain<DX, DY, DZ, K1, EXACT, S::DSP>
         <<<static_cast<unsigned>(blocks), kPlainWarps * 32, 0, stream>>>(sh, xj, n, k, psi,
-                                                                         partial);
+                                                                         partial, eps, cnt);
     return cudaGetLastError();
 }
 

@@ -7,7 +7,7 @@
 // (idtx_cmi_batch), or every candidate of a greedy step with its surrogates
 // (idtx_mte_step).  A group runs as
 //   pack_shared  : Y/Z columns -> sh [n_pad][dsp] (row per sample, +inf pads)
-//   iota + fisher_yates : surrogate permutations, one thread per permutation
+//   shuffle      : surrogate permutations, one warp per permutation
 //   gather_x     : X values of every job, permuted, -> xi [groups][n_pad][GB*DX]
 //   ksg_fused    : kNN + counts + digamma partial sums (ksg_kernel.cuh)
 //   finalize     : psi(k) + sum / N per job, fixed order
@@ -27,6 +27,7 @@
 
 #include "idtx.h"
 #include "ksg_common.cuh"
+#include "shuffle.cuh"
 
 namespace idtx {
 
@@ -68,14 +69,6 @@ struct Job {  // one estimate: X source and permutation slot (-1: identity)
     int32_t src;
     int32_t slot;
 };
-
-__device__ __forceinline__ uint64_t mix64(uint64_t z)
-{
-    // SplitMix64 output function (Steele, Lea & Flood 2014).
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
 
 // psi(n) for n in [0, n_max]: psi(0) is NaN; n < 16 by the finite harmonic sum
 // psi(n) = -gamma + sum_{m<n} 1/m; n >= 16 by the asymptotic expansion
@@ -223,119 +216,96 @@ __global__ void k_morton_keys(const Col *zc, int dz, const Col *yc, int nk, int 
     }
 }
 
-// Fisher-Yates (Durstenfeld) shuffle of a slot's row, driven by SplitMix64
-// from the state seed ^ mix64(stream): for step s = 0 .. n-2, i = n-1-s,
-// r = mix64(state_s) with state_s = seed ^ mix64(stream) + (s+1) * gamma,
-// swap a[i] and a[hi64(r * (i+1))].  One warp per slot.  The steps are
-// sequential, but steps on disjoint positions commute: the warp draws the
-// next 32 steps in parallel (lane t takes step s0 + t) and performs at once
-// the longest prefix of them in which no step draws the same j as an earlier
-// one or has its position i drawn by an earlier one (an earlier step cannot
-// touch a later one's j, since j <= i), then continues after that prefix.
-// The result is the sequential shuffle's, bit for bit.  T: the index type
-// of the row in shared memory (SMEM, uint16_t for n <= 65536; dynamic
-// shared memory n * sizeof(T) bytes) or int32_t for a row shuffled in place
-// in global memory (loads and stores through L2).
-template <typename T, bool SMEM>
-__global__ void __launch_bounds__(32)
-    k_fisher_yates(int32_t *perm, const uint64_t *streams, const uint64_t *seeds, int64_t n)
-{
-    extern __shared__ __align__(16) unsigned char fy_raw[];
-    constexpr unsigned kFull = 0xffffffffu;
-    const int slot = blockIdx.x;
-    const int lane = threadIdx.x;
-    int32_t *out = perm + (int64_t)slot * n;
-    T *a = SMEM ? reinterpret_cast<T *>(fy_raw) : reinterpret_cast<T *>(out);
-    auto ld = [&](int64_t p) -> T { return SMEM ? a[p] : (T)__ldcg(reinterpret_cast<int32_t *>(a) + p); };
-    auto st = [&](int64_t p, T v) {
-        if (SMEM)
-            a[p] = v;
-        else
-            __stcg(reinterpret_cast<int32_t *>(a) + p, (int32_t)v);
-    };
-    for (int64_t i = lane; i < n; i += 32) st(i, (T)i);
-    __syncwarp();
-    const uint64_t base = seeds[slot] ^ mix64(streams[slot]);
-    const uint32_t below = (1u << lane) - 1u;
-    int64_t s0 = 0;
-    while (s0 < n - 1) {
-        const int64_t s = s0 + lane;
-        const bool valid = s < n - 1;
-        const int64_t i = n - 1 - s;
-        int64_t j = 0;
-        if (valid) {
-            const uint64_t r = mix64(base + (uint64_t)(s + 1) * 0x9E3779B97F4A7C15ull);
-            j = (int64_t)__umul64hi(r, (uint64_t)(i + 1));
-        }
-        const uint32_t live = __ballot_sync(kFull, valid);
-        // same j as an earlier lane
-        const uint32_t same = __match_any_sync(kFull, valid ? (int)j : -1 - lane);
-        const uint32_t dup = __ballot_sync(kFull, valid && (same & below) != 0);
-        // position i drawn by an earlier lane: lane a marks lane n-1-s0-j_a
-        const int64_t b = n - 1 - s0 - j;
-        const uint32_t hit =
-            __reduce_or_sync(kFull, (valid && b > lane && b < 32) ? (1u << (int)b) : 0u);
-        const uint32_t bad = (dup | hit) & live;
-        const int run = bad ? __ffs(bad) - 1 : __popc(live);
-        if (lane < run) {
-            const T x = ld(i), y = ld(j);
-            st(i, y);
-            st(j, x);
-        }
-        __syncwarp();
-        s0 += run;
-    }
-    if (SMEM)
-        for (int64_t i = lane; i < n; i += 32) out[i] = (int32_t)a[i];
-}
-
-// xi[grp][j][g*dxb + d] = X_job[d][pi_job(order[j])] (job = grp*gb + g; jobs
-// past the end repeat job 0), 0 for d >= dx, +inf for j >= n.
 // Replication-level surrogates: slot s's permutation of the samples moves
-// whole replications of len samples, perm[s][r*len + t] = blk[s][r]*len + t,
-// blk[s] the permutation of the n_reps replications.
+// whole replications of len samples, pi_s(r*len + t) = blk[s][r]*len + t,
+// blk[s] the permutation of the n_reps replications.  With `order`, the row
+// is written composed with it: perm[s][j] = pi_s(order[j]).
 __global__ void k_expand_reps(const int32_t *blk, int n_slots, int64_t n_reps, int64_t len,
-                              int32_t *perm)
+                              const int32_t *order, int32_t *perm)
 {
     const int64_t n = n_reps * len, total = (int64_t)n_slots * n;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t slot = idx / n, i = idx - slot * n;
+        const int64_t slot = idx / n, j = idx - slot * n;
+        const int64_t i = order ? (int64_t)order[j] : j;
         perm[idx] = (int32_t)((int64_t)blk[slot * n_reps + i / len] * len + i % len);
     }
 }
 
-__global__ void k_gather_x(const Col *xc, int dx, int dxb, const Job *jobs, int n_jobs,
-                           const int32_t *perm, int64_t n, int64_t n_pad, int gb, int n_groups,
-                           const int32_t *order, float *xi, int *err)
+constexpr int kGatherRows = 32;     // sample rows per CTA of k_gather_x
+constexpr int kGatherThreads = 256;
+constexpr int kGatherMaxWidth = 32 * 4;  // jobs per group x padded X width
+constexpr int kGatherJobsPerWarp = 4;    // 32 jobs per group over 8 warps
+
+// xi[grp][j][g*dxb + d] = X_job[d][pi_job(order[j])] (job = grp*gb + g; jobs
+// past the end repeat job 0; pi the identity for slot -1), 0 for d >= dx,
+// +inf for j >= n.  With `composed`, the permutation rows already hold
+// pi(order[j]) at j (k_shuffle_smem, k_expand_reps), so a warp reads 32
+// consecutive entries of a row.  A CTA fills kGatherRows consecutive rows of
+// one group: warp w takes the jobs g = w, w + 8, ... (all their permutation
+// loads issued before the first is used), lane l the row j0 + l; the values
+// are staged in shared memory and the rows, contiguous in xi, are written
+// out in sequence.  Grid: n_groups * (n_pad / kGatherRows) CTAs.
+__global__ void __launch_bounds__(kGatherThreads)
+    k_gather_x(const Col *xc, int dx, int dxb, const Job *jobs, int n_jobs,
+               const int32_t *perm, int64_t n, int64_t n_pad, int gb, const int32_t *order,
+               bool composed, float *xi, int *err)
 {
-    const int xw = gb * dxb;
-    const int64_t per_grp = n_pad * xw;
-    const int64_t total = per_grp * n_groups;
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t grp = idx / per_grp;
-        const int64_t rem = idx - grp * per_grp;
-        const int64_t j = rem / xw;
-        const int w = (int)(rem - j * xw);
-        const int g = w / dxb, d = w - g * dxb;
-        int job = (int)grp * gb + g;
+    constexpr int kWarps = kGatherThreads / 32;
+    __shared__ float s_x[kGatherRows * (kGatherMaxWidth + 1)];
+    const int xw = gb * dxb, ld = xw + 1;
+    const int64_t tiles = n_pad / kGatherRows;
+    const int64_t grp = blockIdx.x / tiles;
+    const int64_t j0 = (blockIdx.x - grp * tiles) * kGatherRows;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t j = j0 + lane;
+    const bool in = j < n;
+    const int64_t t0 = in ? (order ? (int64_t)order[j] : j) : 0;
+    const int64_t at = composed ? j : t0;  // this row's position in a permutation row
+    Job jb[kGatherJobsPerWarp];
+    int64_t t[kGatherJobsPerWarp];
+#pragma unroll
+    for (int u = 0; u < kGatherJobsPerWarp; ++u) {
+        int64_t job = grp * gb + warp + u * kWarps;
         if (job >= n_jobs) job = 0;
-        float v;
-        if (j >= n) {
-            v = INFINITY;
-        } else if (d >= dx) {
-            v = 0.0f;
-        } else {
-            const Job jb = jobs[job];
-            const int64_t t0 = order ? (int64_t)order[j] : j;
-            const int64_t t = jb.slot < 0 ? t0 : (int64_t)perm[(int64_t)jb.slot * n + t0];
-            const Col c = xc[(int64_t)jb.src * dx + d];
-            v = c.base[c.off + t];
-            if (!isfinite(v)) atomicOr(err, kErrNonFinite);
-        }
-        xi[idx] = v;
+        jb[u] = jobs[job];
     }
+#pragma unroll
+    for (int u = 0; u < kGatherJobsPerWarp; ++u) {
+        const bool use = warp + u * kWarps < gb && in && jb[u].slot >= 0;
+        t[u] = use ? (int64_t)perm[(int64_t)jb[u].slot * n + at] : t0;
+    }
+#pragma unroll
+    for (int u = 0; u < kGatherJobsPerWarp; ++u) {
+        const int g = warp + u * kWarps;
+        if (g >= gb) break;
+        float *dst = s_x + lane * ld + g * dxb;
+        for (int d = 0; d < dxb; ++d) {
+            float v = in ? 0.0f : INFINITY;
+            if (in && d < dx) {
+                const Col c = xc[(int64_t)jb[u].src * dx + d];
+                v = c.base[c.off + t[u]];
+                if (!isfinite(v)) atomicOr(err, kErrNonFinite);
+            }
+            dst[d] = v;
+        }
+    }
+    __syncthreads();
+    float *out = xi + (grp * n_pad + j0) * xw;
+    for (int e = threadIdx.x; e < kGatherRows * xw; e += kGatherThreads) {
+        const int r = e / xw;
+        out[e] = s_x[r * ld + (e - r * xw)];
+    }
+}
+
+// The gather's grid; 0 when the shape is outside its limits.
+static int64_t gather_blocks(int64_t n_groups, int64_t n_pad, int gb, int dxb)
+{
+    if (gb > kGatherJobsPerWarp * (kGatherThreads / 32) || gb * dxb > kGatherMaxWidth ||
+        n_pad % kGatherRows)
+        return 0;
+    const int64_t b = n_groups * (n_pad / kGatherRows);
+    return b > 0x7fffffff ? 0 : b;
 }
 
 // cmi[job] = psi(k) + (sum over query tiles, in order) / n.
@@ -1011,31 +981,34 @@ int take_event(idtx_ctx *c, cudaEvent_t *ev)
     return IDTX_OK;
 }
 
-// Enqueue the surrogate permutations of n_slots rows of length n.
 // One-time attribute of the shared-memory shuffle (per device; the attribute
 // is per function and device).  Also called before a graph capture.
 int init_permutation_kernel()
 {
     static DeviceOnce attr;
     IDTX_CUDA(once_per_device(attr, [](int) {
-        return cudaFuncSetAttribute(k_fisher_yates<uint16_t, true>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(65536 * sizeof(uint16_t)));
+        return cudaFuncSetAttribute(k_shuffle_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    shuffle_smem_bytes(65536));
     }));
     return IDTX_OK;
 }
 
+// Enqueue the surrogate permutations of n_slots rows of length n.  With
+// `order` (n <= 65536 only) the rows are written composed with it; *composed
+// says whether they were.
 int enqueue_permutations(int32_t *perm, const uint64_t *streams, const uint64_t *seeds,
-                         int n_slots, int64_t n, cudaStream_t st, int &launches)
+                         int n_slots, int64_t n, const int32_t *order, cudaStream_t st,
+                         int &launches, bool *composed)
 {
+    *composed = false;
     if (n_slots <= 0) return IDTX_OK;
     if (n <= 65536) {
-        const int bytes = (int)(n * sizeof(uint16_t));
         IDTX_TRY(init_permutation_kernel());
-        k_fisher_yates<uint16_t, true><<<(unsigned)n_slots, 32, bytes, st>>>(perm, streams, seeds,
-                                                                             n);
+        k_shuffle_smem<<<(unsigned)n_slots, 32, shuffle_smem_bytes((int)n), st>>>(
+            perm, streams, seeds, (int)n, order);
+        *composed = order != nullptr;
     } else {
-        k_fisher_yates<int32_t, false><<<(unsigned)n_slots, 32, 0, st>>>(perm, streams, seeds, n);
+        k_fisher_yates<<<(unsigned)n_slots, 32, 0, st>>>(perm, streams, seeds, n);
     }
     IDTX_CUDA(cudaGetLastError());
     launches += 1;
@@ -1145,23 +1118,32 @@ int prep_group(idtx_ctx *c, const Group &g, cudaStream_t st, const Slices &sl, f
         IDTX_CUDA(cudaStreamWaitEvent(c->side_stream, fork, 0));
         xs = c->side_stream;
     }
+    // Permutation rows composed with the sample order where the shuffle can
+    // write them so (the gather then reads them in sequence).
+    bool composed = false;
     if (n_slots > 0 && g.n_reps > 0) {
         // permutations of the replications after the sample rows, then expanded
         int32_t *blk = perm + (int64_t)n_slots * g.n;
-        IDTX_TRY(enqueue_permutations(blk, streams, seeds, n_slots, g.n_reps, xs, launches));
+        bool unused = false;
+        IDTX_TRY(enqueue_permutations(blk, streams, seeds, n_slots, g.n_reps, nullptr, xs,
+                                      launches, &unused));
         k_expand_reps<<<grid_for((int64_t)n_slots * g.n, 256), 256, 0, xs>>>(
-            blk, n_slots, g.n_reps, g.n / g.n_reps, perm);
+            blk, n_slots, g.n_reps, g.n / g.n_reps, order, perm);
         IDTX_CUDA(cudaGetLastError());
+        composed = order != nullptr;
         launches += 1;
     } else if (n_slots > 0) {
-        IDTX_TRY(enqueue_permutations(perm, streams, seeds, n_slots, g.n, xs, launches));
+        IDTX_TRY(enqueue_permutations(perm, streams, seeds, n_slots, g.n, order, xs, launches,
+                                      &composed));
     }
     // X of every job, permuted: gb jobs interleaved per sample row for the
     // fused kernels; the plain schedule takes each job's values on their own
     // ([job][n_pad][dx], the same bytes).
     const int gx = g.plain ? 1 : v.gb, ngx = g.plain ? n_jobs : g.n_groups;
-    k_gather_x<<<grid_for((int64_t)ngx * g.n_pad * gx * v.dx, 256), 256, 0, xs>>>(
-        xc, g.dx, v.dx, jobs, n_jobs, perm, g.n, g.n_pad, gx, ngx, order, xi, c->d_err);
+    const int64_t gblocks = gather_blocks(ngx, g.n_pad, gx, v.dx);
+    if (gblocks <= 0) return fail(IDTX_EINTERNAL, "gather shape out of range");
+    k_gather_x<<<(unsigned)gblocks, kGatherThreads, 0, xs>>>(
+        xc, g.dx, v.dx, jobs, n_jobs, perm, g.n, g.n_pad, gx, order, composed, xi, c->d_err);
     IDTX_CUDA(cudaGetLastError());
     if (a.list_a) {
         IDTX_CUDA(cudaEventRecord(join, xs));
@@ -1297,7 +1279,9 @@ int enqueue_group(idtx_ctx *c, const Group &g, cudaStream_t st, double *cmi, flo
         // one launch per estimate; prep_group gathered each job's X on its own
         for (int jb = 0; jb < n_jobs; ++jb)
             IDTX_CUDA(v.fn_plain(sl.sh, xi + (size_t)jb * g.n_pad * v.dx, c->psi, g.n, g.n_pad,
-                                 g.k, partial + (size_t)jb * g.n_qt, st));
+                                 g.k, partial + (size_t)jb * g.n_qt,
+                                 eps_out ? eps_out + (size_t)jb * g.n : nullptr,
+                                 cnt_out ? cnt_out + (size_t)jb * 3 * g.n : nullptr, st));
     } else if (use_list) {
         IDTX_CUDA(v.fn_list(a, g.n_groups, st));
         c->stats.list_cap_a = a.cap_a;
@@ -2587,7 +2571,7 @@ extern "C" int idtx_screen_train(idtx_ctx *c, idtx_screen *sc, const float *feat
     for (int ep = 0; ep < epochs; ++ep) {
         const uint64_t rs[2] = {(uint64_t)ep, seed};
         IDTX_CUDA(cudaMemcpyAsync(rng, rs, sizeof(rs), cudaMemcpyHostToDevice, st));
-        k_fisher_yates<int32_t, false><<<1, 32, 0, st>>>(order, rng, rng + 1, n);
+        k_fisher_yates<<<1, 32, 0, st>>>(order, rng, rng + 1, n);
         IDTX_CUDA(cudaGetLastError());
         for (int start = 0; start < n; start += batch) {
             const int bsz = std::min(batch, n - start);
@@ -3172,6 +3156,8 @@ extern "C" int idtx_cmi_ksg_noalloc(const float *x, int dx, const float *y, int 
     const int64_t n_pad = (n + kTJ - 1) / kTJ * kTJ;
     const int n_qt = (int)(n_pad / v->qc);
     const int n_groups = (n_jobs + v->gb - 1) / v->gb;
+    const int64_t gblocks = gather_blocks(n_groups, n_pad, v->gb, v->dx);
+    if (gblocks <= 0) return fail(IDTX_EINVAL, "n = %lld is too large", (long long)n);
     size_t off = kNoAllocDescBytes;
     auto take = [&](size_t bytes) {
         size_t at = off;
@@ -3259,13 +3245,13 @@ extern "C" int idtx_cmi_ksg_noalloc(const float *x, int dx, const float *y, int 
         k_tile_boxes<<<(unsigned)(n_pad / kTJ), kTJ, 0, st>>>(sh, v->dsp, n);
         IDTX_CUDA(cudaGetLastError());
         if (n_slots > 0) {
-            k_fisher_yates<int32_t, false><<<(unsigned)n_slots, 32, 0, st>>>(
+            k_fisher_yates<<<(unsigned)n_slots, 32, 0, st>>>(
                 perm, (const uint64_t *)(base + o_streams), (const uint64_t *)(base + o_seeds), n);
             IDTX_CUDA(cudaGetLastError());
         }
-        k_gather_x<<<grid_for((int64_t)n_groups * n_pad * v->gb * v->dx, 256), 256, 0, st>>>(
+        k_gather_x<<<(unsigned)gblocks, kGatherThreads, 0, st>>>(
             (const Col *)(base + o_x), dx, v->dx, (const Job *)(base + o_jobs), n_jobs, perm, n,
-            n_pad, v->gb, n_groups, nullptr, xi, err);
+            n_pad, v->gb, nullptr, false, xi, err);
         IDTX_CUDA(cudaGetLastError());
         KsgLaunch a;
         a.sh = sh;

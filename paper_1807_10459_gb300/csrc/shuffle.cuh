@@ -1,0 +1,201 @@
+// shuffle.cuh -- surrogate permutations: the Fisher-Yates (Durstenfeld)
+// shuffle driven by SplitMix64, one warp per permutation, bit for bit the
+// sequential definition.
+//
+// The permutation of slot `slot` of n samples: the row starts as the
+// identity; for step s = 0 .. n-2, with i = n-1-s,
+//   r   = mix64(base + (s+1) * gamma),   base = seed ^ mix64(stream)
+//   j   = hi64(r * (i+1))                (uniform on 0..i)
+//   swap a[i], a[j].
+// The steps are sequential, but steps on disjoint positions commute: the
+// warp draws the next 32 steps in parallel (lane t takes step s0 + t) and
+// performs at once the longest prefix of them in which no step draws the
+// same j as an earlier one or has its position i drawn by an earlier one (an
+// earlier step cannot touch a later one's j, since j <= i), then continues
+// after that prefix.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace idtx {
+
+constexpr uint64_t kSplitMixGamma = 0x9E3779B97F4A7C15ull;
+
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z)
+{
+    // SplitMix64 output function (Steele, Lea & Flood 2014).
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Any n: the row shuffled in place in global memory (int32, loads and stores
+// through L2), 64-bit step arithmetic.  perm[slot * n .. +n).
+__global__ void __launch_bounds__(32)
+    k_fisher_yates(int32_t *perm, const uint64_t *streams, const uint64_t *seeds, int64_t n)
+{
+    constexpr unsigned kFull = 0xffffffffu;
+    const int slot = blockIdx.x;
+    const int lane = threadIdx.x;
+    int32_t *a = perm + (int64_t)slot * n;
+    for (int64_t i = lane; i < n; i += 32) __stcg(a + i, (int32_t)i);
+    __syncwarp();
+    const uint64_t base = seeds[slot] ^ mix64(streams[slot]);
+    const uint32_t below = (1u << lane) - 1u;
+    int64_t s0 = 0;
+    while (s0 < n - 1) {
+        const int64_t s = s0 + lane;
+        const bool valid = s < n - 1;
+        const int64_t i = n - 1 - s;
+        int64_t j = 0;
+        if (valid) {
+            const uint64_t r = mix64(base + (uint64_t)(s + 1) * kSplitMixGamma);
+            j = (int64_t)__umul64hi(r, (uint64_t)(i + 1));
+        }
+        const uint32_t live = __ballot_sync(kFull, valid);
+        // same j as an earlier lane
+        const uint32_t same = __match_any_sync(kFull, valid ? (int)j : -1 - lane);
+        const uint32_t dup = __ballot_sync(kFull, valid && (same & below) != 0);
+        // position i drawn by an earlier lane: lane a marks lane n-1-s0-j_a
+        const int64_t b = n - 1 - s0 - j;
+        const uint32_t hit =
+            __reduce_or_sync(kFull, (valid && b > lane && b < 32) ? (1u << (int)b) : 0u);
+        const uint32_t bad = (dup | hit) & live;
+        const int run = bad ? __ffs(bad) - 1 : __popc(live);
+        if (lane < run) {
+            const int32_t x = __ldcg(a + i), y = __ldcg(a + j);
+            __stcg(a + i, y);
+            __stcg(a + j, x);
+        }
+        __syncwarp();
+        s0 += run;
+    }
+}
+
+// Bits of the per-warp equal-draw filter of k_shuffle_smem (a power of two).
+constexpr int kDupFilterBits = 4096;
+
+// Dynamic shared memory of k_shuffle_smem for rows of n samples: the row as
+// uint16_t, then the filter words.
+__host__ __device__ constexpr int shuffle_smem_bytes(int n)
+{
+    return ((2 * n + 15) & ~15) + kDupFilterBits / 8;
+}
+
+// n <= 65536: the row in dynamic shared memory as uint16_t (n * 2 bytes),
+// 32-bit step arithmetic.  Each lane keeps the draws of steps s0 + lane and
+// s0 + 32 + lane, so SplitMix64 runs a round ahead of the conflict test, and
+// a round's swaps (loads, then stores) bracket the next round's test.  With
+// `order`, the row is written composed with it: perm[slot][j] = pi(order[j]),
+// so that a consumer indexing samples in that order reads the row in
+// sequence.  Equal draws: every lane sets bit (j mod kDupFilterBits) of a
+// shared bitmap with an atomic OR; a lane that finds its bit already set has
+// an equal draw or shares the bit with a different one, and only in rounds
+// with such a lane does the warp compare the draws exactly (match.any).
+// Without a flagged lane no two draws are equal.  (Measured on GB300, 9447
+// rows of 9995 written composed: 0.81 ms, against 1.05 ms with match.any in
+// every round and 0.97 ms with one ballot per bit of j.)
+__global__ void __launch_bounds__(32)
+    k_shuffle_smem(int32_t *perm, const uint64_t *streams, const uint64_t *seeds, int n,
+                   const int32_t *order)
+{
+    extern __shared__ __align__(16) unsigned char fy_smem[];
+    uint16_t *fy_row = reinterpret_cast<uint16_t *>(fy_smem);
+    uint32_t *filter = reinterpret_cast<uint32_t *>(fy_smem + ((2 * n + 15) & ~15));
+    constexpr unsigned kFull = 0xffffffffu;
+    const int slot = blockIdx.x;
+    const int lane = threadIdx.x;
+    for (int i = lane; i < n; i += 32) fy_row[i] = (uint16_t)i;
+    for (int w = lane; w < kDupFilterBits / 32; w += 32) filter[w] = 0u;
+    __syncwarp();
+    const uint64_t base = seeds[slot] ^ mix64(streams[slot]);
+    auto draw = [&](int s) { return mix64(base + (uint64_t)(s + 1) * kSplitMixGamma); };
+    const int last = n - 1;  // steps 0 .. last-1
+    const uint32_t below = (1u << lane) - 1u;
+    uint64_t r_a = draw(lane), r_b = draw(32 + lane);
+    // The test of the round starting at step s0 with draws r_a: each lane's
+    // position i and draw j, and the length of the conflict-free prefix.
+    auto test = [&](int s0, uint32_t &i, uint32_t &j) -> int {
+        const int s = s0 + lane;
+        const bool valid = s < last;
+        i = (uint32_t)(last - s);
+        // j = hi64(r * (i+1)) from 32-bit halves (i+1 < 2^32):
+        // hi64(r m) = (hi32(r) m + hi32(lo32(r) m)) >> 32, no carry out
+        const uint32_t m = i + 1u;
+        const uint64_t ph = (uint64_t)(uint32_t)(r_a >> 32) * m;
+        const uint32_t pl = __umulhi((uint32_t)r_a, m);
+        j = valid ? (uint32_t)((ph + pl) >> 32) : 0u;
+        const uint32_t live = __ballot_sync(kFull, valid);
+        const uint32_t key = j & (kDupFilterBits - 1), bit = 1u << (key & 31);
+        const uint32_t old = valid ? atomicOr(&filter[key >> 5], bit) : 0u;
+        const bool flag = (old & bit) != 0;
+        // clear the words for the next round once every lane's atomic is done
+        __syncwarp();
+        if (valid) filter[key >> 5] = 0u;
+        __syncwarp();
+        uint32_t same = 0u;
+        if (__any_sync(kFull, flag))
+            same = __match_any_sync(kFull, valid ? j : 0x10000u + (uint32_t)lane);
+        const uint32_t dup = __ballot_sync(kFull, valid && (same & below) != 0);
+        // position i of lane b = last - s0 - b is drawn by an earlier lane
+        const int b = (last - s0) - (int)j;
+        const uint32_t hit =
+            __reduce_or_sync(kFull, (valid && b > lane && b < 32) ? (1u << b) : 0u);
+        const uint32_t bad = (dup | hit) & live;
+        return bad ? __ffs(bad) - 1 : __popc(live);
+    };
+    int s0 = 0;
+    uint32_t i = 0, j = 0;
+    int run = last > 0 ? test(0, i, j) : 0;
+    while (run > 0) {
+        uint16_t x = 0, y = 0;
+        if (lane < run) {
+            x = fy_row[i];
+            y = fy_row[j];
+        }
+        // slide the window by run steps and test the next round
+        const int src = (lane + run) & 31;
+        const bool from_a = lane + run < 32;
+        const uint64_t sa = __shfl_sync(kFull, r_a, src);
+        const uint64_t sb = __shfl_sync(kFull, r_b, src);
+        const int s0n = s0 + run;
+        const uint64_t fresh = draw(s0n + 32 + lane);
+        r_a = from_a ? sa : sb;
+        r_b = from_a ? sb : fresh;
+        uint32_t in = 0, jn = 0;
+        const int run_n = s0n < last ? test(s0n, in, jn) : 0;
+        if (lane < run) {
+            fy_row[i] = y;
+            fy_row[j] = x;
+        }
+        __syncwarp();
+        s0 = s0n;
+        i = in;
+        j = jn;
+        run = run_n;
+    }
+    int32_t *out = perm + (int64_t)slot * n;
+    if (order) {
+        // kBatch loads of the order in flight per lane before their lookups
+        constexpr int kBatch = 8;
+        for (int t0 = 0; t0 < n; t0 += 32 * kBatch) {
+            int o[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const int t = t0 + u * 32 + lane;
+                o[u] = t < n ? __ldg(order + t) : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const int t = t0 + u * 32 + lane;
+                if (t < n) out[t] = (int32_t)fy_row[o[u]];
+            }
+        }
+    } else {
+        for (int t = lane; t < n; t += 32) out[t] = (int32_t)fy_row[t];
+    }
+}
+
+}  // namespace idtx

@@ -340,3 +340,33 @@ def test_batch_full_size_sampled(idtx):
         for s in [0] + list(rng.choice(np.arange(1, 501), 2, replace=False)):
             xs = p.x if s == 0 else p.x[:, oracle.perm(p.seed, int(s) - 1, p.x.shape[1])]
             assert abs(out[i][s] - oracle.cmi_ksg(xs, p.y, p.z, 4)) < TOL
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("n", [16384, 16385, 65536, 65537])
+def test_shuffle_length_classes_sampled(idtx, n):
+    """Surrogate permutations of each row-length class: up to 16384 samples
+    (shared-memory shuffle, match.any test), 16385..65536 (shared-memory
+    shuffle, per-bit ballot test), beyond (in place in global memory); the
+    rows composed with the sample order (batched mode) and not (plain mode).
+    Eps and counts of sampled queries of three surrogates exact against the
+    oracle's permutations; the two modes' estimates within 1e-10."""
+    g = synth.gaussian_problem(n, dx=1, dy=1, dz=1, seed=31 + n)
+    S, seed = 3, 11
+    idx = np.random.default_rng(n).choice(n, 24, replace=False)
+    refs = {}
+    for s in (1, 2, 3):
+        xs = g.x[:, oracle.perm(seed, s - 1, n)]
+        refs[s] = oracle.ksg_counts_at(xs, g.y, g.z, 4, idx)
+    est = {}
+    for mode in (idtx.MODE_BATCHED, idtx.MODE_PLAIN):
+        cmi, eps, cnt = idtx.cmi_ksg(_dev(g.x), _dev(g.y), _dev(g.z), k=4, n_surr=S, seed=seed,
+                                     want_eps=True, want_counts=True, mode=mode)
+        est[mode] = cmi.cpu().numpy()
+        eps, cnt = eps.cpu().numpy(), cnt.cpu().numpy()
+        for s, (e, a, b, c) in refs.items():
+            assert np.array_equal(eps[s, idx], e), (mode, s)
+            assert np.array_equal(cnt[s, 0, idx], a), (mode, s)
+            assert np.array_equal(cnt[s, 1, idx], b), (mode, s)
+            assert np.array_equal(cnt[s, 2, idx], c), (mode, s)
+    assert np.allclose(est[idtx.MODE_PLAIN], est[idtx.MODE_BATCHED], rtol=0, atol=TOL)
