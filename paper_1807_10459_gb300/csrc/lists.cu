@@ -26,6 +26,11 @@ constexpr int kBins = 4096;          // bins on bits 30..19 of a non-negative fl
 constexpr int kBinShift = 19;
 constexpr int kBinsPerThread = kBins / kLThreads;
 
+// Digit width of the block radix sorts: 7 passes over a 32-bit key instead
+// of CUB's default 8 (measured on GB300: 1.82 against 1.97 ms for 9995
+// queries, lists of 2048 and 4096; 6 bits spills).
+constexpr int kSortRadixBits = 5;
+
 constexpr int kMaxRow4 = 5;  // float4 columns of a row of sh: dsp <= 20 (dz' <= 16, dy <= 4)
 constexpr int kUnrollJ = 4;  // samples a thread has in flight per step of a distance pass
 
@@ -87,7 +92,7 @@ template <int ITEMS>
 __device__ void sort_and_store(const uint32_t *keys, const int32_t *vals, int n, int cap,
                                void *tmp, int2 *out)
 {
-    using Sort = cub::BlockRadixSort<uint32_t, kLThreads, ITEMS, int32_t>;
+    using Sort = cub::BlockRadixSort<uint32_t, kLThreads, ITEMS, int32_t, kSortRadixBits>;
     uint32_t k[ITEMS];
     int32_t v[ITEMS];
     const int t0 = threadIdx.x * ITEMS;
@@ -112,7 +117,7 @@ __device__ void sort_and_store(const uint32_t *keys, const int32_t *vals, int n,
 template <int ITEMS>
 constexpr size_t sort_tmp_bytes()
 {
-    return sizeof(typename cub::BlockRadixSort<uint32_t, kLThreads, ITEMS, int32_t>::TempStorage);
+    return sizeof(typename cub::BlockRadixSort<uint32_t, kLThreads, ITEMS, int32_t, kSortRadixBits>::TempStorage);
 }
 
 // One block per query.  Dynamic shared memory (build_smem): the two

@@ -232,7 +232,7 @@ __global__ void k_expand_reps(const int32_t *blk, int n_slots, int64_t n_reps, i
     }
 }
 
-constexpr int kGatherRows = 32;     // sample rows per CTA of k_gather_x
+constexpr int kGatherRows = kTJ % 64 == 0 ? 64 : 32;  // sample rows per CTA of k_gather_x
 constexpr int kGatherThreads = 256;
 constexpr int kGatherMaxWidth = 32 * 4;  // jobs per group x padded X width
 constexpr int kGatherJobsPerWarp = 4;    // 32 jobs per group over 8 warps
@@ -242,52 +242,63 @@ constexpr int kGatherJobsPerWarp = 4;    // 32 jobs per group over 8 warps
 // +inf for j >= n.  With `composed`, the permutation rows already hold
 // pi(order[j]) at j (k_shuffle_smem, k_expand_reps), so a warp reads 32
 // consecutive entries of a row.  A CTA fills kGatherRows consecutive rows of
-// one group: warp w takes the jobs g = w, w + 8, ... (all their permutation
-// loads issued before the first is used), lane l the row j0 + l; the values
-// are staged in shared memory and the rows, contiguous in xi, are written
-// out in sequence.  Grid: n_groups * (n_pad / kGatherRows) CTAs.
+// one group: warp w takes the jobs g = w, w + 8, ..., lane l the rows
+// j0 + l + 32 h; all of a warp's permutation loads are issued before the
+// first is used; the values are staged in shared memory and the rows,
+// contiguous in xi, are written out in sequence.  Grid: n_groups * (n_pad /
+// kGatherRows) CTAs.
 __global__ void __launch_bounds__(kGatherThreads)
     k_gather_x(const Col *xc, int dx, int dxb, const Job *jobs, int n_jobs,
                const int32_t *perm, int64_t n, int64_t n_pad, int gb, const int32_t *order,
                bool composed, float *xi, int *err)
 {
-    constexpr int kWarps = kGatherThreads / 32;
+    constexpr int kWarps = kGatherThreads / 32, kHalves = kGatherRows / 32;
     __shared__ float s_x[kGatherRows * (kGatherMaxWidth + 1)];
     const int xw = gb * dxb, ld = xw + 1;
     const int64_t tiles = n_pad / kGatherRows;
     const int64_t grp = blockIdx.x / tiles;
     const int64_t j0 = (blockIdx.x - grp * tiles) * kGatherRows;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t j = j0 + lane;
-    const bool in = j < n;
-    const int64_t t0 = in ? (order ? (int64_t)order[j] : j) : 0;
-    const int64_t at = composed ? j : t0;  // this row's position in a permutation row
+    bool in[kHalves];
+    int64_t t0[kHalves], at[kHalves];
+#pragma unroll
+    for (int h = 0; h < kHalves; ++h) {
+        const int64_t j = j0 + h * 32 + lane;
+        in[h] = j < n;
+        t0[h] = in[h] ? (order ? (int64_t)order[j] : j) : 0;
+        at[h] = composed ? j : t0[h];  // the row's position in a permutation row
+    }
     Job jb[kGatherJobsPerWarp];
-    int64_t t[kGatherJobsPerWarp];
 #pragma unroll
     for (int u = 0; u < kGatherJobsPerWarp; ++u) {
         int64_t job = grp * gb + warp + u * kWarps;
         if (job >= n_jobs) job = 0;
         jb[u] = jobs[job];
     }
+    int64_t t[kGatherJobsPerWarp][kHalves];
 #pragma unroll
-    for (int u = 0; u < kGatherJobsPerWarp; ++u) {
-        const bool use = warp + u * kWarps < gb && in && jb[u].slot >= 0;
-        t[u] = use ? (int64_t)perm[(int64_t)jb[u].slot * n + at] : t0;
-    }
+    for (int u = 0; u < kGatherJobsPerWarp; ++u)
+#pragma unroll
+        for (int h = 0; h < kHalves; ++h) {
+            const bool use = warp + u * kWarps < gb && in[h] && jb[u].slot >= 0;
+            t[u][h] = use ? (int64_t)perm[(int64_t)jb[u].slot * n + at[h]] : t0[h];
+        }
 #pragma unroll
     for (int u = 0; u < kGatherJobsPerWarp; ++u) {
         const int g = warp + u * kWarps;
         if (g >= gb) break;
-        float *dst = s_x + lane * ld + g * dxb;
         for (int d = 0; d < dxb; ++d) {
-            float v = in ? 0.0f : INFINITY;
-            if (in && d < dx) {
-                const Col c = xc[(int64_t)jb[u].src * dx + d];
-                v = c.base[c.off + t[u]];
-                if (!isfinite(v)) atomicOr(err, kErrNonFinite);
+            const bool real = d < dx;
+            const Col c = real ? xc[(int64_t)jb[u].src * dx + d] : Col{nullptr, 0};
+#pragma unroll
+            for (int h = 0; h < kHalves; ++h) {
+                float v = in[h] ? 0.0f : INFINITY;
+                if (in[h] && real) {
+                    v = c.base[c.off + t[u][h]];
+                    if (!isfinite(v)) atomicOr(err, kErrNonFinite);
+                }
+                s_x[(h * 32 + lane) * ld + g * dxb + d] = v;
             }
-            dst[d] = v;
         }
     }
     __syncthreads();
