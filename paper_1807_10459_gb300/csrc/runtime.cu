@@ -992,14 +992,20 @@ int take_event(idtx_ctx *c, cudaEvent_t *ev)
     return IDTX_OK;
 }
 
-// One-time attribute of the shared-memory shuffle (per device; the attribute
-// is per function and device).  Also called before a graph capture.
+// One-time attributes of the shared-memory shuffles (per device; the
+// attribute is per function and device).  Also called before a graph capture.
 int init_permutation_kernel()
 {
     static DeviceOnce attr;
     IDTX_CUDA(once_per_device(attr, [](int) {
-        return cudaFuncSetAttribute(k_shuffle_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    shuffle_smem_bytes(65536));
+        cudaError_t e = cudaFuncSetAttribute(k_shuffle_smem<true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             shuffle_smem_bytes(kPosFlagMaxN, true));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_shuffle_smem<false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     shuffle_smem_bytes(65536, false));
+        return e;
     }));
     return IDTX_OK;
 }
@@ -1015,8 +1021,13 @@ int enqueue_permutations(int32_t *perm, const uint64_t *streams, const uint64_t 
     if (n_slots <= 0) return IDTX_OK;
     if (n <= 65536) {
         IDTX_TRY(init_permutation_kernel());
-        k_shuffle_smem<<<(unsigned)n_slots, 32, shuffle_smem_bytes((int)n), st>>>(
-            perm, streams, seeds, (int)n, order);
+        if (n <= kPosFlagMaxN)
+            k_shuffle_smem<true><<<(unsigned)n_slots, 32, shuffle_smem_bytes((int)n, true), st>>>(
+                perm, streams, seeds, (int)n, order);
+        else
+            k_shuffle_smem<false>
+                <<<(unsigned)n_slots, 32, shuffle_smem_bytes((int)n, false), st>>>(
+                    perm, streams, seeds, (int)n, order);
         *composed = order != nullptr;
     } else {
         k_fisher_yates<<<(unsigned)n_slots, 32, 0, st>>>(perm, streams, seeds, n);

@@ -74,14 +74,15 @@ __global__ void __launch_bounds__(32)
     }
 }
 
-// Bits of the per-warp equal-draw filter of k_shuffle_smem (a power of two).
-constexpr int kDupFilterBits = 4096;
+// Longest row whose entries leave the top bit of a uint16_t free.
+constexpr int kPosFlagMaxN = 32768;
 
-// Dynamic shared memory of k_shuffle_smem for rows of n samples: the row as
-// uint16_t, then the filter words.
-__host__ __device__ constexpr int shuffle_smem_bytes(int n)
+// Dynamic shared memory of k_shuffle_smem<POS_FLAG> for rows of n samples:
+// the row as uint16_t (padded to whole 32-bit words), then, without
+// POS_FLAG, a bitmap of n bits.
+__host__ __device__ constexpr int shuffle_smem_bytes(int n, bool pos_flag)
 {
-    return ((2 * n + 15) & ~15) + kDupFilterBits / 8;
+    return pos_flag ? ((2 * n + 3) & ~3) : ((2 * n + 15) & ~15) + (n + 31) / 32 * 4;
 }
 
 // n <= 65536: the row in dynamic shared memory as uint16_t (n * 2 bytes),
@@ -90,30 +91,39 @@ __host__ __device__ constexpr int shuffle_smem_bytes(int n)
 // a round's swaps (loads, then stores) bracket the next round's test.  With
 // `order`, the row is written composed with it: perm[slot][j] = pi(order[j]),
 // so that a consumer indexing samples in that order reads the row in
-// sequence.  Equal draws: every lane sets bit (j mod kDupFilterBits) of a
-// shared bitmap with an atomic OR; a lane that finds its bit already set has
-// an equal draw or shares the bit with a different one, and only in rounds
-// with such a lane does the warp compare the draws exactly (match.any).
-// Without a flagged lane no two draws are equal.  (Measured on GB300, 9447
-// rows of 9995 written composed: 0.81 ms, against 1.05 ms with match.any in
-// every round and 0.97 ms with one ballot per bit of j.)
+// sequence.
+//
+// Equal draws.  Each lane sets a flag bit for its position j with an atomic
+// OR, and of any lanes with equal draws all but the first to arrive find
+// the bit already set.  A flagged lane is treated as a conflict: that cuts
+// the prefix at a flagged lane of every equal pair, which may be the earlier
+// lane of the pair (the prefix is then shorter than it could be, never
+// wrong).  The flags are cleared before the round's swaps store.  The flag
+// of position j is the top bit of entry j itself when POS_FLAG (n <=
+// kPosFlagMaxN, so every entry leaves that bit free), else bit j of a bitmap
+// after the row.  Measured on GB300, 9447 rows of 9995 written composed:
+// 0.62 ms, against 0.79 ms with a 4096-bit bitmap indexed by j mod 4096
+// (whose flags needed an exact match.any to confirm), 1.05 ms with
+// match.any in every round and 0.97 ms with one ballot per bit of j;
+// match.any has 373 cycles of latency there.
+template <bool POS_FLAG>
 __global__ void __launch_bounds__(32)
     k_shuffle_smem(int32_t *perm, const uint64_t *streams, const uint64_t *seeds, int n,
                    const int32_t *order)
 {
     extern __shared__ __align__(16) unsigned char fy_smem[];
     uint16_t *fy_row = reinterpret_cast<uint16_t *>(fy_smem);
-    uint32_t *filter = reinterpret_cast<uint32_t *>(fy_smem + ((2 * n + 15) & ~15));
+    uint32_t *bitmap = reinterpret_cast<uint32_t *>(fy_smem + ((2 * n + 15) & ~15));
     constexpr unsigned kFull = 0xffffffffu;
     const int slot = blockIdx.x;
     const int lane = threadIdx.x;
     for (int i = lane; i < n; i += 32) fy_row[i] = (uint16_t)i;
-    for (int w = lane; w < kDupFilterBits / 32; w += 32) filter[w] = 0u;
+    if (!POS_FLAG)
+        for (int w = lane; w < (n + 31) / 32; w += 32) bitmap[w] = 0u;
     __syncwarp();
     const uint64_t base = seeds[slot] ^ mix64(streams[slot]);
     auto draw = [&](int s) { return mix64(base + (uint64_t)(s + 1) * kSplitMixGamma); };
     const int last = n - 1;  // steps 0 .. last-1
-    const uint32_t below = (1u << lane) - 1u;
     uint64_t r_a = draw(lane), r_b = draw(32 + lane);
     // The test of the round starting at step s0 with draws r_a: each lane's
     // position i and draw j, and the length of the conflict-free prefix.
@@ -128,17 +138,19 @@ __global__ void __launch_bounds__(32)
         const uint32_t pl = __umulhi((uint32_t)r_a, m);
         j = valid ? (uint32_t)((ph + pl) >> 32) : 0u;
         const uint32_t live = __ballot_sync(kFull, valid);
-        const uint32_t key = j & (kDupFilterBits - 1), bit = 1u << (key & 31);
-        const uint32_t old = valid ? atomicOr(&filter[key >> 5], bit) : 0u;
-        const bool flag = (old & bit) != 0;
-        // clear the words for the next round once every lane's atomic is done
+        uint32_t *word = POS_FLAG ? reinterpret_cast<uint32_t *>(fy_row) + (j >> 1)
+                                  : bitmap + (j >> 5);
+        const uint32_t bit = POS_FLAG ? 0x8000u << ((j & 1u) * 16) : 1u << (j & 31u);
+        const uint32_t old = valid ? atomicOr(word, bit) : 0u;
+        __syncwarp();  // every lane's OR is done before any flag is cleared
+        if (valid) {
+            if (POS_FLAG)
+                atomicAnd(word, ~bit);
+            else
+                *word = 0u;
+        }
         __syncwarp();
-        if (valid) filter[key >> 5] = 0u;
-        __syncwarp();
-        uint32_t same = 0u;
-        if (__any_sync(kFull, flag))
-            same = __match_any_sync(kFull, valid ? j : 0x10000u + (uint32_t)lane);
-        const uint32_t dup = __ballot_sync(kFull, valid && (same & below) != 0);
+        const uint32_t dup = __ballot_sync(kFull, (old & bit) != 0);
         // position i of lane b = last - s0 - b is drawn by an earlier lane
         const int b = (last - s0) - (int)j;
         const uint32_t hit =
@@ -155,6 +167,7 @@ __global__ void __launch_bounds__(32)
             x = fy_row[i];
             y = fy_row[j];
         }
+        if (POS_FLAG) __syncwarp();  // the loads are done before the next test flags
         // slide the window by run steps and test the next round
         const int src = (lane + run) & 31;
         const bool from_a = lane + run < 32;
