@@ -85,12 +85,15 @@ __device__ int cut_bin(const int *hist, int cap, int *s_part, int *s_cut)
 // Sort the n collected (distance bits, sample) pairs of one list ascending by
 // distance and write them, then +inf sentinels up to a multiple of 32 (at
 // most cap), to out.  Ties may land in any order: nothing downstream depends
-// on the order of equal distances.  The pairs are first taken into
-// registers, so the sort's scratch may overlay the collection buffers
-// (tmp); all threads of the block call it.
+// on the order of equal distances.  Every key is below `bound` (the bits of
+// the list's cut, a non-negative float), so only its low 32 - clz(bound)
+// bits can differ and the sort passes over those alone; the padding keys
+// (all ones) stay above every real key in those bits.  The pairs are first
+// taken into registers, so the sort's scratch may overlay the collection
+// buffers (tmp); all threads of the block call it.
 template <int ITEMS>
 __device__ void sort_and_store(const uint32_t *keys, const int32_t *vals, int n, int cap,
-                               void *tmp, int2 *out)
+                               uint32_t bound, void *tmp, int2 *out)
 {
     using Sort = cub::BlockRadixSort<uint32_t, kLThreads, ITEMS, int32_t, kSortRadixBits>;
     uint32_t k[ITEMS];
@@ -103,7 +106,8 @@ __device__ void sort_and_store(const uint32_t *keys, const int32_t *vals, int n,
         v[i] = at < n ? vals[at] : 0;
     }
     __syncthreads();  // the collection buffers may now be overwritten
-    Sort(*reinterpret_cast<typename Sort::TempStorage *>(tmp)).Sort(k, v, 0, 32);
+    const int end_bit = max(1, 32 - __clz(bound));
+    Sort(*reinterpret_cast<typename Sort::TempStorage *>(tmp)).Sort(k, v, 0, end_bit);
     const int end = min(cap, (n + 31) & ~31);
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
@@ -240,8 +244,8 @@ __global__ void __launch_bounds__(kLThreads, 3)
     const int na = min(s_cnt[0], cap_a), nb = min(s_cnt[1], cap_b);
     // List B first: its pairs go to registers, then its scratch overlays
     // list B's buffers (list A's stay intact below them).
-    sort_and_store<IB>(key_b, val_b, nb, cap_b, key_b, list_b + i * cap_b);
-    sort_and_store<IA>(key_a, val_a, na, cap_a, key_a, list_a + i * cap_a);
+    sort_and_store<IB>(key_b, val_b, nb, cap_b, __float_as_uint(r_b), key_b, list_b + i * cap_b);
+    sort_and_store<IA>(key_a, val_a, na, cap_a, __float_as_uint(r_a), key_a, list_a + i * cap_a);
     if (tid == 0) meta[i] = make_int4(na, nb, __float_as_int(r_a), __float_as_int(r_b));
 }
 
