@@ -76,6 +76,13 @@
 #ifndef IDTX_LIST_REPACK
 #define IDTX_LIST_REPACK 8
 #endif
+// Entries a lane takes per step of a repacked count phase (their X loads are
+// in flight together; a step's entries past the lane's share are predicated
+// off).  Measured on GB300, list kernel of the greedy step: 1 / 2 / 4 / 8
+// entries 15.80 / 15.75 / 16.05 / 17.72 ms.
+#ifndef IDTX_LIST_PHASE_STEP
+#define IDTX_LIST_PHASE_STEP 2
+#endif
 // Job groups per super-block of the chunk order (see the kernel).
 #ifndef IDTX_LIST_GSB
 #define IDTX_LIST_GSB 16
@@ -480,7 +487,7 @@ __global__ void __launch_bounds__(ListShape<DX, DY, DZ, K1, EXACT, QCTA, NWARPS>
             walked_b = cf + co < len_b ? cf + co : len_b;
             // Repacked phases: M job slots (M a power of two <= 16), slot s on
             // lanes s, s+M, ..., which take the staged chunk's entries r,
-            // r + 32/M, ... (r = lane / M), four per step.
+            // r + 32/M, ... (r = lane / M), IDTX_LIST_PHASE_STEP per step.
             while (rem) {
                 const int c = __popc(rem);
                 const int lg = c > 8 ? 4 : (c > 4 ? 3 : (c > 2 ? 2 : (c > 1 ? 1 : 0)));
@@ -499,11 +506,12 @@ __global__ void __launch_bounds__(ListShape<DX, DY, DZ, K1, EXACT, QCTA, NWARPS>
                 int cz = 0, cx = 0;
                 uint32_t still = 0;
                 while (true) {
-                    for (int u0 = 0; u0 < M; u0 += 4) {
-                        bool in[4];
-                        float xv[4][DX];
+                    for (int u0 = 0; u0 < M; u0 += IDTX_LIST_PHASE_STEP) {
+                        constexpr int PS = IDTX_LIST_PHASE_STEP;
+                        bool in[PS];
+                        float xv[PS][DX];
 #pragma unroll
-                        for (int t = 0; t < 4; ++t) {
+                        for (int t = 0; t < PS; ++t) {
                             const int idx = r + per * (u0 + t);
                             const int2 e = ent[idx & 31];
                             in[t] = u0 + t < M && idx >= co && __int_as_float(e.y) < es;
@@ -512,7 +520,7 @@ __global__ void __launch_bounds__(ListShape<DX, DY, DZ, K1, EXACT, QCTA, NWARPS>
                             for (int d = 0; d < DX; ++d) xv[t][d] = in[t] ? xr[d] : xs[d];
                         }
 #pragma unroll
-                        for (int t = 0; t < 4; ++t) {
+                        for (int t = 0; t < PS; ++t) {
                             float dxv = fabsf(xs[0] - xv[t][0]);
 #pragma unroll
                             for (int d = 1; d < DX; ++d) dxv = fmaxf(dxv, fabsf(xs[d] - xv[t][d]));

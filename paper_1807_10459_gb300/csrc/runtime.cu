@@ -3266,11 +3266,11 @@ extern "C" int idtx_cmi_ksg_noalloc(const float *x, int dx, const float *y, int 
         IDTX_CUDA(cudaGetLastError());
         k_tile_boxes<<<(unsigned)(n_pad / kTJ), kTJ, 0, st>>>(sh, v->dsp, n);
         IDTX_CUDA(cudaGetLastError());
-        if (n_slots > 0) {
-            k_fisher_yates<<<(unsigned)n_slots, 32, 0, st>>>(
-                perm, (const uint64_t *)(base + o_streams), (const uint64_t *)(base + o_seeds), n);
-            IDTX_CUDA(cudaGetLastError());
-        }
+        int unused_launches = 0;
+        bool composed = false;
+        IDTX_TRY(enqueue_permutations(perm, (const uint64_t *)(base + o_streams),
+                                      (const uint64_t *)(base + o_seeds), n_slots, n, nullptr, st,
+                                      unused_launches, &composed));
         k_gather_x<<<(unsigned)gblocks, kGatherThreads, 0, st>>>(
             (const Col *)(base + o_x), dx, v->dx, (const Job *)(base + o_jobs), n_jobs, perm, n,
             n_pad, v->gb, nullptr, false, xi, err);
