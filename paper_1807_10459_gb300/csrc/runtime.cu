@@ -244,8 +244,10 @@ constexpr int kGatherJobsPerWarp = 4;    // 32 jobs per group over 8 warps
 // consecutive entries of a row.  A CTA fills kGatherRows consecutive rows of
 // one group: warp w takes the jobs g = w, w + 8, ..., lane l the rows
 // j0 + l + 32 h; all of a warp's permutation loads are issued before the
-// first is used; the values are staged in shared memory and the rows,
-// contiguous in xi, are written out in sequence.  Grid: n_groups * (n_pad /
+// first is used; the values are staged in shared memory (gather_smem bytes)
+// and the rows, contiguous in xi, are written out in sequence.  Permutation
+// entries and xi are touched once: loaded and stored as streaming, so that L1
+// keeps the X columns the random reads hit.  Grid: n_groups * (n_pad /
 // kGatherRows) CTAs.
 __global__ void __launch_bounds__(kGatherThreads)
     k_gather_x(const Col *xc, int dx, int dxb, const Job *jobs, int n_jobs,
@@ -253,7 +255,7 @@ __global__ void __launch_bounds__(kGatherThreads)
                bool composed, float *xi, int *err)
 {
     constexpr int kWarps = kGatherThreads / 32, kHalves = kGatherRows / 32;
-    __shared__ float s_x[kGatherRows * (kGatherMaxWidth + 1)];
+    extern __shared__ float s_x[];  // [kGatherRows][xw + 1]
     const int xw = gb * dxb, ld = xw + 1;
     const int64_t tiles = n_pad / kGatherRows;
     const int64_t grp = blockIdx.x / tiles;
@@ -281,7 +283,7 @@ __global__ void __launch_bounds__(kGatherThreads)
 #pragma unroll
         for (int h = 0; h < kHalves; ++h) {
             const bool use = warp + u * kWarps < gb && in[h] && jb[u].slot >= 0;
-            t[u][h] = use ? (int64_t)perm[(int64_t)jb[u].slot * n + at[h]] : t0[h];
+            t[u][h] = use ? (int64_t)__ldcs(perm + (int64_t)jb[u].slot * n + at[h]) : t0[h];
         }
 #pragma unroll
     for (int u = 0; u < kGatherJobsPerWarp; ++u) {
@@ -305,8 +307,14 @@ __global__ void __launch_bounds__(kGatherThreads)
     float *out = xi + (grp * n_pad + j0) * xw;
     for (int e = threadIdx.x; e < kGatherRows * xw; e += kGatherThreads) {
         const int r = e / xw;
-        out[e] = s_x[r * ld + (e - r * xw)];
+        __stcs(out + e, s_x[r * ld + (e - r * xw)]);
     }
+}
+
+// Dynamic shared memory of k_gather_x: the staged rows.
+static size_t gather_smem(int gb, int dxb)
+{
+    return (size_t)kGatherRows * (gb * dxb + 1) * sizeof(float);
 }
 
 // The gather's grid; 0 when the shape is outside its limits.
@@ -1164,7 +1172,7 @@ int prep_group(idtx_ctx *c, const Group &g, cudaStream_t st, const Slices &sl, f
     const int gx = g.plain ? 1 : v.gb, ngx = g.plain ? n_jobs : g.n_groups;
     const int64_t gblocks = gather_blocks(ngx, g.n_pad, gx, v.dx);
     if (gblocks <= 0) return fail(IDTX_EINTERNAL, "gather shape out of range");
-    k_gather_x<<<(unsigned)gblocks, kGatherThreads, 0, xs>>>(
+    k_gather_x<<<(unsigned)gblocks, kGatherThreads, gather_smem(gx, v.dx), xs>>>(
         xc, g.dx, v.dx, jobs, n_jobs, perm, g.n, g.n_pad, gx, order, composed, xi, c->d_err);
     IDTX_CUDA(cudaGetLastError());
     if (a.list_a) {
@@ -3271,7 +3279,7 @@ extern "C" int idtx_cmi_ksg_noalloc(const float *x, int dx, const float *y, int 
         IDTX_TRY(enqueue_permutations(perm, (const uint64_t *)(base + o_streams),
                                       (const uint64_t *)(base + o_seeds), n_slots, n, nullptr, st,
                                       unused_launches, &composed));
-        k_gather_x<<<(unsigned)gblocks, kGatherThreads, 0, st>>>(
+        k_gather_x<<<(unsigned)gblocks, kGatherThreads, gather_smem(v->gb, v->dx), st>>>(
             (const Col *)(base + o_x), dx, v->dx, (const Job *)(base + o_jobs), n_jobs, perm, n,
             n_pad, v->gb, nullptr, false, xi, err);
         IDTX_CUDA(cudaGetLastError());
