@@ -33,10 +33,10 @@ METRIC = "KSG CMI estimates/s incl. surrogates (N=1e4,k=4); batched/screened vs 
 # Tile kernel: profiles/ksg_fused_kernel_greedy_step_small.md (15-surrogate case,
 # 31.68 MB, scaled by job groups 296/24).  List kernel: captured directly on the
 # full-size launch (profiles/ksg_list_kernel_greedy_step_small.md).
-TRAFFIC_BYTES = {"tile": 390.7e6, "list": 3238.4e6 + 735.4e6}
+TRAFFIC_BYTES = {"tile": 390.7e6, "list": 3288.1e6 + 744.7e6}
 # Pipe utilisation of the list kernel from its committed full ncu capture
 # (small case of the same step; profiles/ksg_list_kernel_greedy_step_small.md).
-PIPES_FROM_PROFILE = {"alu_pct": 50.2, "fma_pct": 29.1, "lsu_pct": 32.1, "issue_active_pct": 72.5,
+PIPES_FROM_PROFILE = {"alu_pct": 49.5, "fma_pct": 28.9, "lsu_pct": 30.7, "issue_active_pct": 71.5,
                       "l1_hit_pct": 68.6, "unit": "% of each pipe's peak, sustained active",
                       "source": "profiles/ksg_list_kernel_greedy_step_small.md"}
 
