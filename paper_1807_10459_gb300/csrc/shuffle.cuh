@@ -98,7 +98,9 @@ __host__ __device__ constexpr int shuffle_smem_bytes(int n, bool pos_flag)
 // the bit already set.  A flagged lane is treated as a conflict: that cuts
 // the prefix at a flagged lane of every equal pair, which may be the earlier
 // lane of the pair (the prefix is then shorter than it could be, never
-// wrong).  The flags are cleared before the round's swaps store.  The flag
+// wrong; when that lane is the round's first it runs alone).  The order in
+// which the hardware serves a warp's atomics is not relied on.  The flags
+// are cleared before the round's swaps store.  The flag
 // of position j is the top bit of entry j itself when POS_FLAG (n <=
 // kPosFlagMaxN, so every entry leaves that bit free), else bit j of a bitmap
 // after the row.  Measured on GB300, 9447 rows of 9995 written composed:
@@ -156,7 +158,10 @@ __global__ void __launch_bounds__(32)
         const uint32_t hit =
             __reduce_or_sync(kFull, (valid && b > lane && b < 32) ? (1u << b) : 0u);
         const uint32_t bad = (dup | hit) & live;
-        return bad ? __ffs(bad) - 1 : __popc(live);
+        // Lane 0 never conflicts (no earlier lane), but its flag is set when
+        // a later equal draw's atomic was served first: it then runs alone.
+        // Every round so advances by at least one step.
+        return bad ? max(1, __ffs(bad) - 1) : __popc(live);
     };
     int s0 = 0;
     uint32_t i = 0, j = 0;
