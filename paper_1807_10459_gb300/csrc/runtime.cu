@@ -1000,46 +1000,69 @@ int take_event(idtx_ctx *c, cudaEvent_t *ev)
     return IDTX_OK;
 }
 
+// Whether this device's blocks may hold the kShufWide row (per device).
+static bool g_shuffle_wide[kMaxDevices];
+
 // One-time attributes of the shared-memory shuffles (per device; the
 // attribute is per function and device).  Also called before a graph capture.
 int init_permutation_kernel()
 {
     static DeviceOnce attr;
-    IDTX_CUDA(once_per_device(attr, [](int) {
-        cudaError_t e = cudaFuncSetAttribute(k_shuffle_smem<true>,
+    IDTX_CUDA(once_per_device(attr, [](int dev) {
+        cudaError_t e = cudaFuncSetAttribute(k_shuffle_smem<kShufPosFlag>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             shuffle_smem_bytes(kPosFlagMaxN, true));
+                                             shuffle_smem_bytes(kPosFlagMaxN, kShufPosFlag));
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_shuffle_smem<false>,
+            e = cudaFuncSetAttribute(k_shuffle_smem<kShufBitmap>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     shuffle_smem_bytes(65536, false));
+                                     shuffle_smem_bytes(65536, kShufBitmap));
+        int optin = 0;
+        if (e == cudaSuccess)
+            e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        const int wide = shuffle_smem_bytes(kWideMaxN, kShufWide);
+        g_shuffle_wide[dev] = e == cudaSuccess && optin >= wide;
+        if (e == cudaSuccess && g_shuffle_wide[dev])
+            e = cudaFuncSetAttribute(k_shuffle_smem<kShufWide>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, wide);
         return e;
     }));
     return IDTX_OK;
 }
 
 // Enqueue the surrogate permutations of n_slots rows of length n.  With
-// `order` (n <= 65536 only) the rows are written composed with it; *composed
-// says whether they were.
+// `order` the rows shuffled in shared memory (n <= kWideMaxN) are written
+// composed with it; *composed says whether they were.
 int enqueue_permutations(int32_t *perm, const uint64_t *streams, const uint64_t *seeds,
                          int n_slots, int64_t n, const int32_t *order, cudaStream_t st,
                          int &launches, bool *composed)
 {
     *composed = false;
     if (n_slots <= 0) return IDTX_OK;
-    if (n <= 65536) {
-        IDTX_TRY(init_permutation_kernel());
-        if (n <= kPosFlagMaxN)
-            k_shuffle_smem<true><<<(unsigned)n_slots, 32, shuffle_smem_bytes((int)n, true), st>>>(
-                perm, streams, seeds, (int)n, order);
-        else
-            k_shuffle_smem<false>
-                <<<(unsigned)n_slots, 32, shuffle_smem_bytes((int)n, false), st>>>(
-                    perm, streams, seeds, (int)n, order);
-        *composed = order != nullptr;
-    } else {
-        k_fisher_yates<<<(unsigned)n_slots, 32, 0, st>>>(perm, streams, seeds, n);
+    IDTX_TRY(init_permutation_kernel());
+    int dev = 0;
+    IDTX_CUDA(cudaGetDevice(&dev));
+    int mode = shuffle_mode(n);
+    if (mode == kShufWide && !g_shuffle_wide[dev]) mode = -1;
+    const unsigned grid = (unsigned)n_slots;
+    const int ni = (int)std::min<int64_t>(n, kWideMaxN);
+    switch (mode) {
+    case kShufPosFlag:
+        k_shuffle_smem<kShufPosFlag><<<grid, 32, shuffle_smem_bytes(ni, mode), st>>>(
+            perm, streams, seeds, ni, order);
+        break;
+    case kShufBitmap:
+        k_shuffle_smem<kShufBitmap><<<grid, 32, shuffle_smem_bytes(ni, mode), st>>>(
+            perm, streams, seeds, ni, order);
+        break;
+    case kShufWide:
+        k_shuffle_smem<kShufWide><<<grid, 32, shuffle_smem_bytes(ni, mode), st>>>(
+            perm, streams, seeds, ni, order);
+        break;
+    default:
+        k_fisher_yates<<<grid, 32, 0, st>>>(perm, streams, seeds, n);
+        break;
     }
+    *composed = mode >= 0 && order != nullptr;
     IDTX_CUDA(cudaGetLastError());
     launches += 1;
     return IDTX_OK;

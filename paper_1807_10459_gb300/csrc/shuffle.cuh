@@ -74,18 +74,32 @@ __global__ void __launch_bounds__(32)
     }
 }
 
-// Longest row whose entries leave the top bit of a uint16_t free.
+// Layouts of k_shuffle_smem's row in shared memory, by row length.
+enum ShuffleMode : int {
+    kShufPosFlag = 0,  // n <= 32768: uint16_t entries, flags in their top bits
+    kShufBitmap = 1,   // n <= 65536: uint16_t entries, then an n-bit flag bitmap
+    kShufWide = 2,     // n <= kWideMaxN: the low 16 bits of the entries, then a
+                       // bitmap of their bit 16, then the flag bitmap
+};
 constexpr int kPosFlagMaxN = 32768;
+constexpr int kWideMaxN = 102400;  // 230400 bytes: within 227 KB of shared memory
 
-// Dynamic shared memory of k_shuffle_smem<POS_FLAG> for rows of n samples:
-// the row as uint16_t (padded to whole 32-bit words), then, without
-// POS_FLAG, a bitmap of n bits.
-__host__ __device__ constexpr int shuffle_smem_bytes(int n, bool pos_flag)
+// Dynamic shared memory of k_shuffle_smem<MODE> for rows of n samples.
+__host__ __device__ constexpr int shuffle_smem_bytes(int n, int mode)
 {
-    return pos_flag ? ((2 * n + 3) & ~3) : ((2 * n + 15) & ~15) + (n + 31) / 32 * 4;
+    return mode == kShufPosFlag
+               ? ((2 * n + 3) & ~3)
+               : ((2 * n + 15) & ~15) + (mode == kShufWide ? 2 : 1) * ((n + 31) / 32) * 4;
 }
 
-// n <= 65536: the row in dynamic shared memory as uint16_t (n * 2 bytes),
+// The layout for a row of n samples (-1: too long for shared memory).
+__host__ __device__ constexpr int shuffle_mode(int64_t n)
+{
+    return n <= kPosFlagMaxN ? kShufPosFlag
+                             : (n <= 65536 ? kShufBitmap : (n <= kWideMaxN ? kShufWide : -1));
+}
+
+// n <= kWideMaxN: the row in dynamic shared memory (layout MODE, above),
 // 32-bit step arithmetic.  Each lane keeps the draws of steps s0 + lane and
 // s0 + 32 + lane, so SplitMix64 runs a round ahead of the conflict test, and
 // a round's swaps (loads, then stores) bracket the next round's test.  With
@@ -100,28 +114,49 @@ __host__ __device__ constexpr int shuffle_smem_bytes(int n, bool pos_flag)
 // lane of the pair (the prefix is then shorter than it could be, never
 // wrong; when that lane is the round's first it runs alone).  The order in
 // which the hardware serves a warp's atomics is not relied on.  The flags
-// are cleared before the round's swaps store.  The flag
-// of position j is the top bit of entry j itself when POS_FLAG (n <=
-// kPosFlagMaxN, so every entry leaves that bit free), else bit j of a bitmap
-// after the row.  Measured on GB300, 9447 rows of 9995 written composed:
+// are cleared before the round's swaps store.  The flag of position j is
+// the top bit of entry j itself in kShufPosFlag (every entry leaves that bit
+// free), else bit j of the flag bitmap.  Measured on GB300, 9447 rows of 9995 written composed:
 // 0.62 ms, against 0.79 ms with a 4096-bit bitmap indexed by j mod 4096
 // (whose flags needed an exact match.any to confirm), 1.05 ms with
 // match.any in every round and 0.97 ms with one ballot per bit of j;
 // match.any has 373 cycles of latency there.
-template <bool POS_FLAG>
+template <int MODE>
 __global__ void __launch_bounds__(32)
     k_shuffle_smem(int32_t *perm, const uint64_t *streams, const uint64_t *seeds, int n,
                    const int32_t *order)
 {
+    constexpr bool POS_FLAG = MODE == kShufPosFlag;
     extern __shared__ __align__(16) unsigned char fy_smem[];
     uint16_t *fy_row = reinterpret_cast<uint16_t *>(fy_smem);
-    uint32_t *bitmap = reinterpret_cast<uint32_t *>(fy_smem + ((2 * n + 15) & ~15));
+    const int words = (n + 31) / 32;
+    uint32_t *hib = reinterpret_cast<uint32_t *>(fy_smem + ((2 * n + 15) & ~15));
+    uint32_t *bitmap = MODE == kShufWide ? hib + words : hib;
     constexpr unsigned kFull = 0xffffffffu;
     const int slot = blockIdx.x;
     const int lane = threadIdx.x;
+    // entry p of the row; kShufWide keeps bit 16 in hib (set with atomics:
+    // a round's lanes write distinct entries that may share a word)
+    auto read = [&](uint32_t p) -> uint32_t {
+        uint32_t v = fy_row[p];
+        if (MODE == kShufWide) v |= ((hib[p >> 5] >> (p & 31u)) & 1u) << 16;
+        return v;
+    };
+    auto write = [&](uint32_t p, uint32_t v) {
+        fy_row[p] = (uint16_t)v;
+        if (MODE == kShufWide) {
+            const uint32_t b = 1u << (p & 31u);
+            if (v >> 16)
+                atomicOr(&hib[p >> 5], b);
+            else
+                atomicAnd(&hib[p >> 5], ~b);
+        }
+    };
     for (int i = lane; i < n; i += 32) fy_row[i] = (uint16_t)i;
+    if (MODE == kShufWide)
+        for (int w = lane; w < words; w += 32) hib[w] = w * 32 >= 65536 ? 0xffffffffu : 0u;
     if (!POS_FLAG)
-        for (int w = lane; w < (n + 31) / 32; w += 32) bitmap[w] = 0u;
+        for (int w = lane; w < words; w += 32) bitmap[w] = 0u;
     __syncwarp();
     const uint64_t base = seeds[slot] ^ mix64(streams[slot]);
     auto draw = [&](int s) { return mix64(base + (uint64_t)(s + 1) * kSplitMixGamma); };
@@ -167,10 +202,10 @@ __global__ void __launch_bounds__(32)
     uint32_t i = 0, j = 0;
     int run = last > 0 ? test(0, i, j) : 0;
     while (run > 0) {
-        uint16_t x = 0, y = 0;
+        uint32_t x = 0, y = 0;
         if (lane < run) {
-            x = fy_row[i];
-            y = fy_row[j];
+            x = read(i);
+            y = read(j);
         }
         if (POS_FLAG) __syncwarp();  // the loads are done before the next test flags
         // slide the window by run steps and test the next round
@@ -185,8 +220,8 @@ __global__ void __launch_bounds__(32)
         uint32_t in = 0, jn = 0;
         const int run_n = s0n < last ? test(s0n, in, jn) : 0;
         if (lane < run) {
-            fy_row[i] = y;
-            fy_row[j] = x;
+            write(i, y);
+            write(j, x);
         }
         __syncwarp();
         s0 = s0n;
@@ -208,11 +243,11 @@ __global__ void __launch_bounds__(32)
 #pragma unroll
             for (int u = 0; u < kBatch; ++u) {
                 const int t = t0 + u * 32 + lane;
-                if (t < n) out[t] = (int32_t)fy_row[o[u]];
+                if (t < n) out[t] = (int32_t)read((uint32_t)o[u]);
             }
         }
     } else {
-        for (int t = lane; t < n; t += 32) out[t] = (int32_t)fy_row[t];
+        for (int t = lane; t < n; t += 32) out[t] = (int32_t)read((uint32_t)t);
     }
 }
 

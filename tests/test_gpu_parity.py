@@ -343,12 +343,13 @@ def test_batch_full_size_sampled(idtx):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("n", [16384, 16385, 65536, 65537])
+@pytest.mark.parametrize("n", [16384, 16385, 32768, 32769, 65536, 65537, 102400, 102401])
 def test_shuffle_length_classes_sampled(idtx, n):
-    """Surrogate permutations of each row-length class: up to 16384 samples
-    (shared-memory shuffle, match.any test), 16385..65536 (shared-memory
-    shuffle, per-bit ballot test), beyond (in place in global memory); the
-    rows composed with the sample order (batched mode) and not (plain mode).
+    """Surrogate permutations of each row-length class: up to 32768 samples
+    (shared-memory row, equal-draw flags in the entries' top bits),
+    32769..65536 (shared-memory row, flag bitmap), 65537..102400 (entries'
+    bit 16 in a shared bitmap), beyond (in place in global memory); the rows
+    composed with the sample order (batched mode) and not (plain mode).
     Eps and counts of sampled queries of three surrogates exact against the
     oracle's permutations; the two modes' estimates within 1e-10."""
     g = synth.gaussian_problem(n, dx=1, dy=1, dz=1, seed=31 + n)
