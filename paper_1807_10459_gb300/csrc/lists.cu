@@ -1,13 +1,15 @@
 // lists.cu -- per-query sorted neighbour lists in the shared (Y,Z) and Z
 // subspaces, the preparation step of ksg_list_kernel (ksg_list.cuh).
 //
-// For every query i (sorted sample position) and every other sample j, the
-// max-norm distances d_Z(i,j) over the z columns and d_YZ(i,j) over the z and
-// y columns of sh are formed exactly as in the estimator's definition (fp32
-// |a-b| and maxima).  List A holds every j != i with d_YZ < r_A(i), list B
-// every j != i with d_Z < r_B(i), each ascending by (distance, j); r_A, r_B
-// are the largest histogram-bin edges for which the lists fit their
-// capacities (+inf when every sample fits).
+// For every query i (sorted sample position) and every other sample j that
+// may belong to a list (whole tiles that cannot are skipped: see the
+// kernel), the max-norm distances d_Z(i,j) over the z columns and d_YZ(i,j)
+// over the z and y columns of sh are formed exactly as in the estimator's
+// definition (fp32 |a-b| and maxima).  List A holds every j != i with
+// d_YZ < r_A(i), list B every j != i with d_Z < r_B(i), each ascending by
+// distance (equal distances in any order); r_A, r_B are the largest
+// histogram-bin edges for which the lists fit their capacities (+inf when
+// every sample fits).
 #include <cuda_runtime.h>
 
 #include <algorithm>
