@@ -35,11 +35,14 @@ constexpr int kSortRadixBits = 5;
 
 // Largest tile-visit bitmap (32-bit words): calls with more tiles visit all.
 constexpr int kMaxVisitWords = 1024;
-// Fewest tiles for which tile pruning runs: below, its per-query set-up (two
+// Tile pruning runs for calls of at least kPruneMinTiles tiles whose lists
+// hold at most an eighth of the samples: otherwise its per-query set-up (two
 // histogram clears, bounds of every tile, two ranking scans) costs more than
-// it saves (measured on GB300: N = 1000 lost 7 %, N = 9995 neither gained nor
-// lost, N = 99850 with lists of 512 and 1024 built 1.8x faster).
+// it saves (measured on GB300: N = 1000 lost 7 %; the greedy step's build,
+// N = 9995 with lists of 2048 and 4096, 0.15 ms; N = 99850 with lists of
+// 512 and 1024 was built 1.8x faster).
 constexpr int kPruneMinTiles = 64;
+constexpr int kPruneMaxListShare = 8;  // lists of at most n / 8 entries
 
 constexpr int kMaxRow4 = 5;  // float4 columns of a row of sh: dsp <= 20 (dz' <= 16, dy <= 4)
 constexpr int kUnrollJ = 4;  // samples a thread has in flight per step of a distance pass
@@ -179,7 +182,8 @@ __global__ void __launch_bounds__(kLThreads, 3)
     const int warp = tid >> 5;
     const int n_tiles = (int)((n + kTJ - 1) / kTJ);
     const int vwords = (n_tiles + 31) / 32;
-    const bool prune = vwords <= kMaxVisitWords && n_tiles >= kPruneMinTiles;
+    const bool prune = vwords <= kMaxVisitWords && n_tiles >= kPruneMinTiles &&
+                       (int64_t)max(cap_a, cap_b) * kPruneMaxListShare <= n;
     uint32_t *visit = reinterpret_cast<uint32_t *>(l_smem + visit_off);
     // Box gap and far-corner bounds of tile t in Z and (Y,Z).
     auto tile_bounds = [&](int t, float &gz, float &gyz, float &fz, float &fyz) {

@@ -118,10 +118,9 @@ __host__ __device__ constexpr int shuffle_mode(int64_t n)
 // the top bit of entry j itself in kShufPosFlag (every entry leaves that bit
 // free), else bit j of the flag bitmap.  Measured on GB300, 9447 rows of
 // 9995 written composed: 0.62 ms, against 0.79 ms with a 4096-bit bitmap
-// indexed by j mod 4096
-// (whose flags needed an exact match.any to confirm), 1.05 ms with
-// match.any in every round and 0.97 ms with one ballot per bit of j;
-// match.any has 373 cycles of latency there.
+// indexed by j mod 4096 (whose flags needed an exact match.any to confirm),
+// 1.05 ms with match.any in every round and 0.97 ms with one ballot per bit
+// of j; match.any has 373 cycles of latency there.
 template <int MODE>
 __global__ void __launch_bounds__(32)
     k_shuffle_smem(int32_t *perm, const uint64_t *streams, const uint64_t *seeds, int n,
